@@ -1,0 +1,178 @@
+/*
+ * lks.h -- C ABI of the GB300 lattice kinetic scheme for MHD with Shercliff
+ * thin-conducting-wall closures (Yahia & Premnath, arXiv 2112.13930).
+ *
+ * The problem a caller poses (Sec. VI.A, Sec. VII, App. B, App. C): a 2D
+ * channel of nx x ny nodes, periodic in x, bounded in y by two plates that
+ * carry wall conductance ratios c_bottom, c_top (Eq. wallconductanceratiodefinition)
+ * and tangential speeds u_bottom, u_top, with an applied field B0 along y and an
+ * optional body force Fx along x.  The library advances the coupled D2Q9
+ * hydrodynamic distribution f (Sec. V, Eq. LBMforflowfield, Maxwell stress in
+ * f^eq) and D2Q5 vector distribution g for the induced field (Sec. IV,
+ * Eq. LKSformagneticfield) with one fused collide-stream kernel per step, the
+ * chosen wall closure applied inside the same pass:
+ *   LKS_LINK   -- link-based weighted bounce-back / anti-bounce-back for g
+ *                 (Eq. linkbasedBCschemefinal, moving wall Eq.
+ *                 movingwalllinkbasedclosure) with half-way bounce-back for f
+ *                 (Sec. VI; moving wall App. B.1); walls half-way outside rows
+ *                 0 and ny-1, half-width a = ny/2;
+ *   LKS_MOMENT -- on-node moment-based closure for g (Eqs.
+ *                 momentbasedBCslowerboundary, momentbasedBCsupperboundary,
+ *                 momentbasedclosureformovingwall) with the moment-based no-slip
+ *                 closure for f (App. A, App. B.2); walls on rows 0 and ny-1,
+ *                 half-width a = (ny-1)/2.
+ *
+ * Units: lattice units, dx = dt = 1, c_s^2 = c_sm^2 = 1/3, rho0 = 1, mu_m = 1.
+ * Directions: D2Q9 e0=(0,0) e1=(1,0) e2=(0,1) e3=(-1,0) e4=(0,-1) e5=(1,1)
+ * e6=(-1,1) e7=(-1,-1) e8=(1,-1); D2Q5 uses e0..e4.
+ *
+ * Memory layout in HBM (structure of arrays, x fastest):
+ *   f[a][y][x] for a = 0..8 and g[k][a][y][x] for k = x,y component, a = 0..4,
+ *   stored as deviations from the rest equilibrium (rho = 1, u = 0,
+ *   B = (0, B0)) in the storage type of lks_params.storage; two such buffers
+ *   (ping-pong).  The state held between steps is the post-collision field.
+ *
+ * Ownership: a handle owns its device buffers, or borrows caller memory
+ * (lks_params.dev_buffer), which must outlive the handle.  Host pointers
+ * passed to any call are only read or written during that call.  A handle is
+ * not thread-safe; separate handles are independent.
+ *
+ * Streams: all device work of a handle is enqueued on lks_params.cuda_stream
+ * (a cudaStream_t, NULL = legacy default stream).  Calls documented as
+ * "asynchronous" return before the work finishes; errors of asynchronous work
+ * surface at the next synchronising call.
+ *
+ * Errors: every call returns an lks_status; LKS_OK is 0.  After an error,
+ * lks_last_error(h) (or lks_last_error(NULL) for handle-less calls) gives a
+ * one-line message.  A state that became non-finite gives LKS_EUNSTABLE.
+ */
+#ifndef LKS_H_
+#define LKS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LKS_OK = 0,
+    LKS_EINVAL = 1,          /* a parameter is out of range */
+    LKS_ENOMEM = 2,          /* device or host allocation failed, or dev_buffer too small */
+    LKS_ECUDA = 3,           /* a CUDA call failed */
+    LKS_EUNSTABLE = 4,       /* the state became non-finite */
+    LKS_ETIMEOUT = 5,        /* a bounded device wait gave up */
+    LKS_ENOTCONVERGED = 6,   /* max_steps reached before the residual tolerance */
+    LKS_EBUSY = 7            /* no free slot / memory budget (batched and served solves) */
+} lks_status;
+
+typedef enum { LKS_LINK = 0, LKS_MOMENT = 1 } lks_closure;
+
+/* Storage type of the populations; arithmetic is FP64 for LKS_F64 and FP32 otherwise. */
+typedef enum { LKS_F64 = 0, LKS_F32 = 1, LKS_BF16_DEV = 2, LKS_F16_DEV = 3 } lks_storage;
+
+typedef struct lks_params {
+    int32_t nx;            /* nodes along x (periodic), >= 1 */
+    int32_t ny;            /* nodes across the channel: >= 2 (link), >= 3 (moment) */
+    int32_t closure;       /* lks_closure */
+    int32_t storage;       /* lks_storage */
+    double tau_f;          /* relaxation time of f, > 1/2; nu = (tau_f - 1/2)/3 */
+    double tau_m;          /* relaxation time of g, > 1/2; eta = (tau_m - 1/2)/3 */
+    double B0;             /* applied field along y (Sec. VI.A) */
+    double Fx;             /* external body force along x */
+    uint64_t seed;         /* seed of the initial velocity perturbation */
+    double perturb_amp;    /* 0 => rest start; else u0 ~ U(-amp, amp) per component */
+    void* cuda_stream;     /* cudaStream_t; NULL = legacy default stream */
+    void* dev_buffer;      /* optional caller-owned device memory (NULL = library allocates) */
+    size_t dev_buffer_bytes; /* size of dev_buffer; must be >= lks_footprint_bytes() */
+} lks_params;
+
+typedef struct lks_handle lks_handle;
+
+/* Device bytes a handle with these parameters needs (both population buffers,
+ * residual snapshot, reduction and profile buffers); 0 if the parameters are
+ * invalid.  Used for admission control. */
+size_t lks_footprint_bytes(const lks_params* p);
+
+/* Validate p, allocate (or carve dev_buffer), and enqueue the initial state:
+ * equilibria at rho = 1, B = (0, B0), u = u0, where u0 = 0 or, if
+ * perturb_amp != 0, each component uniform in [-amp, amp] drawn from
+ * SplitMix64(seed XOR counter) with counter 2*node (x) and 2*node+1 (y),
+ * node = y*nx + x.  Both walls start insulating and at rest.  Asynchronous.
+ * *out is NULL on error. */
+lks_status lks_create(const lks_params* p, lks_handle** out);
+
+/* Set the Shercliff wall conductance ratios (>= 0; INFINITY = perfectly
+ * conducting) and tangential wall speeds (|u| < 0.3) of the bottom (row 0)
+ * and top (row ny-1) walls.  Only the closure coefficients change: theta =
+ * c a/(tau_m - 1/2) (Eq. weightingfactor) for LKS_LINK, beta = c a/(tau_m c_sm^2)
+ * for LKS_MOMENT (Eq. momentconstraintgx multiplied through by c a).  Takes
+ * effect for steps enqueued afterwards. */
+lks_status lks_set_walls(lks_handle* h, double c_bottom, double c_top, double u_bottom, double u_top);
+
+/* Enqueue n >= 0 fused collide-stream steps (steps a1-a6 of the hot path).
+ * Asynchronous; long runs go through a captured CUDA graph. */
+lks_status lks_step(lks_handle* h, int64_t n);
+
+/* Steps taken since lks_create / lks_set_state. */
+int64_t lks_steps_taken(const lks_handle* h);
+
+enum {
+    LKS_MOMENTS_NODES = 0,   /* out: 5 x ny x nx doubles: rho, u_x, u_y, B_x, B_y */
+    LKS_MOMENTS_PROFILES = 1 /* out: 5 x ny doubles: the same fields averaged over x */
+};
+
+/* Moments of the current state: rho = sum f, rho u = sum f e - F/2 (the
+ * post-collision form of rho u = sum f e + F/2 of Sec. V), B = sum g
+ * (Eq. zerothmomentofg), accumulated in FP64.  host_out is caller-allocated
+ * host memory.  Synchronises the stream. */
+lks_status lks_moments(lks_handle* h, int what, double* host_out);
+
+/* Same as lks_moments but writes into caller-allocated device memory
+ * dev_out, asynchronously on the handle's stream. */
+lks_status lks_moments_device(lks_handle* h, int what, double* dev_out);
+
+/* Steady-state residual (no criterion in the paper; the reading used here):
+ * r_u = |u_x - u_x'|_2 / |u_x|_2 and r_b = |B_x - B_x'|_2 / |B_x|_2 over all
+ * nodes, FP64, fixed reduction order, where ' is the snapshot taken by the
+ * previous lks_residual call (or at creation); the snapshot is then replaced.
+ * A term whose denominator is <= 1e-30 is reported as 0.  Returns
+ * LKS_EUNSTABLE if any moment is non-finite.  Synchronises the stream. */
+lks_status lks_residual(lks_handle* h, double* r_u, double* r_b);
+
+/* Repeat { lks_step(h, check_every); lks_residual } until max(r_u, r_b) < tol
+ * or max_steps steps have been taken.  *steps_out (nullable) gets the steps
+ * taken by this call and *r_out (nullable) the last residual.  Returns
+ * LKS_ENOTCONVERGED at max_steps.  Synchronises. */
+lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int64_t max_steps,
+                             int64_t* steps_out, double* r_out);
+
+/* Copy the state out as FP64 absolute populations (deviation + rest
+ * equilibrium): host_f 9 x ny x nx, host_g 2 x 5 x ny x nx, layouts as above.
+ * Synchronises. */
+lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g);
+
+/* Replace the state by FP64 absolute populations from host memory (same
+ * layout as lks_get_state), rounded to the storage type; resets the step
+ * counter and the residual snapshot.  Synchronises. */
+lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host_g);
+
+/* Block until all work of the handle has finished; reports asynchronous errors. */
+lks_status lks_sync(lks_handle* h);
+
+/* Release the handle and the memory it owns.  Safe on NULL. */
+lks_status lks_destroy(lks_handle* h);
+
+/* Message of the last error of h (NULL: of the calling thread's last
+ * handle-less error).  Never NULL. */
+const char* lks_last_error(const lks_handle* h);
+
+/* Static name of a status code. */
+const char* lks_status_string(lks_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LKS_H_ */
