@@ -1,0 +1,377 @@
+"""Benchmark of the fused LKS-MHD collide-stream step on GB300.
+
+Default workload (one "step" = one time step of the whole lattice, steps a1-a6 of the hot path in
+one fused kernel): shear-driven Hartmann-Couette channel, 4096 x 4096 nodes, periodic in x,
+moment-based Shercliff closure on both walls (c = 1), top wall at U_w = 0.05, Ha = 20,
+tau_f = tau_m = 0.8, rest start, FP32 deviation storage.  Inputs (2.5 GB of populations) are far
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the host cores instead.
+Multi-GPU runs (torchrun) are independent replicas, one lattice per GPU (the path does not shard).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (f+g)"
+UNIT = "MLUPS"
+BYTES_PER_NODE = {"f64": 304, "f32": 152, "bf16": 76, "f16": 76}
+
+
+def _workload(args):
+    n = args.n
+    return {
+        "workload": "Hartmann-Couette %dx%d, moment-based closure, U_w=0.05, Ha=20, c=1 both walls, "
+                    "tau_f=tau_m=0.8, rest start" % (n, n),
+        "nx": n, "ny": n, "closure": "moment", "storage": args.storage,
+        "l2": "inputs larger than L2 (%.2f GB of populations read per step vs 129 MB L2)"
+              % (BYTES_PER_NODE[args.storage] / 2 * n * n / 1e9),
+    }
+
+
+def _physics(n):
+    a = (n - 1) / 2
+    nu = eta = (0.8 - 0.5) / 3
+    b0 = 20.0 * math.sqrt(nu * eta) / a
+    return dict(tau_f=0.8, tau_m=0.8, B0=b0, Fx=0.0, c=1.0, u_w=0.05)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2112_13930_gb300/csrc/lks_step.cu", "paper_2112_13930_gb300/csrc/lks_device.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(storage, n):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it was taken on
+    the current kernel source (same hash) for this storage type; else None."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    for m in re.finditer(r"^traffic storage=(\w+) nodes=(\d+) kernel_hash=(\w+) dram_bytes=([0-9.eE+]+)$", text, re.M):
+        st, nodes, kh, b = m.group(1), int(m.group(2)), m.group(3), float(m.group(4))
+        if st == storage and kh == _kernel_hash():
+            return b * (n * n) / nodes
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_oracle_sample(n, seconds, phys):
+    """FP64 CPU oracle on the same lattice, as many whole steps as fit in about `seconds`."""
+    import numpy as np
+    import oracle
+    o = oracle.Oracle(n, n, phys["tau_f"], phys["tau_m"], phys["B0"], phys["Fx"], oracle.MOMENT,
+                      phys["c"], phys["c"], 0.0, phys["u_w"])
+    o.step(1)  # warm-up (page-in)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    mlups = n * n * steps / dt / 1e6
+    return {"value": round(mlups, 3), "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
+            "sample": "%d full steps of the %dx%d lattice (FP64, OpenMP over rows), %.1f s" % (steps, n, n, dt)}
+
+
+def bench_reference(args):
+    """The FP64 oracle on the host cores.  Each timed step is one oracle step over a bounded sample
+    of the lattice: the full 4096-wide channel cut to r rows (walls included), r chosen so that the
+    whole warm-up + timed run takes about --ref-seconds."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    phys = _physics(args.n)
+
+    def make(rows):
+        return oracle.Oracle(args.n, rows, phys["tau_f"], phys["tau_m"], phys["B0"], phys["Fx"], oracle.MOMENT,
+                             phys["c"], phys["c"], 0.0, phys["u_w"])
+
+    probe = make(256)
+    probe.step(1)
+    t0 = time.perf_counter()
+    probe.step(1)
+    t1 = time.perf_counter() - t0
+    del probe
+    per_step = args.ref_seconds / max(1, args.steps + args.warmup)
+    rows = int(max(3, min(args.n, 256 * per_step / max(t1, 1e-6))))
+    o = make(rows)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    mlups = args.n * rows * args.steps / dt / 1e6
+    cfg = _workload(args)
+    cfg["storage"] = "f64"
+    sample = "each step: one FP64 oracle step over %d x %d nodes of the %d x %d channel (walls included)" % (
+        args.n, rows, args.n, args.n)
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": cfg,
+            "cpu_baseline": {"value": round(mlups, 3), "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(mlups, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _time_steps(lat, steps, stream):
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    lat.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def bench_ours(args):
+    import numpy as np
+    import torch
+    from paper_2112_13930_gb300 import build, lks
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    lks.load()
+    n = args.n
+    phys = _physics(n)
+    stream = torch.cuda.current_stream()
+
+    def make(storage, nn=n):
+        lat = lks.Lattice(nn, nn, phys["tau_f"], phys["tau_m"], phys["B0"], phys["Fx"], "moment", storage)
+        lat.set_walls(phys["c"], phys["c"], 0.0, phys["u_w"])
+        return lat
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if ws > 1:
+            t = torch.tensor([x], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    # --- main measurement -------------------------------------------------------------------
+    lat = make(args.storage)
+    lat.step(args.warmup)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    t = _time_steps(lat, args.steps, stream)
+    barrier()
+    clocks = sampler.stop()
+    t = max_over_ranks(t)
+    nodes = n * n
+    value = nodes * args.steps * ws / t / 1e6
+    per_launch = t / args.steps
+    peak, peak_kind = _peaks()
+    bpn = BYTES_PER_NODE[args.storage]
+    achieved = bpn * nodes / per_launch / 1e9
+    traffic = _ncu_traffic(args.storage, n)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
+                "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": bpn * nodes, "kernel": "step_kernel<%s,moment>" % args.storage}
+    # sanity: the state must still be finite
+    ru, rb = lat.residual()
+
+    # --- end to end through the C ABI with host buffers -------------------------------------
+    e2e = None
+    if not args.skip_e2e:
+        f_host = torch.empty((9, n, n), dtype=torch.float64, pin_memory=True).numpy()
+        g_host = torch.empty((2, 5, n, n), dtype=torch.float64, pin_memory=True).numpy()
+        m_host = torch.empty((5, n, n), dtype=torch.float64, pin_memory=True).numpy()
+        f0, g0 = lat.get_state()  # a valid state to upload (taken outside the timed region)
+        f_host[...] = f0
+        g_host[...] = g0
+        del f0, g0
+        barrier()
+        t0 = time.perf_counter()
+        lat.set_state(f_host, g_host)       # H2D from pinned host memory + conversion
+        lat.step(args.steps)
+        lks._check(lks.load().lks_moments(lat._h, lks.MOMENTS_NODES, lks._dptr(m_host)), lat._h)  # D2H
+        barrier()
+        te = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": round(nodes * args.steps * ws / te / 1e6, 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(round(19 * 8 * nodes / args.steps)),
+               "d2h_bytes_per_step": int(round(5 * 8 * nodes / args.steps)),
+               "timed": "lks_set_state (FP64 host->device + conversion) + lks_step(K) + lks_moments (nodes, "
+                        "device->host), pinned host buffers"}
+        del f_host, g_host, m_host
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+
+    # --- FP64 storage on the same workload (compute-bound on GB300's FP64 rate) --------------
+    extra = {}
+    if not args.skip_extra:
+        k64 = max(10, min(args.steps, args.fp64_steps))
+        l64 = make("f64")
+        l64.step(3)
+        barrier()
+        t64 = max_over_ranks(_time_steps(l64, k64, stream))
+        v64 = nodes * k64 * ws / t64 / 1e6
+        a64 = 304 * nodes / (t64 / k64) / 1e9
+        extra["fp64"] = {"value": round(v64, 1), "unit": UNIT, "steps": k64,
+                         "roofline_hbm": {"achieved": round(a64, 1), "peak": peak, "unit": "GB/s",
+                                          "frac": round(a64 / peak, 4)},
+                         "roofline_alu": {"bound": "alu", "flops_per_node": FP64_FLOPS_PER_NODE,
+                                          "achieved": round(FP64_FLOPS_PER_NODE * v64 * 1e6 / 1e12, 3),
+                                          "peak": 1.25, "unit": "TFLOP/s",
+                                          "frac": round(FP64_FLOPS_PER_NODE * v64 * 1e6 / 1.25e12, 4),
+                                          "peak_source": "nominal GB300 FP64 rate"}}
+        l64.close()
+        del l64
+        for st in ("bf16", "f16"):
+            lr = make(st)
+            lr.step(3)
+            barrier()
+            kr = max(10, min(args.steps, 2000))
+            tr = max_over_ranks(_time_steps(lr, kr, stream))
+            vr = nodes * kr * ws / tr / 1e6
+            ar = 76 * nodes / (tr / kr) / 1e9
+            extra[st] = {"value": round(vr, 1), "unit": UNIT, "steps": kr,
+                         "roofline": {"bound": "hbm", "achieved": round(ar, 1), "peak": peak, "unit": "GB/s",
+                                      "frac": round(ar / peak, 4)}}
+            lr.close()
+            del lr
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = run_oracle_sample(n, args.cpu_seconds, phys)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(per_launch * 1e3, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage != "f64" else "f64",
+                "data": "synthetic", "config": _workload(args), "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+                "residual_after_run": [ru, rb], "parallelism": "replicas" if ws > 1 else "single GPU"}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+# FP64 arithmetic per node per step in the fused kernel (adds, multiplies, FMAs counted as 2,
+# one division), counted from the kernel source; used for the FP64 ALU roofline.
+FP64_FLOPS_PER_NODE = 260
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f32", "f64", "bf16", "f16"], default="f32")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--fp64-steps", type=int, default=300)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

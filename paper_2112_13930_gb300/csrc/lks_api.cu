@@ -1,0 +1,468 @@
+// lks_api.cu -- the C ABI declared in include/lks.h: parameter validation, device memory
+// layout, wall-closure coefficients, CUDA-graph stepping, moments and residual calls.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/lks.h"
+#include "lks_internal.h"
+
+using lks::StepParams;
+using lks::WallCoef;
+
+namespace {
+
+thread_local std::string g_last_error = "";
+constexpr int64_t kGraphSteps = 64;  // even, so a graph returns the state to the buffer it started in
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct Layout {
+    size_t f_bytes, g_bytes, off_fa, off_ga, off_fb, off_gb, off_snap, off_partial, off_out, off_prof, total;
+};
+
+Layout make_layout(const lks_params* p) {
+    Layout L;
+    const size_t N = (size_t)p->nx * (size_t)p->ny;
+    const size_t sb = lks::storage_bytes(p->storage);
+    L.f_bytes = align_up(9 * N * sb);
+    L.g_bytes = align_up(10 * N * sb);
+    size_t o = 0;
+    L.off_fa = o; o += L.f_bytes;
+    L.off_ga = o; o += L.g_bytes;
+    L.off_fb = o; o += L.f_bytes;
+    L.off_gb = o; o += L.g_bytes;
+    L.off_snap = o; o += align_up(2 * N * sizeof(double));
+    L.off_partial = o; o += align_up(4 * (size_t)lks::residual_blocks((int64_t)N) * sizeof(double));
+    L.off_out = o; o += align_up(8 * sizeof(double));
+    L.off_prof = o; o += align_up(5 * (size_t)p->ny * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+const char* validate(const lks_params* p) {
+    if (!p) return "params is NULL";
+    if (p->nx < 1) return "nx must be >= 1";
+    if (p->closure != LKS_LINK && p->closure != LKS_MOMENT) return "closure must be LKS_LINK or LKS_MOMENT";
+    if (p->closure == LKS_LINK && p->ny < 2) return "ny must be >= 2 for the link-based closure";
+    if (p->closure == LKS_MOMENT && p->ny < 3) return "ny must be >= 3 for the moment-based closure";
+    if (p->storage < LKS_F64 || p->storage > LKS_F16_DEV) return "storage must be one of lks_storage";
+    if ((int64_t)p->nx * (int64_t)p->ny > (int64_t)1 << 30) return "nx*ny exceeds 2^30 nodes";
+    if (!(p->tau_f > 0.5) || !isfinite(p->tau_f)) return "tau_f must be finite and > 1/2";
+    if (!(p->tau_m > 0.5) || !isfinite(p->tau_m)) return "tau_m must be finite and > 1/2";
+    if (!isfinite(p->B0) || !isfinite(p->Fx)) return "B0 and Fx must be finite";
+    if (!isfinite(p->perturb_amp) || fabs(p->perturb_amp) >= 0.3) return "|perturb_amp| must be < 0.3";
+    return nullptr;
+}
+
+}  // namespace
+
+struct lks_handle {
+    lks_params p;
+    Layout L;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    char* base = nullptr;
+    bool owns = false;
+    void* f[2] = {nullptr, nullptr};
+    void* g[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* snap = nullptr;
+    double* partial = nullptr;
+    double* dout = nullptr;
+    double* prof = nullptr;
+    double* node_stage = nullptr;  // lazily allocated 5*N doubles for per-node host moments
+    double* host_small = nullptr;  // pinned 8 doubles
+    double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
+    StepParams<double> sp;
+    int64_t steps = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graphs_disabled = false;
+    std::string err;
+};
+
+namespace {
+
+lks_status fail(lks_handle* h, lks_status s, const std::string& msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_last_error = msg;
+    return s;
+}
+
+lks_status cuda_fail(lks_handle* h, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, LKS_ECUDA, m);
+}
+
+double half_width(const lks_params& p) { return p.closure == LKS_LINK ? 0.5 * p.ny : 0.5 * (p.ny - 1); }
+
+// Closure coefficients of one wall (see WallCoef).  e_y = +1 for the bottom wall's incoming
+// direction, -1 for the top wall's.
+WallCoef<double> wall_coef(const lks_params& p, double c, double U, double ey) {
+    WallCoef<double> w;
+    const double a = half_width(p);
+    const double B0 = p.B0;
+    w.U = U;
+    w.du = 6.0 * (1.0 / 36.0) * U;  // 2 w_a e_ax U / c_s^2 for the diagonal links (|e_ax| = 1)
+    if (p.closure == LKS_LINK) {
+        // theta = c a / (tau_m - 1/2) (Eq. weightingfactor); r = (theta-1)/(theta+1),
+        // s = 2 theta/(theta+1); kx = -s W e_y B0 U / c_sm^2 with W = 1/6 (Eq. movingwalllinkbasedclosure)
+        double r, s;
+        if (isinf(c)) {
+            r = 1.0;
+            s = 2.0;
+        } else {
+            const double theta = c * a / (p.tau_m - 0.5);
+            r = (theta - 1.0) / (theta + 1.0);
+            s = 2.0 * theta / (theta + 1.0);
+        }
+        w.r = r;
+        w.bc = 0.0;
+        w.kx = -s * (1.0 / 6.0) * ey * B0 * U * 3.0;
+    } else {
+        // beta = c a / (tau_m c_sm^2): unknown = [(beta-1) opp - (g0+g1+g3) - e_y beta B0 U]/(beta+1)
+        double r, bc, k;
+        if (isinf(c)) {
+            r = 1.0;
+            bc = 0.0;
+            k = 1.0;
+        } else {
+            const double beta = c * a / (p.tau_m / 3.0);
+            r = (beta - 1.0) / (beta + 1.0);
+            bc = 1.0 / (beta + 1.0);
+            k = beta / (beta + 1.0);
+        }
+        w.r = r;
+        w.bc = bc;
+        w.kx = -ey * k * B0 * U;
+    }
+    return w;
+}
+
+void refresh_params(lks_handle* h) {
+    const lks_params& p = h->p;
+    StepParams<double>& s = h->sp;
+    s.nx = p.nx;
+    s.ny = p.ny;
+    s.N = (int64_t)p.nx * p.ny;
+    s.omega_f = 1.0 / p.tau_f;
+    s.omega_m = 1.0 / p.tau_m;
+    s.src_coef = 1.0 - 0.5 / p.tau_f;
+    s.Fx = p.Fx;
+    s.B0 = p.B0;
+    s.bot = wall_coef(p, h->c_bot, h->u_bot, +1.0);
+    s.top = wall_coef(p, h->c_top, h->u_top, -1.0);
+}
+
+void drop_graphs(lks_handle* h) {
+    for (int k = 0; k < 2; ++k)
+        if (h->graph[k]) {
+            cudaGraphExecDestroy(h->graph[k]);
+            h->graph[k] = nullptr;
+        }
+}
+
+cudaError_t step_once(lks_handle* h, int src, cudaStream_t st) {
+    return lks::launch_step(h->p.storage, h->p.closure, h->f[src], h->g[src], h->f[src ^ 1], h->g[src ^ 1], h->sp, st);
+}
+
+// Capture kGraphSteps steps starting from buffer `start` into an executable graph.
+cudaError_t build_graph(lks_handle* h, int start) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    int src = start;
+    cudaError_t le = cudaSuccess;
+    for (int64_t k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
+        le = step_once(h, src, h->cap_stream);
+        src ^= 1;
+    }
+    e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return le;
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&h->graph[start], graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lks_footprint_bytes(const lks_params* p) {
+    if (validate(p)) return 0;
+    return make_layout(p).total;
+}
+
+lks_status lks_create(const lks_params* p, lks_handle** out) {
+    if (!out) return fail(nullptr, LKS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (const char* m = validate(p)) return fail(nullptr, LKS_EINVAL, m);
+    lks_handle* h = new (std::nothrow) lks_handle();
+    if (!h) return fail(nullptr, LKS_ENOMEM, "host allocation of the handle failed");
+    h->p = *p;
+    h->L = make_layout(p);
+    h->stream = (cudaStream_t)p->cuda_stream;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(nullptr, e, "cudaGetDevice");
+    }
+    if (p->dev_buffer) {
+        if (p->dev_buffer_bytes < h->L.total || ((uintptr_t)p->dev_buffer % kAlign) != 0) {
+            delete h;
+            return fail(nullptr, LKS_ENOMEM, "dev_buffer is smaller than lks_footprint_bytes() or not 256-byte aligned");
+        }
+        h->base = (char*)p->dev_buffer;
+        h->owns = false;
+    } else {
+        e = cudaMalloc((void**)&h->base, h->L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(nullptr, LKS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        h->owns = true;
+    }
+    h->f[0] = h->base + h->L.off_fa;
+    h->g[0] = h->base + h->L.off_ga;
+    h->f[1] = h->base + h->L.off_fb;
+    h->g[1] = h->base + h->L.off_gb;
+    h->snap = (double*)(h->base + h->L.off_snap);
+    h->partial = (double*)(h->base + h->L.off_partial);
+    h->dout = (double*)(h->base + h->L.off_out);
+    h->prof = (double*)(h->base + h->L.off_prof);
+    e = cudaHostAlloc((void**)&h->host_small, 8 * sizeof(double), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        lks_destroy(h);
+        return cuda_fail(nullptr, e, "lks_create");
+    }
+    refresh_params(h);
+    e = lks::launch_init(p->storage, h->f[0], h->g[0], p->nx, p->ny, p->B0, p->seed, p->perturb_amp, h->stream);
+    if (e == cudaSuccess)
+        e = lks::launch_snapshot(p->storage, h->f[0], h->g[0], p->nx, p->ny, p->B0, p->Fx, h->snap, h->stream);
+    if (e != cudaSuccess) {
+        lks_destroy(h);
+        return cuda_fail(nullptr, e, "lks_create: init kernel");
+    }
+    *out = h;
+    return LKS_OK;
+}
+
+lks_status lks_set_walls(lks_handle* h, double c_bottom, double c_top, double u_bottom, double u_top) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!(c_bottom >= 0.0) || !(c_top >= 0.0)) return fail(h, LKS_EINVAL, "wall conductance ratios must be >= 0");
+    if (!(fabs(u_bottom) < 0.3) || !(fabs(u_top) < 0.3)) return fail(h, LKS_EINVAL, "|wall speed| must be < 0.3");
+    h->c_bot = c_bottom;
+    h->c_top = c_top;
+    h->u_bot = u_bottom;
+    h->u_top = u_top;
+    refresh_params(h);
+    drop_graphs(h);
+    return LKS_OK;
+}
+
+lks_status lks_step(lks_handle* h, int64_t n) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (n < 0) return fail(h, LKS_EINVAL, "n must be >= 0");
+    while (n >= kGraphSteps && !h->graphs_disabled) {
+        if (!h->graph[h->cur]) {
+            cudaError_t e = build_graph(h, h->cur);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                h->graphs_disabled = true;  // fall back to direct launches
+                break;
+            }
+        }
+        cudaError_t e = cudaGraphLaunch(h->graph[h->cur], h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+        n -= kGraphSteps;
+        h->steps += kGraphSteps;
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        cudaError_t e = step_once(h, h->cur, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel launch");
+        h->cur ^= 1;
+        h->steps += 1;
+    }
+    return LKS_OK;
+}
+
+int64_t lks_steps_taken(const lks_handle* h) { return h ? h->steps : -1; }
+
+lks_status lks_moments_device(lks_handle* h, int what, double* dev_out) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!dev_out) return fail(h, LKS_EINVAL, "dev_out is NULL");
+    if (what != LKS_MOMENTS_NODES && what != LKS_MOMENTS_PROFILES) return fail(h, LKS_EINVAL, "bad 'what'");
+    cudaError_t e = lks::launch_moments(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0,
+                                        h->p.Fx, what, dev_out, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
+    return LKS_OK;
+}
+
+lks_status lks_moments(lks_handle* h, int what, double* host_out) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!host_out) return fail(h, LKS_EINVAL, "host_out is NULL");
+    if (what != LKS_MOMENTS_NODES && what != LKS_MOMENTS_PROFILES) return fail(h, LKS_EINVAL, "bad 'what'");
+    const size_t N = (size_t)h->p.nx * h->p.ny;
+    double* dst = h->prof;
+    size_t count = 5 * (size_t)h->p.ny;
+    if (what == LKS_MOMENTS_NODES) {
+        if (!h->node_stage) {
+            cudaError_t e = cudaMalloc((void**)&h->node_stage, 5 * N * sizeof(double));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                h->node_stage = nullptr;
+                return fail(h, LKS_ENOMEM, "cudaMalloc of the per-node moment staging buffer failed");
+            }
+        }
+        dst = h->node_stage;
+        count = 5 * N;
+    }
+    lks_status s = lks_moments_device(h, what, dst);
+    if (s != LKS_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(host_out, dst, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lks_moments");
+    return LKS_OK;
+}
+
+lks_status lks_residual(lks_handle* h, double* r_u, double* r_b) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    cudaError_t e = lks::launch_residual(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0,
+                                         h->p.Fx, h->snap, h->partial, h->dout, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->host_small, h->dout, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lks_residual");
+    const double* s = h->host_small;
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(s[k])) return fail(h, LKS_EUNSTABLE, "the state became non-finite");
+    const double ru = s[1] > 1e-60 ? sqrt(s[0] / s[1]) : 0.0;
+    const double rb = s[3] > 1e-60 ? sqrt(s[2] / s[3]) : 0.0;
+    if (r_u) *r_u = ru;
+    if (r_b) *r_b = rb;
+    return LKS_OK;
+}
+
+lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int64_t max_steps, int64_t* steps_out,
+                             double* r_out) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (check_every < 1 || max_steps < 0 || !(tol > 0.0)) return fail(h, LKS_EINVAL, "bad run_to_steady arguments");
+    int64_t taken = 0;
+    double r = INFINITY;
+    lks_status s = LKS_OK;
+    while (taken < max_steps) {
+        const int64_t n = (max_steps - taken < check_every) ? max_steps - taken : check_every;
+        s = lks_step(h, n);
+        if (s != LKS_OK) break;
+        taken += n;
+        double ru, rb;
+        s = lks_residual(h, &ru, &rb);
+        if (s != LKS_OK) break;
+        r = ru > rb ? ru : rb;
+        if (r < tol) break;
+    }
+    if (steps_out) *steps_out = taken;
+    if (r_out) *r_out = r;
+    if (s != LKS_OK) return s;
+    if (!(r < tol)) return fail(h, LKS_ENOTCONVERGED, "max_steps reached before the residual tolerance");
+    return LKS_OK;
+}
+
+lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
+    const size_t N = (size_t)h->p.nx * h->p.ny;
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc((void**)&tmp, 19 * N * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
+    }
+    e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], (int64_t)N, h->p.B0, tmp, tmp + 9 * N,
+                           h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_g, tmp + 9 * N, 10 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lks_get_state");
+    return LKS_OK;
+}
+
+lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host_g) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
+    const size_t N = (size_t)h->p.nx * h->p.ny;
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc((void**)&tmp, 19 * N * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
+    }
+    e = cudaMemcpyAsync(tmp, host_f, 9 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tmp + 9 * N, host_g, 10 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = lks::launch_from_abs(h->p.storage, tmp, tmp + 9 * N, (int64_t)N, h->p.B0, h->f[h->cur], h->g[h->cur],
+                                 h->stream);
+    if (e == cudaSuccess)
+        e = lks::launch_snapshot(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0, h->p.Fx,
+                                 h->snap, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lks_set_state");
+    h->steps = 0;
+    return LKS_OK;
+}
+
+lks_status lks_sync(lks_handle* h) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "lks_sync");
+    return LKS_OK;
+}
+
+lks_status lks_destroy(lks_handle* h) {
+    if (!h) return LKS_OK;
+    if (h->stream || h->base) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    if (h->node_stage) cudaFree(h->node_stage);
+    if (h->owns && h->base) cudaFree(h->base);
+    if (h->host_small) cudaFreeHost(h->host_small);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+    return LKS_OK;
+}
+
+const char* lks_last_error(const lks_handle* h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+const char* lks_status_string(lks_status s) {
+    switch (s) {
+        case LKS_OK: return "LKS_OK";
+        case LKS_EINVAL: return "LKS_EINVAL";
+        case LKS_ENOMEM: return "LKS_ENOMEM";
+        case LKS_ECUDA: return "LKS_ECUDA";
+        case LKS_EUNSTABLE: return "LKS_EUNSTABLE";
+        case LKS_ETIMEOUT: return "LKS_ETIMEOUT";
+        case LKS_ENOTCONVERGED: return "LKS_ENOTCONVERGED";
+        case LKS_EBUSY: return "LKS_EBUSY";
+    }
+    return "LKS_UNKNOWN";
+}
+
+}  // extern "C"

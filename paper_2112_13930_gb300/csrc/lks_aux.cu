@@ -1,0 +1,278 @@
+// lks_aux.cu -- initial state, moments, x-averaged profiles, the steady-state residual
+// reduction and the FP64 <-> storage conversions.  None of these is on the per-step path.
+#include "lks_device.cuh"
+#include "lks_internal.h"
+
+namespace lks {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double w9(int a) { return a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+__device__ __forceinline__ double w5(int a) { return a == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+__device__ __forceinline__ int ex9(int a) {
+    const int t[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    return t[a];
+}
+__device__ __forceinline__ int ey9(int a) {
+    const int t[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    return t[a];
+}
+// Rest equilibrium f^eq(rho = 1, u = 0, B = (0, B0)) including the Maxwell stress.
+__device__ __forceinline__ double f_rest(int a, double B0) {
+    const double m = (a == 1 || a == 3) ? 0.5 * B0 * B0 : ((a == 2 || a == 4) ? -0.5 * B0 * B0 : 0.0);
+    return w9(a) * (1.0 + 4.5 * m);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) of seed XOR counter -> [0, 1) with 53 bits.
+__device__ __forceinline__ double splitmix_unit(uint64_t seed, uint64_t counter) {
+    uint64_t z = (seed ^ counter) + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+template <typename S, typename C>
+__global__ void init_kernel(S* f, S* g, int64_t N, double B0, uint64_t seed, double amp) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double ux = 0.0, uy = 0.0;
+    if (amp != 0.0) {
+        ux = amp * (2.0 * splitmix_unit(seed, 2ull * (uint64_t)n) - 1.0);
+        uy = amp * (2.0 * splitmix_unit(seed, 2ull * (uint64_t)n + 1ull) - 1.0);
+    }
+    const double usq = 1.5 * (ux * ux + uy * uy);
+    for (int a = 0; a < 9; ++a) {
+        const double eu = ex9(a) * ux + ey9(a) * uy;
+        const double b = 3.0 * eu + 4.5 * eu * eu - usq;  // rho = 1, B = rest
+        store_s<S, C>(f + a * N + n, (C)(w9(a) * b));
+    }
+    const double E = ux * B0;  // u_x B_y - u_y B_x at B = (0, B0)
+    for (int a = 0; a < 5; ++a) {
+        store_s<S, C>(g + a * N + n, (C)(-3.0 * w5(a) * ey9(a) * E));
+        store_s<S, C>(g + (5 + a) * N + n, (C)(3.0 * w5(a) * ex9(a) * E));
+    }
+}
+
+// FP64 moments of node n of a stored state: rho, u_x, u_y, B_x, B_y.
+template <typename S, typename C>
+__device__ __forceinline__ void node_moments(const S* f, const S* g, int64_t N, int64_t n, double B0, double Fx,
+                                             double m[5]) {
+    double drho = 0.0, jx = 0.0, jy = 0.0, bx = 0.0, dby = 0.0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const double v = (double)load_s<S, C>(f + a * N + n);
+        drho += v;
+        jx += ex9(a) * v;
+        jy += ey9(a) * v;
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+        bx += (double)load_s<S, C>(g + a * N + n);
+        dby += (double)load_s<S, C>(g + (5 + a) * N + n);
+    }
+    const double rho = 1.0 + drho;
+    m[0] = rho;
+    m[1] = (jx - 0.5 * Fx) / rho;
+    m[2] = jy / rho;
+    m[3] = bx;
+    m[4] = B0 + dby;
+}
+
+template <typename S, typename C>
+__global__ void moments_kernel(const S* f, const S* g, int64_t N, double B0, double Fx, double* out) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double m[5];
+    node_moments<S, C>(f, g, N, n, B0, Fx, m);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) out[k * N + n] = m[k];
+}
+
+// Fixed-order block sum of K values per thread (tree in shared memory).
+template <int K>
+__device__ __forceinline__ void block_sum(double v[K], double* sh) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k * kThreads + t] = v[k];
+    __syncthreads();
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
+        if (t < s) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) sh[k * kThreads + t] += sh[k * kThreads + t + s];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = sh[k * kThreads];
+}
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(kThreads) profiles_kernel(const S* f, const S* g, int nx, int ny, double B0,
+                                                           double Fx, double* out) {
+    __shared__ double sh[5 * kThreads];
+    const int j = blockIdx.x;
+    const int64_t N = (int64_t)nx * ny;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < nx; i += kThreads) {
+        double m[5];
+        node_moments<S, C>(f, g, N, (int64_t)j * nx + i, B0, Fx, m);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[k] += m[k];
+    }
+    block_sum<5>(acc, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) out[k * ny + j] = acc[k] / nx;
+}
+
+template <typename S, typename C>
+__global__ void __launch_bounds__(kThreads) residual_partial_kernel(const S* f, const S* g, int64_t N, double B0,
+                                                                   double Fx, double* snap, double* partial) {
+    __shared__ double sh[4 * kThreads];
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x; n < N; n += (int64_t)gridDim.x * kThreads) {
+        double m[5];
+        node_moments<S, C>(f, g, N, n, B0, Fx, m);
+        const double du = m[1] - snap[n];
+        const double db = m[3] - snap[N + n];
+        acc[0] += du * du;
+        acc[1] += m[1] * m[1];
+        acc[2] += db * db;
+        acc[3] += m[3] * m[3];
+        snap[n] = m[1];
+        snap[N + n] = m[3];
+    }
+    block_sum<4>(acc, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) partial[4 * blockIdx.x + k] = acc[k];
+}
+
+__global__ void __launch_bounds__(kThreads) residual_final_kernel(const double* partial, int nblk, double* out) {
+    __shared__ double sh[4 * kThreads];
+    double acc[4] = {0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblk; b += kThreads)
+        for (int k = 0; k < 4; ++k) acc[k] += partial[4 * b + k];
+    block_sum<4>(acc, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) out[k] = acc[k];
+}
+
+template <typename S, typename C>
+__global__ void snapshot_kernel(const S* f, const S* g, int64_t N, double B0, double Fx, double* snap) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double m[5];
+    node_moments<S, C>(f, g, N, n, B0, Fx, m);
+    snap[n] = m[1];
+    snap[N + n] = m[3];
+}
+
+template <typename S, typename C>
+__global__ void to_abs_kernel(const S* f, const S* g, int64_t N, double B0, double* fa, double* ga) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    for (int a = 0; a < 9; ++a) fa[a * N + n] = (double)load_s<S, C>(f + a * N + n) + f_rest(a, B0);
+    for (int a = 0; a < 5; ++a) {
+        ga[a * N + n] = (double)load_s<S, C>(g + a * N + n);
+        ga[(5 + a) * N + n] = (double)load_s<S, C>(g + (5 + a) * N + n) + w5(a) * B0;
+    }
+}
+
+template <typename S, typename C>
+__global__ void from_abs_kernel(const double* fa, const double* ga, int64_t N, double B0, S* f, S* g) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    for (int a = 0; a < 9; ++a) store_s<S, C>(f + a * N + n, (C)(fa[a * N + n] - f_rest(a, B0)));
+    for (int a = 0; a < 5; ++a) {
+        store_s<S, C>(g + a * N + n, (C)ga[a * N + n]);
+        store_s<S, C>(g + (5 + a) * N + n, (C)(ga[(5 + a) * N + n] - w5(a) * B0));
+    }
+}
+
+inline unsigned grid_for(int64_t N) { return (unsigned)((N + kThreads - 1) / kThreads); }
+
+}  // namespace
+
+#define LKS_DISPATCH(storage, CALL)                          \
+    do {                                                     \
+        if ((storage) == 0) {                                \
+            typedef double S;                                \
+            typedef double C;                                \
+            CALL;                                            \
+        } else if ((storage) == 1) {                         \
+            typedef float S;                                 \
+            typedef float C;                                 \
+            CALL;                                            \
+        } else if ((storage) == 2) {                         \
+            typedef __nv_bfloat16 S;                         \
+            typedef float C;                                 \
+            CALL;                                            \
+        } else {                                             \
+            typedef __half S;                                \
+            typedef float C;                                 \
+            CALL;                                            \
+        }                                                    \
+    } while (0)
+
+cudaError_t launch_init(int storage, void* f, void* g, int nx, int ny, double B0, uint64_t seed, double amp,
+                        cudaStream_t st) {
+    const int64_t N = (int64_t)nx * ny;
+    LKS_DISPATCH(storage, (init_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((S*)f, (S*)g, N, B0, seed, amp)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
+                           int what, double* out, cudaStream_t st) {
+    const int64_t N = (int64_t)nx * ny;
+    if (what == 0) {
+        LKS_DISPATCH(storage, (moments_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N,
+                                                                                      B0, Fx, out)));
+    } else {
+        LKS_DISPATCH(storage, (profiles_kernel<S, C><<<ny, kThreads, 0, st>>>((const S*)f, (const S*)g, nx, ny, B0,
+                                                                              Fx, out)));
+    }
+    return cudaGetLastError();
+}
+
+int residual_blocks(int64_t N) {
+    int64_t b = (N + 2047) / 2048;
+    if (b < 1) b = 1;
+    if (b > 1216) b = 1216;  // 8 per SM on 152 SMs
+    return (int)b;
+}
+
+cudaError_t launch_residual(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
+                            double* snap, double* partial, double* out, cudaStream_t st) {
+    const int64_t N = (int64_t)nx * ny;
+    const int nblk = residual_blocks(N);
+    LKS_DISPATCH(storage, (residual_partial_kernel<S, C><<<nblk, kThreads, 0, st>>>((const S*)f, (const S*)g, N,
+                                                                                    B0, Fx, snap, partial)));
+    residual_final_kernel<<<1, kThreads, 0, st>>>(partial, nblk, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
+                            double* snap, cudaStream_t st) {
+    const int64_t N = (int64_t)nx * ny;
+    LKS_DISPATCH(storage, (snapshot_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N, B0,
+                                                                                   Fx, snap)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, double B0, double* fabs,
+                          double* gabs, cudaStream_t st) {
+    LKS_DISPATCH(storage, (to_abs_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N, B0,
+                                                                                 fabs, gabs)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, double B0, void* f,
+                            void* g, cudaStream_t st) {
+    LKS_DISPATCH(storage, (from_abs_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>(fabs, gabs, N, B0, (S*)f,
+                                                                                   (S*)g)));
+    return cudaGetLastError();
+}
+
+}  // namespace lks

@@ -1,0 +1,168 @@
+// lks_device.cuh -- device-side building blocks of the fused LKS-MHD step.
+//
+// Everything here works on deviations from the rest equilibrium
+//   f_rest_a = f^eq_a(rho = 1, u = 0, B = (0, B0)),  g_rest_xa = 0,  g_rest_ya = W_a B0,
+// so that FP32 and 16-bit storage keep the small signal (u ~ 1e-2, B_x ~ 1e-2 B0 scales)
+// instead of the O(1) rest populations.  With d = f - f_rest:
+//   rho - 1 = sum d, rho u = sum d e (+ F/2), B_x = sum dg_x, B_y - B0 = sum dg_y,
+// because the rest populations have unit mass, no first moment and sum_a W_a = 1.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lks {
+
+// Coefficients of one wall's closure, precomputed on the host in FP64.
+//   link   : g_in,x = r * g_out,x(opposite, own node) + kx      (Eq. movingwalllinkbasedclosure)
+//            f_in   = f_out(opposite, own node) +/- du          (Ladd's moving bounce-back, App. B.1)
+//   moment : g_unknown,x = r * g_opposite,x - bc * (g0x + g1x + g3x) + kx
+//            (Eq. momentconstraintgx / momentbasedclosureformovingwall times c a, beta = c a/(tau_m c^2),
+//             r = (beta-1)/(beta+1), bc = 1/(beta+1), kx = -/+ beta/(beta+1) B0 U)
+//            f: moment closure of App. A / App. B.2 with wall speed U.
+template <typename C>
+struct WallCoef {
+    C r, bc, kx, du, U;
+};
+
+template <typename C>
+struct StepParams {
+    int32_t nx, ny;
+    int64_t N;            // nx * ny
+    C omega_f;            // 1 / tau_f
+    C omega_m;            // 1 / tau_m
+    C src_coef;           // 1 - 1/(2 tau_f)
+    C Fx;                 // body force along x
+    C B0;                 // applied field along y
+    WallCoef<C> bot, top;
+};
+
+// Storage conversions (round to nearest even on the way down).
+template <typename S, typename C> __device__ __forceinline__ C load_s(const S* p);
+template <> __device__ __forceinline__ double load_s<double, double>(const double* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float load_s<float, float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float load_s<__nv_bfloat16, float>(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float load_s<__half, float>(const __half* p) { return __half2float(__ldg(p)); }
+
+template <typename S, typename C> __device__ __forceinline__ void store_s(S* p, C v);
+template <> __device__ __forceinline__ void store_s<double, double>(double* p, double v) { *p = v; }
+template <> __device__ __forceinline__ void store_s<float, float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void store_s<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
+    *p = __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ void store_s<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
+
+// Equilibrium deviations and the collision, for one node whose post-stream, post-closure
+// populations are in f[9], gx[5], gy[5] (deviation form).  Overwrites them with the
+// post-collision deviations.  Returns nothing; moments are recomputed by callers that need them.
+//
+// f^eq (Sec. V) with Dellar's Maxwell stress:
+//   f^eq_a = w_a [rho + 3 rho e.u + 4.5 rho (e.u)^2 - 1.5 rho u^2]
+//          + 4.5 w_a [ |B|^2 |e_a|^2 / 2 - (e_a . B)^2 ]
+// source (Sec. V): S_a = 3 (e_a - u) . F  f^eq,hyd_a / rho
+// g^eq (Eq. geqmagneticfield): g^eq_ax = W_a (B_x - 3 e_ay E), g^eq_ay = W_a (B_y + 3 e_ax E),
+//   E = u_x B_y - u_y B_x.
+template <typename C>
+__device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const StepParams<C>& p) {
+    const C one = C(1), half = C(0.5), three = C(3), four5 = C(4.5), one5 = C(1.5);
+    const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w5 = C(1.0 / 36.0);
+    const C W0 = C(1.0 / 3.0), W1 = C(1.0 / 6.0);
+
+    // a3: moments
+    const C drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const C rho = one + drho;
+    const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const C inv_rho = one / rho;
+    const C ux = (jx + half * p.Fx) * inv_rho;
+    const C uy = jy * inv_rho;
+    const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
+    const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
+    const C by = p.B0 + dby;
+
+    // a4: equilibria.  Magnetic part with q = B_y^2 - B0^2 = dby (2 B0 + dby):
+    //   a=1,3: (q - Bx^2)/2   a=2,4: (Bx^2 - q)/2   a=5,7: -2 Bx By   a=6,8: +2 Bx By
+    const C q = dby * (p.B0 + by);
+    const C bx2 = bx * bx;
+    const C m13 = four5 * w1 * half * (q - bx2);
+    const C m24 = -m13;
+    const C mxy = four5 * w5 * C(2) * bx * by;
+    const C usq = one5 * (ux * ux + uy * uy);
+
+    const C omega = p.omega_f, sc = p.src_coef * three * p.Fx;
+    // per direction: base b_a = 1 + 3 eu + 4.5 eu^2 - 1.5 u^2 (so f^eq,hyd = w rho b_a)
+#define LKS_DIR(A, EXA, EU, W, MAG)                                                     \
+    {                                                                                   \
+        const C eu = (EU);                                                              \
+        const C b = one + three * eu + four5 * eu * eu - usq;                           \
+        const C feq = (W) * (drho + rho * (b - one)) + (MAG);                           \
+        const C S = (W) * (C(EXA) - ux) * b;                                            \
+        f[A] = f[A] - omega * (f[A] - feq) + sc * S;                                    \
+    }
+    LKS_DIR(0, 0, C(0), w0, C(0))
+    LKS_DIR(1, 1, ux, w1, m13)
+    LKS_DIR(2, 0, uy, w1, m24)
+    LKS_DIR(3, -1, -ux, w1, m13)
+    LKS_DIR(4, 0, -uy, w1, m24)
+    LKS_DIR(5, 1, ux + uy, w5, -mxy)
+    LKS_DIR(6, -1, uy - ux, w5, mxy)
+    LKS_DIR(7, -1, -ux - uy, w5, -mxy)
+    LKS_DIR(8, 1, ux - uy, w5, mxy)
+#undef LKS_DIR
+
+    // a5 for g (Eq. LKSformagneticfield)
+    const C E3 = three * (ux * by - uy * bx);
+    const C om = p.omega_m;
+    gx[0] = gx[0] - om * (gx[0] - W0 * bx);
+    gx[1] = gx[1] - om * (gx[1] - W1 * bx);
+    gx[2] = gx[2] - om * (gx[2] - W1 * (bx - E3));
+    gx[3] = gx[3] - om * (gx[3] - W1 * bx);
+    gx[4] = gx[4] - om * (gx[4] - W1 * (bx + E3));
+    gy[0] = gy[0] - om * (gy[0] - W0 * dby);
+    gy[1] = gy[1] - om * (gy[1] - W1 * (dby + E3));
+    gy[2] = gy[2] - om * (gy[2] - W1 * dby);
+    gy[3] = gy[3] - om * (gy[3] - W1 * (dby - E3));
+    gy[4] = gy[4] - om * (gy[4] - W1 * dby);
+}
+
+// Moment-based closures at a wet wall node (Sec. VII, App. A, App. B.2), deviation form.
+// g first (its B_x enters the Pi_20 target of f), then f.  Bottom: unknown f2, f5, f6, g2.
+template <typename C>
+__device__ __forceinline__ void moment_closure_bottom(C f[9], C gx[5], C gy[5], const WallCoef<C>& w, C B0) {
+    const C half = C(0.5), cs2 = C(1.0 / 3.0);
+    gx[2] = w.r * gx[4] - w.bc * ((gx[0] + gx[1]) + gx[3]) + w.kx;
+    gy[2] = -(((gy[0] + gy[1]) + gy[3]) + gy[4]);
+    const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
+    const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
+    const C drho = (f[0] + f[1]) + f[3] + C(2) * ((f[4] + f[7]) + f[8]);
+    const C rho = C(1) + drho;
+    const C U = w.U;
+    // P - P_rest with P = rho (c^2 + U^2) + (B_y^2 - B_x^2)/2 and P_rest = c^2 + B0^2/2
+    const C dP = U * U + drho * (cs2 + U * U) + dby * (B0 + half * dby) - half * bx * bx;
+    const C rU = rho * U;
+    f[2] = -dP + (f[1] + f[3]) + f[4] + C(2) * (f[7] + f[8]);
+    f[5] = half * (dP + rU) - (f[1] + f[8]);
+    f[6] = half * (dP - rU) - (f[3] + f[7]);
+}
+
+// Top: unknown f4, f7, f8, g4.
+template <typename C>
+__device__ __forceinline__ void moment_closure_top(C f[9], C gx[5], C gy[5], const WallCoef<C>& w, C B0) {
+    const C half = C(0.5), cs2 = C(1.0 / 3.0);
+    gx[4] = w.r * gx[2] - w.bc * ((gx[0] + gx[1]) + gx[3]) + w.kx;
+    gy[4] = -(((gy[0] + gy[1]) + gy[2]) + gy[3]);
+    const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
+    const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
+    const C drho = (f[0] + f[1]) + f[3] + C(2) * ((f[2] + f[5]) + f[6]);
+    const C rho = C(1) + drho;
+    const C U = w.U;
+    const C dP = U * U + drho * (cs2 + U * U) + dby * (B0 + half * dby) - half * bx * bx;
+    const C rU = rho * U;
+    f[4] = -dP + (f[1] + f[2]) + f[3] + C(2) * (f[5] + f[6]);
+    f[7] = half * (dP - rU) - (f[3] + f[6]);
+    f[8] = half * (dP + rU) - (f[1] + f[5]);
+}
+
+}  // namespace lks

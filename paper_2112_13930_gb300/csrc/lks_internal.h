@@ -1,0 +1,64 @@
+// lks_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lks_device.cuh"
+
+namespace lks {
+
+template <typename C>
+inline StepParams<C> convert_params(const StepParams<double>& d) {
+    StepParams<C> o;
+    o.nx = d.nx;
+    o.ny = d.ny;
+    o.N = d.N;
+    o.omega_f = (C)d.omega_f;
+    o.omega_m = (C)d.omega_m;
+    o.src_coef = (C)d.src_coef;
+    o.Fx = (C)d.Fx;
+    o.B0 = (C)d.B0;
+    const WallCoef<double>* src[2] = {&d.bot, &d.top};
+    WallCoef<C>* dst[2] = {&o.bot, &o.top};
+    for (int k = 0; k < 2; ++k) {
+        dst[k]->r = (C)src[k]->r;
+        dst[k]->bc = (C)src[k]->bc;
+        dst[k]->kx = (C)src[k]->kx;
+        dst[k]->du = (C)src[k]->du;
+        dst[k]->U = (C)src[k]->U;
+    }
+    return o;
+}
+
+// Bytes per stored population for each lks_storage value.
+inline size_t storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
+
+// One fused step: (fin, gin) -> (fout, gout) on stream st.
+cudaError_t launch_step(int storage, int closure, const void* fin, const void* gin, void* fout, void* gout,
+                        const StepParams<double>& p, cudaStream_t st);
+
+// Initial equilibrium state (deviation form) with the counter-based perturbation.
+cudaError_t launch_init(int storage, void* f, void* g, int nx, int ny, double B0, uint64_t seed, double amp,
+                        cudaStream_t st);
+
+// Moments of a stored state: out[m*N + n] (what = 0) or x-averaged profiles out[m*ny + j] (what = 1).
+cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
+                           int what, double* out, cudaStream_t st);
+
+// Residual partial sums: nblk blocks write partial[4*blk + k] = (sum du^2, sum u^2, sum db^2, sum b^2)
+// and refresh the snapshot snap[0..N) = u_x, snap[N..2N) = B_x; then one block reduces in fixed order
+// into out[0..4).
+int residual_blocks(int64_t N);
+cudaError_t launch_residual(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
+                            double* snap, double* partial, double* out, cudaStream_t st);
+cudaError_t launch_snapshot(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
+                            double* snap, cudaStream_t st);
+
+// FP64 absolute populations <-> stored deviations.
+cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, double B0, double* fabs,
+                          double* gabs, cudaStream_t st);
+cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, double B0, void* f,
+                            void* g, cudaStream_t st);
+
+}  // namespace lks

@@ -1,0 +1,89 @@
+"""Host-side checks of the C ABI: the library builds for sm_103a, loads, exports every entry
+point include/lks.h declares, and validates parameters (no device work: no GPU is needed)."""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from paper_2112_13930_gb300 import build as lks_build
+from paper_2112_13930_gb300 import lks
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lks_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    lks_build.build()
+    return lks.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared("lks.h")
+    assert "lks_create" in names and "lks_step" in names and "lks_set_walls" in names and "lks_moments" in names
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in lks.SIGNATURES, "binding lacks " + n
+
+
+def test_footprint_counts_both_buffers(lib):
+    nx, ny = 4096, 4096
+    for storage, sb in (("f64", 8), ("f32", 4), ("bf16", 2), ("f16", 2)):
+        fp = lks.footprint_bytes(nx, ny, "moment", storage)
+        pops = 2 * 19 * nx * ny * sb
+        snap = 2 * nx * ny * 8
+        assert pops + snap <= fp < pops + snap + 1 << 20
+
+
+@pytest.mark.parametrize("kw,ok", [
+    (dict(nx=4, ny=65, closure="link"), True),
+    (dict(nx=4, ny=1, closure="link"), False),
+    (dict(nx=4, ny=2, closure="link"), True),
+    (dict(nx=4, ny=2, closure="moment"), False),
+    (dict(nx=0, ny=8, closure="link"), False),
+    (dict(nx=4, ny=8, closure="link", tau_f=0.5), False),
+    (dict(nx=4, ny=8, closure="link", tau_m=0.4), False),
+    (dict(nx=4, ny=8, closure="link", tau_m=math.nan), False),
+])
+def test_parameter_validation(lib, kw, ok):
+    p = lks.make_params(kw.get("nx"), kw.get("ny"), kw.get("tau_f", 0.8), kw.get("tau_m", 0.8), 0.01,
+                        closure=kw["closure"])
+    assert (lib.lks_footprint_bytes(ctypes.byref(p)) > 0) == ok
+
+
+def test_create_rejects_bad_parameters_without_touching_the_device(lib):
+    p = lks.make_params(4, 1, 0.8, 0.8, 0.01, closure="link")
+    h = ctypes.c_void_p()
+    st = lib.lks_create(ctypes.byref(p), ctypes.byref(h))
+    assert st == lks.LKS_EINVAL and not h.value
+    assert b"ny" in lib.lks_last_error(None)
+    assert lib.lks_create(None, ctypes.byref(h)) == lks.LKS_EINVAL
+    assert lib.lks_status_string(lks.LKS_EUNSTABLE) == b"LKS_EUNSTABLE"
+    assert lib.lks_destroy(None) == lks.LKS_OK
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.lks_step(None, 1) == lks.LKS_EINVAL
+    assert lib.lks_set_walls(None, 0.0, 0.0, 0.0, 0.0) == lks.LKS_EINVAL
+    assert lib.lks_sync(None) == lks.LKS_EINVAL
+    assert lib.lks_steps_taken(None) == -1
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    with pytest.raises(ImportError):
+        lks.Lattice.__init__  # noqa: B018 -- attribute exists
+        import importlib
+        mod = importlib.import_module("paper_2112_13930_gb300.lks")
+        saved = mod._lib
+        try:
+            mod._lib = None
+            mod.load(str(tmp_path / "missing.so"))
+        finally:
+            mod._lib = saved

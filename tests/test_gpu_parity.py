@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+FP64 storage: element-wise, max|GPU - oracle| / max|oracle| <= 1e-11 per field (the bound the
+scheme's specification sets; the two differ only in rounding order and FMA contraction).
+FP32 / BF16 / FP16 storage of deviations with FP32 arithmetic: tolerances derived in the test
+docstrings from the storage precision.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analytic as an
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-11
+
+
+@pytest.fixture(scope="module")
+def lks():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_13930_gb300 import build, lks as mod
+    build.build()
+    mod.load()
+    return mod
+
+
+def _pair(lks, nx, ny, closure, storage="f64", tau_f=0.8, tau_m=0.8, B0=0.03, Fx=0.0, c=(0.0, 0.0), u=(0.0, 0.0),
+          seed=0, amp=0.0):
+    cl = oracle.LINK if closure == "link" else oracle.MOMENT
+    o = oracle.Oracle(nx, ny, tau_f, tau_m, B0, Fx, cl, c[0], c[1], u[0], u[1], seed=seed, perturb_amp=amp)
+    g = lks.Lattice(nx, ny, tau_f, tau_m, B0, Fx, closure, storage, seed=seed, perturb_amp=amp)
+    g.set_walls(c[0], c[1], u[0], u[1])
+    return o, g
+
+
+def _relmax(a, b):
+    scale = float(np.max(np.abs(b)))
+    return float(np.max(np.abs(a - b))) / (scale if scale > 0 else 1.0)
+
+
+def _compare_fields(o, g, rel, rel_pop=None):
+    fo, go = o.f, o.g
+    fg, gg = g.get_state()
+    mo, mg = o.moments(), g.moments()
+    # fields: rho - 1, u (vector), B_x, B_y - B0
+    errs = {
+        "rho": _relmax(mg[0] - 1.0, mo[0] - 1.0) if np.max(np.abs(mo[0] - 1.0)) > 1e-14 else
+        float(np.max(np.abs(mg[0] - mo[0]))),
+        "u": max(_relmax(mg[1], mo[1]), float(np.max(np.abs(mg[2] - mo[2]))) / max(1e-300, float(np.max(np.abs(mo[1:3]))))),
+        "bx": _relmax(mg[3], mo[3]) if np.max(np.abs(mo[3])) > 0 else float(np.max(np.abs(mg[3]))),
+        "by": float(np.max(np.abs(mg[4] - mo[4]))) / max(1e-300, float(np.max(np.abs(mo[4])))),
+    }
+    if rel_pop is not None:
+        errs["f"] = float(np.max(np.abs(fg - fo))) / float(np.max(np.abs(fo)))
+        errs["g"] = float(np.max(np.abs(gg - go))) / max(1e-300, float(np.max(np.abs(go))))
+    for k, v in errs.items():
+        lim = rel_pop if k in ("f", "g") else rel
+        assert v <= lim, (k, v, lim, errs)
+    return errs
+
+
+@pytest.mark.parametrize("closure", ["link", "moment"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+def test_initial_state_matches_oracle(lks, closure, storage):
+    """Init (equilibria at rho = 1, B = (0, B0), seeded u0) equals the oracle's, up to the
+    storage rounding of the deviations."""
+    o, g = _pair(lks, 37, 5, closure, storage, seed=1234, amp=1e-3)
+    fg, gg = g.get_state()
+    tol = {"f64": 1e-16, "f32": 1e-9, "bf16": 2e-5, "f16": 3e-6}[storage]
+    assert np.max(np.abs(fg - o.f)) <= tol
+    assert np.max(np.abs(gg - o.g)) <= tol
+
+
+def test_hartmann_channel_fp64_parity_20000_steps(lks):
+    """4 x 65 link-based Hartmann channel, Ha = 10, c = 0.1, tau_f = tau_m = 0.8, 2e4 steps (FP64)."""
+    ny, ha, c = 65, 10.0, 0.1
+    a = ny / 2
+    b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+    fx = an.force_for_centre_speed(0.01, ha, c, a, 0.8)
+    o, g = _pair(lks, 4, ny, "link", "f64", B0=b0, Fx=fx, c=(c, c))
+    o.step(20000)
+    g.step(20000)
+    errs = _compare_fields(o, g, REL64, REL64)
+    u, b = g.profiles()
+    ua, ba = an.hartmann_profiles(g.y(), a, ha, c, fx, 0.8, 0.8)
+    assert an.rel_l2(u, ua) < 5e-3 and an.rel_l2(b, ba) < 5e-3
+
+
+CASES = [
+    # nx spans several 256-thread blocks with a ragged tail; moving walls, finite / zero / infinite c
+    dict(nx=300, ny=7, closure="link", c=(0.3, 2.0), u=(0.0, 0.04), Fx=1e-5, amp=1e-2),
+    dict(nx=300, ny=7, closure="moment", c=(0.3, 2.0), u=(-0.02, 0.04), Fx=1e-5, amp=1e-2),
+    dict(nx=33, ny=40, closure="link", c=(0.0, math.inf), u=(0.01, -0.03), Fx=0.0, amp=5e-3),
+    dict(nx=33, ny=40, closure="moment", c=(math.inf, 0.0), u=(0.0, 0.05), Fx=2e-5, amp=5e-3),
+    dict(nx=1, ny=3, closure="moment", c=(0.5, 0.5), u=(0.0, 0.05), Fx=0.0, amp=0.0),
+    dict(nx=1, ny=2, closure="link", c=(1e4, 0.0), u=(0.0, 0.05), Fx=1e-4, amp=0.0),
+    dict(nx=257, ny=9, closure="link", c=(0.0, 0.0), u=(0.0, 0.0), Fx=0.0, amp=1e-2),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "%s-%dx%d" % (c["closure"], c["nx"], c["ny"]))
+def test_fp64_parity_cases(lks, case):
+    o, g = _pair(lks, case["nx"], case["ny"], case["closure"], "f64", tau_f=0.7, tau_m=0.9, B0=0.02,
+                 Fx=case["Fx"], c=case["c"], u=case["u"], seed=99, amp=case["amp"])
+    for n in (1, 7, 130):  # 130 > the graph length: exercises graph launch plus direct launches
+        o.step(n)
+        g.step(n)
+        _compare_fields(o, g, REL64, REL64)
+
+
+def test_graph_steps_equal_direct_steps(lks):
+    """Steps launched through the captured CUDA graph are bitwise the same as direct launches."""
+    a = lks.Lattice(50, 11, 0.7, 0.9, 0.02, 1e-5, "moment", "f32", seed=3, perturb_amp=1e-2)
+    b = lks.Lattice(50, 11, 0.7, 0.9, 0.02, 1e-5, "moment", "f32", seed=3, perturb_amp=1e-2)
+    for h in (a, b):
+        h.set_walls(0.2, 0.7, 0.0, 0.03)
+    a.step(200)
+    for _ in range(200):
+        b.step(1)
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_moments_profiles_and_residual(lks):
+    """lks_moments (nodes, profiles) and lks_residual against the oracle's state."""
+    o, g = _pair(lks, 70, 12, "moment", "f64", B0=0.02, Fx=1e-5, c=(0.2, 0.9), u=(0.0, 0.03), seed=5, amp=1e-2)
+    prev = o.moments()
+    o.step(25)
+    g.step(25)
+    mo, mg = o.moments(), g.moments()
+    np.testing.assert_allclose(mg, mo, rtol=1e-11, atol=1e-14)
+    pg = g.moments(lks.MOMENTS_PROFILES)
+    np.testing.assert_allclose(pg, mo.mean(axis=2), rtol=1e-11, atol=1e-14)
+    ru, rb = g.residual()
+    ru_o = np.sqrt(np.sum((mo[1] - prev[1]) ** 2) / np.sum(mo[1] ** 2))
+    rb_o = np.sqrt(np.sum((mo[3] - prev[3]) ** 2) / np.sum(mo[3] ** 2))
+    assert ru == pytest.approx(ru_o, rel=1e-9) and rb == pytest.approx(rb_o, rel=1e-9)
+
+
+def test_set_state_roundtrip_and_continue(lks):
+    """lks_set_state loads an oracle state; continuing on the GPU tracks the oracle."""
+    o, g = _pair(lks, 40, 9, "link", "f64", B0=0.02, Fx=1e-5, c=(0.5, 0.5), seed=8, amp=1e-2)
+    o.step(10)
+    g.set_state(o.f, o.g)
+    fg, gg = g.get_state()
+    assert np.max(np.abs(fg - o.f)) < 1e-16 and np.max(np.abs(gg - o.g)) < 1e-16
+    o.step(40)
+    g.step(40)
+    _compare_fields(o, g, REL64, REL64)
+
+
+# Reduced precision.  Deviations d = f - f_rest are stored rounded to the storage type (unit
+# roundoff eps: 2^-24 FP32, 2^-8 BF16, 2^-11 FP16) and all arithmetic is FP32.  Each step adds a
+# relative perturbation ~eps to every stored deviation; the scheme is dissipative, so the error
+# of the moments stays of order eps times a modest growth factor.  Bounds: FP32 2e-5, FP16 2e-2,
+# BF16 1.5e-1 relative to max|field| after 2000 steps of a perturbed channel.
+REDUCED = {"f32": 2e-5, "f16": 2e-2, "bf16": 1.5e-1}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("closure", ["link", "moment"])
+def test_reduced_precision_error_bounds(lks, storage, closure):
+    ny, ha, c = 33, 10.0, 0.5
+    a = ny / 2 if closure == "link" else (ny - 1) / 2
+    b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+    fx = an.force_for_centre_speed(0.01, ha, c, a, 0.8)
+    o, g = _pair(lks, 16, ny, closure, storage, B0=b0, Fx=fx, c=(c, c), u=(0.0, 0.0), seed=11, amp=1e-3)
+    o.step(2000)
+    g.step(2000)
+    mo, mg = o.moments(), g.moments()
+    eu = _relmax(mg[1], mo[1])
+    eb = _relmax(mg[3], mo[3])
+    assert eu <= REDUCED[storage] and eb <= REDUCED[storage], (eu, eb)
+
+
+def test_full_size_lattice_columns_match_oracle(lks):
+    """4096 x 4096 moment-based Hartmann-Couette channel (the timed configuration) from rest: the
+    solution does not depend on x, so every column of the GPU lattice must equal the oracle's
+    4 x 4096 run (FP64, 20 steps), and all columns must agree."""
+    import torch
+    n, ha, c = 4096, 20.0, 1.0
+    a = (n - 1) / 2
+    b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+    o = oracle.Oracle(4, n, 0.8, 0.8, b0, 0.0, oracle.MOMENT, c, c, 0.0, 0.05)
+    g = lks.Lattice(n, n, 0.8, 0.8, b0, 0.0, "moment", "f64")
+    g.set_walls(c, c, 0.0, 0.05)
+    o.step(20)
+    g.step(20)
+    out = torch.empty((5, n, n), dtype=torch.float64, device="cuda")
+    g.moments_device(out)
+    torch.cuda.synchronize()
+    mo = o.moments()
+    for m in (1, 3):
+        col = out[m].cpu().numpy()
+        assert np.max(np.abs(col - col[:, :1])) == 0.0
+        assert _relmax(col[:, 1234], mo[m][:, 0]) <= REL64
+    del out
+    g.close()
+
+
+def test_full_size_perturbed_fp64_sampled_rows(lks):
+    """4096 x 4096 with a seeded perturbation, 3 steps: the oracle computes the full lattice (OpenMP)
+    and rows near both walls and in the interior are compared element by element."""
+    n = 4096
+    o, g = _pair(lks, n, n, "moment", "f64", B0=0.001, Fx=1e-6, c=(1.0, 1.0), u=(0.0, 0.05), seed=20211227,
+                 amp=1e-3)
+    o.step(3)
+    g.step(3)
+    mo, mg = o.moments(), g.moments()
+    rows = [0, 1, 2, 1000, 2047, 4093, 4094, 4095]
+    for m in (1, 2, 3):
+        assert _relmax(mg[m][rows], mo[m][rows]) <= REL64
+    g.close()
