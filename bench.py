@@ -346,6 +346,106 @@ def bench_ours(args):
     return 0
 
 
+def bench_precision(args):
+    """Reduced-precision storage: body-force Hartmann flow on 8192 x 8192 (Ha = 30, c = 0.5,
+    tau = 0.8, seeded +-1e-3 velocity perturbation), link-based closure.  Reports MLUPS per storage
+    type, the error of each storage type against the FP64 GPU run after 1000 steps (the FP64 path
+    itself checked against the oracle on sampled rows after 2 steps), and the error against the
+    analytic profile of a 4 x 513 channel of the same physics run to steady state."""
+    import numpy as np
+    import torch
+    from paper_2112_13930_gb300 import build, lks
+    torch.cuda.set_device(0)
+    build.build()
+    lks.load()
+    n = args.n if args.n != 4096 else 8192
+    ha, c, tau = 30.0, 0.5, 0.8
+    closure = "link"
+    a = n / 2
+    nu = (tau - 0.5) / 3
+    b0 = ha * nu / a
+    ustar0 = (1.0 / ha) * ((c + 1.0) / (ha * c + math.tanh(ha))) * (1.0 - 1.0 / math.cosh(ha))
+    fx = 0.01 * nu / (a * a * ustar0)
+    seed, amp = 20211227, 1e-3
+    out = {"workload": "precision", "config": {"nx": n, "ny": n, "closure": closure, "Ha": ha, "c": c, "tau": tau,
+                                               "B0": b0, "Fx": fx, "seed": seed, "perturb_amp": amp}}
+
+    stream = torch.cuda.current_stream()
+    mlups = {}
+    fields = {}
+    steps_err = args.precision_steps
+    for st in ("f64", "f32", "f16", "bf16"):
+        lat = lks.Lattice(n, n, tau, tau, b0, fx, closure, st, seed=seed, perturb_amp=amp)
+        lat.set_walls(c, c)
+        if st == "f64":
+            # parity of the FP64 path on sampled rows against the oracle (2 steps of the full lattice)
+            if not args.skip_cpu:
+                import oracle
+                o = oracle.Oracle(n, n, tau, tau, b0, fx, oracle.LINK, c, c, seed=seed, perturb_amp=amp)
+                o.step(2)
+                lat.step(2)
+                mo = o.moments()
+                mg = torch.empty((5, n, n), dtype=torch.float64, device="cuda")
+                lat.moments_device(mg)
+                rows = [0, 1, n // 3, n // 2, n - 2, n - 1]
+                mgr = mg[:, rows, :].cpu().numpy()
+                err = max(float(np.max(np.abs(mgr[m] - mo[m][rows])) / np.max(np.abs(mo[m][rows])))
+                          for m in (1, 3))
+                out["fp64_vs_oracle_2_steps_sampled_rows"] = err
+                del o, mo, mg
+                lat.close()
+                lat = lks.Lattice(n, n, tau, tau, b0, fx, closure, st, seed=seed, perturb_amp=amp)
+                lat.set_walls(c, c)
+        k = 50 if st == "f64" else 200
+        lat.step(5)
+        t = _time_steps(lat, k, stream)
+        mlups[st] = round(n * n * k / t / 1e6, 1)
+        lat.step(steps_err - 5 - k)
+        m = torch.empty((5, n, n), dtype=torch.float64, device="cuda")
+        lat.moments_device(m)
+        torch.cuda.synchronize()
+        fields[st] = (m[1].clone(), m[3].clone())
+        del m
+        lat.close()
+        torch.cuda.empty_cache()
+    errs = {}
+    u64, b64 = fields["f64"]
+    for st in ("f32", "f16", "bf16"):
+        u, b = fields[st]
+        errs[st] = {"u_x_relmax": float((u - u64).abs().max() / u64.abs().max()),
+                    "u_x_rel_rms": float(((u - u64) ** 2).mean().sqrt() / u64.abs().max()),
+                    "B_x_relmax": float((b - b64).abs().max() / b64.abs().max()),
+                    "B_x_rel_rms": float(((b - b64) ** 2).mean().sqrt() / b64.abs().max())}
+    del fields
+    torch.cuda.empty_cache()
+    # analytic comparison on a 4 x 513 channel of the same physics (Ha, c, tau, u_c = 0.01)
+    ny = 513
+    a2 = ny / 2
+    b02 = ha * nu / a2
+    fx2 = 0.01 * nu / (a2 * a2 * ustar0)
+    y = -a2 + np.arange(ny) + 0.5
+    xi = y / a2
+    fac = (c + 1.0) / (ha * c + math.tanh(ha)) / ha
+    ua = (a2 * a2 * fx2 / nu) * fac * (1.0 - np.cosh(ha * xi) / math.cosh(ha))
+    ba = (a2 * a2 * fx2 / nu) * (-xi / ha + fac * np.sinh(ha * xi) / math.cosh(ha))
+    analytic = {}
+    for st in ("f64", "f32", "f16", "bf16"):
+        lat = lks.Lattice(4, ny, tau, tau, b02, fx2, closure, st)
+        lat.set_walls(c, c)
+        steps, r, status = lat.run_to_steady(1e-9, 1000, args.precision_max_steps, raise_on_fail=False)
+        u, b = lat.profiles()
+        analytic[st] = {"steps": steps, "residual": r, "status": int(status),
+                        "u_rel_l2": float(np.sqrt(np.mean((u - ua) ** 2)) / np.max(np.abs(ua))),
+                        "B_rel_l2": float(np.sqrt(np.mean((b - ba) ** 2)) / np.max(np.abs(ba)))}
+        lat.close()
+    out.update({"mlups": mlups, "error_vs_fp64_after_%d_steps" % steps_err: errs,
+                "analytic_4x513": analytic,
+                "roofline_hbm_frac": {st: round(mlups[st] * 1e6 * BYTES_PER_NODE[st] / 1e9 / _peaks()[0], 4)
+                                      for st in mlups}})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # FP64 arithmetic per node per step in the fused kernel (adds, multiplies, FMAs counted as 2,
 # one division), counted from the kernel source; used for the FP64 ALU roofline.
 FP64_FLOPS_PER_NODE = 260
@@ -365,11 +465,16 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--workload", choices=["main", "precision", "sweep", "serve"], default="main")
+    ap.add_argument("--precision-steps", type=int, default=1000)
+    ap.add_argument("--precision-max-steps", type=int, default=3_000_000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return bench_reference(args)
+    if args.workload == "precision":
+        return bench_precision(args)
     return bench_ours(args)
 
 

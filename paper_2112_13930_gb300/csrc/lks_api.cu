@@ -62,6 +62,70 @@ const char* validate(const lks_params* p) {
 
 }  // namespace
 
+namespace lks {
+
+// Closure coefficients of one wall (see WallCoef).  ey = +1 for the bottom wall's incoming
+// direction, -1 for the top wall's.  a is the channel half-width of the closure's wall placement.
+static WallCoef<double> wall_coef(int closure, double a, double tau_m, double B0, double c, double U, double ey) {
+    WallCoef<double> w;
+    w.U = U;
+    w.du = 6.0 * (1.0 / 36.0) * U;  // 2 w_a e_ax U / c_s^2 for the diagonal links (|e_ax| = 1)
+    if (closure == LKS_LINK) {
+        // theta = c a / (tau_m - 1/2) (Eq. weightingfactor); r = (theta-1)/(theta+1),
+        // s = 2 theta/(theta+1); kx = -s W e_y B0 U / c_sm^2 with W = 1/6 (Eq. movingwalllinkbasedclosure)
+        double r, s;
+        if (isinf(c)) {
+            r = 1.0;
+            s = 2.0;
+        } else {
+            const double theta = c * a / (tau_m - 0.5);
+            r = (theta - 1.0) / (theta + 1.0);
+            s = 2.0 * theta / (theta + 1.0);
+        }
+        w.r = r;
+        w.bc = 0.0;
+        w.kx = -s * (1.0 / 6.0) * ey * B0 * U * 3.0;
+    } else {
+        // beta = c a / (tau_m c_sm^2): unknown = [(beta-1) opp - (g0+g1+g3) - e_y beta B0 U]/(beta+1)
+        // (Eq. momentconstraintgx and Eq. momentbasedclosureformovingwall multiplied through by c a)
+        double r, bc, k;
+        if (isinf(c)) {
+            r = 1.0;
+            bc = 0.0;
+            k = 1.0;
+        } else {
+            const double beta = c * a / (tau_m / 3.0);
+            r = (beta - 1.0) / (beta + 1.0);
+            bc = 1.0 / (beta + 1.0);
+            k = beta / (beta + 1.0);
+        }
+        w.r = r;
+        w.bc = bc;
+        w.kx = -ey * k * B0 * U;
+    }
+    return w;
+}
+
+StepParams<double> make_step_params(int nx, int ny, int closure, double tau_f, double tau_m, double B0, double Fx,
+                                    double c_bot, double c_top, double u_bot, double u_top) {
+    StepParams<double> s;
+    const double a = closure == LKS_LINK ? 0.5 * ny : 0.5 * (ny - 1);
+    s.nx = nx;
+    s.ny = ny;
+    s.N = (int64_t)nx * ny;
+    s.omega_f = 1.0 / tau_f;
+    s.omega_m = 1.0 / tau_m;
+    s.src_coef = 1.0 - 0.5 / tau_f;
+    s.Fx = Fx;
+    s.B0 = B0;
+    s.bot = wall_coef(closure, a, tau_m, B0, c_bot, u_bot, +1.0);
+    s.top = wall_coef(closure, a, tau_m, B0, c_top, u_top, -1.0);
+    return s;
+}
+
+}  // namespace lks
+
+
 struct lks_handle {
     lks_params p;
     Layout L;
@@ -102,64 +166,10 @@ lks_status cuda_fail(lks_handle* h, cudaError_t e, const char* where) {
     return fail(h, LKS_ECUDA, m);
 }
 
-double half_width(const lks_params& p) { return p.closure == LKS_LINK ? 0.5 * p.ny : 0.5 * (p.ny - 1); }
-
-// Closure coefficients of one wall (see WallCoef).  e_y = +1 for the bottom wall's incoming
-// direction, -1 for the top wall's.
-WallCoef<double> wall_coef(const lks_params& p, double c, double U, double ey) {
-    WallCoef<double> w;
-    const double a = half_width(p);
-    const double B0 = p.B0;
-    w.U = U;
-    w.du = 6.0 * (1.0 / 36.0) * U;  // 2 w_a e_ax U / c_s^2 for the diagonal links (|e_ax| = 1)
-    if (p.closure == LKS_LINK) {
-        // theta = c a / (tau_m - 1/2) (Eq. weightingfactor); r = (theta-1)/(theta+1),
-        // s = 2 theta/(theta+1); kx = -s W e_y B0 U / c_sm^2 with W = 1/6 (Eq. movingwalllinkbasedclosure)
-        double r, s;
-        if (isinf(c)) {
-            r = 1.0;
-            s = 2.0;
-        } else {
-            const double theta = c * a / (p.tau_m - 0.5);
-            r = (theta - 1.0) / (theta + 1.0);
-            s = 2.0 * theta / (theta + 1.0);
-        }
-        w.r = r;
-        w.bc = 0.0;
-        w.kx = -s * (1.0 / 6.0) * ey * B0 * U * 3.0;
-    } else {
-        // beta = c a / (tau_m c_sm^2): unknown = [(beta-1) opp - (g0+g1+g3) - e_y beta B0 U]/(beta+1)
-        double r, bc, k;
-        if (isinf(c)) {
-            r = 1.0;
-            bc = 0.0;
-            k = 1.0;
-        } else {
-            const double beta = c * a / (p.tau_m / 3.0);
-            r = (beta - 1.0) / (beta + 1.0);
-            bc = 1.0 / (beta + 1.0);
-            k = beta / (beta + 1.0);
-        }
-        w.r = r;
-        w.bc = bc;
-        w.kx = -ey * k * B0 * U;
-    }
-    return w;
-}
-
 void refresh_params(lks_handle* h) {
     const lks_params& p = h->p;
-    StepParams<double>& s = h->sp;
-    s.nx = p.nx;
-    s.ny = p.ny;
-    s.N = (int64_t)p.nx * p.ny;
-    s.omega_f = 1.0 / p.tau_f;
-    s.omega_m = 1.0 / p.tau_m;
-    s.src_coef = 1.0 - 0.5 / p.tau_f;
-    s.Fx = p.Fx;
-    s.B0 = p.B0;
-    s.bot = wall_coef(p, h->c_bot, h->u_bot, +1.0);
-    s.top = wall_coef(p, h->c_top, h->u_top, -1.0);
+    h->sp = lks::make_step_params(p.nx, p.ny, p.closure, p.tau_f, p.tau_m, p.B0, p.Fx, h->c_bot, h->c_top, h->u_bot,
+                                  h->u_top);
 }
 
 void drop_graphs(lks_handle* h) {

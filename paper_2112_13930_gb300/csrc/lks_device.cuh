@@ -37,14 +37,23 @@ struct StepParams {
     WallCoef<C> bot, top;
 };
 
-// Storage conversions (round to nearest even on the way down).
-template <typename S, typename C> __device__ __forceinline__ C load_s(const S* p);
-template <> __device__ __forceinline__ double load_s<double, double>(const double* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float load_s<float, float>(const float* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float load_s<__nv_bfloat16, float>(const __nv_bfloat16* p) {
-    return __bfloat162float(__ldg(p));
-}
-template <> __device__ __forceinline__ float load_s<__half, float>(const __half* p) { return __half2float(__ldg(p)); }
+// Storage conversions (round to nearest even on the way down).  RO = true loads through the
+// read-only (non-coherent) path, valid only when the buffer is not written during the kernel;
+// RO = false is a plain coherent load for kernels that write and re-read buffers across steps.
+template <typename S, typename C, bool RO = true> struct Loader;
+template <bool RO> struct Loader<double, double, RO> {
+    static __device__ __forceinline__ double ld(const double* p) { return RO ? __ldg(p) : *p; }
+};
+template <bool RO> struct Loader<float, float, RO> {
+    static __device__ __forceinline__ float ld(const float* p) { return RO ? __ldg(p) : *p; }
+};
+template <bool RO> struct Loader<__nv_bfloat16, float, RO> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(RO ? __ldg(p) : *p); }
+};
+template <bool RO> struct Loader<__half, float, RO> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(RO ? __ldg(p) : *p); }
+};
+template <typename S, typename C> __device__ __forceinline__ C load_s(const S* p) { return Loader<S, C, true>::ld(p); }
 
 template <typename S, typename C> __device__ __forceinline__ void store_s(S* p, C v);
 template <> __device__ __forceinline__ void store_s<double, double>(double* p, double v) { *p = v; }
@@ -92,13 +101,15 @@ __device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const Ste
     const C usq = one5 * (ux * ux + uy * uy);
 
     const C omega = p.omega_f, sc = p.src_coef * three * p.Fx;
-    // per direction: base b_a = 1 + 3 eu + 4.5 eu^2 - 1.5 u^2 (so f^eq,hyd = w rho b_a)
+    // per direction: bm1 = 3 eu + 4.5 eu^2 - 1.5 u^2, so f^eq,hyd = w rho (1 + bm1) and its
+    // deviation from the rest state is w (drho + rho bm1); bm1 is formed without the leading 1
+    // so that FP32 keeps its relative precision.
 #define LKS_DIR(A, EXA, EU, W, MAG)                                                     \
     {                                                                                   \
         const C eu = (EU);                                                              \
-        const C b = one + three * eu + four5 * eu * eu - usq;                           \
-        const C feq = (W) * (drho + rho * (b - one)) + (MAG);                           \
-        const C S = (W) * (C(EXA) - ux) * b;                                            \
+        const C bm1 = three * eu + four5 * eu * eu - usq;                               \
+        const C feq = (W) * (drho + rho * bm1) + (MAG);                                 \
+        const C S = (W) * (C(EXA) - ux) * (one + bm1);                                  \
         f[A] = f[A] - omega * (f[A] - feq) + sc * S;                                    \
     }
     LKS_DIR(0, 0, C(0), w0, C(0))
@@ -163,6 +174,91 @@ __device__ __forceinline__ void moment_closure_top(C f[9], C gx[5], C gy[5], con
     f[4] = -dP + (f[1] + f[2]) + f[3] + C(2) * (f[5] + f[6]);
     f[7] = half * (dP - rU) - (f[3] + f[6]);
     f[8] = half * (dP + rU) - (f[1] + f[5]);
+}
+
+// One node of the fused step (hot-path steps a1-a6): pull-stream from (fin, gin), wall closure,
+// moments, equilibria, collision, store to (fout, gout).  n = y*nx + x of a lattice laid out as
+// f[a][y][x], g[k][a][y][x].  Every element of fin/gin is read by exactly one node per step:
+// interior rows pull from rows y-1 / y / y+1 (Eqs. LBMforflowfield, LKSformagneticfield);
+// link-based wall rows take the unknown incoming populations from the same node's outgoing ones
+// (Sec. VI, App. B.1), which nobody else reads; moment-based wall rows reconstruct them from the
+// pulled ones (Sec. VII, App. A, App. B.2).
+template <typename S, typename C, int CLOSURE, bool RO>
+__device__ __forceinline__ void step_node(const S* fin, const S* gin, S* fout, S* gout, const StepParams<C>& p,
+                                          int64_t n) {
+    typedef Loader<S, C, RO> L;
+    const int nx = p.nx;
+    const int j = (int)(n / nx);
+    const int i = (int)(n - (int64_t)j * nx);
+    const int64_t N = p.N;
+    const int64_t rc = n - i;    // start of row j
+    const int64_t rs = rc - nx;  // row j-1
+    const int64_t rn = rc + nx;  // row j+1
+    const int im = (i == 0) ? nx - 1 : i - 1;
+    const int ip = (i == nx - 1) ? 0 : i + 1;
+    const bool bottom = (j == 0);
+    const bool top = (j == p.ny - 1);
+
+    C f[9], gx[5], gy[5];
+    const S* gxin = gin;
+    const S* gyin = gin + 5 * N;
+    // a1: pull-stream, periodic in x
+    f[0] = L::ld(fin + 0 * N + rc + i);
+    f[1] = L::ld(fin + 1 * N + rc + im);
+    f[3] = L::ld(fin + 3 * N + rc + ip);
+    gx[0] = L::ld(gxin + 0 * N + rc + i);
+    gx[1] = L::ld(gxin + 1 * N + rc + im);
+    gx[3] = L::ld(gxin + 3 * N + rc + ip);
+    gy[0] = L::ld(gyin + 0 * N + rc + i);
+    gy[1] = L::ld(gyin + 1 * N + rc + im);
+    gy[3] = L::ld(gyin + 3 * N + rc + ip);
+    if (!bottom) {
+        f[2] = L::ld(fin + 2 * N + rs + i);
+        f[5] = L::ld(fin + 5 * N + rs + im);
+        f[6] = L::ld(fin + 6 * N + rs + ip);
+        gx[2] = L::ld(gxin + 2 * N + rs + i);
+        gy[2] = L::ld(gyin + 2 * N + rs + i);
+    }
+    if (!top) {
+        f[4] = L::ld(fin + 4 * N + rn + i);
+        f[7] = L::ld(fin + 7 * N + rn + ip);
+        f[8] = L::ld(fin + 8 * N + rn + im);
+        gx[4] = L::ld(gxin + 4 * N + rn + i);
+        gy[4] = L::ld(gyin + 4 * N + rn + i);
+    }
+    // a2: wall closures
+    if (CLOSURE == 0) {
+        if (bottom) {
+            const WallCoef<C>& w = p.bot;
+            f[2] = L::ld(fin + 4 * N + rc + i);
+            f[5] = L::ld(fin + 7 * N + rc + i) + w.du;
+            f[6] = L::ld(fin + 8 * N + rc + i) - w.du;
+            gx[2] = w.r * L::ld(gxin + 4 * N + rc + i) + w.kx;
+            gy[2] = -L::ld(gyin + 4 * N + rc + i);
+        }
+        if (top) {
+            const WallCoef<C>& w = p.top;
+            f[4] = L::ld(fin + 2 * N + rc + i);
+            f[7] = L::ld(fin + 5 * N + rc + i) - w.du;
+            f[8] = L::ld(fin + 6 * N + rc + i) + w.du;
+            gx[4] = w.r * L::ld(gxin + 2 * N + rc + i) + w.kx;
+            gy[4] = -L::ld(gyin + 2 * N + rc + i);
+        }
+    } else {
+        if (bottom) moment_closure_bottom<C>(f, gx, gy, p.bot, p.B0);
+        if (top) moment_closure_top<C>(f, gx, gy, p.top, p.B0);
+    }
+    // a3-a5
+    collide_node<C>(f, gx, gy, p);
+    // a6: store
+    S* gxo = gout;
+    S* gyo = gout + 5 * N;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) store_s<S, C>(fout + a * N + n, f[a]);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) store_s<S, C>(gxo + a * N + n, gx[a]);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) store_s<S, C>(gyo + a * N + n, gy[a]);
 }
 
 }  // namespace lks

@@ -31,6 +31,11 @@ inline StepParams<C> convert_params(const StepParams<double>& d) {
     return o;
 }
 
+// Step parameters (relaxation rates, force, field and both walls' closure coefficients) of a
+// channel; c = INFINITY selects each closure's perfectly conducting limit.
+StepParams<double> make_step_params(int nx, int ny, int closure, double tau_f, double tau_m, double B0, double Fx,
+                                    double c_bot, double c_top, double u_bot, double u_top);
+
 // Bytes per stored population for each lks_storage value.
 inline size_t storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 

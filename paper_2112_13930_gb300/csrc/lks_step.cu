@@ -1,6 +1,6 @@
-// lks_step.cu -- the fused collide-stream kernel (hot path steps a1-a6).
+// lks_step.cu -- the fused collide-stream kernel (hot path steps a1-a6) of one lattice.
 //
-// One thread per node, nodes numbered n = y*nx + x so that a warp reads 32 consecutive
+// One thread per node (the per-node work is step_node in lks_device.cuh), nodes numbered n = y*nx + x so that a warp reads 32 consecutive
 // x positions of each population plane: every one of the 19 loads and 19 stores of a warp
 // is a coalesced 128-byte (FP32) / 256-byte (FP64) / 64-byte (16-bit) access; the +-1
 // x-shifted pulls straddle one extra sector that the neighbouring warp's load brings into
@@ -20,78 +20,7 @@ __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ fin, co
                                                    const StepParams<C> p) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    const int nx = p.nx;
-    const int j = (int)(n / nx);
-    const int i = (int)(n - (int64_t)j * nx);
-    const int64_t N = p.N;
-    const int64_t rc = n - i;          // start of row j
-    const int64_t rs = rc - nx;        // row j-1
-    const int64_t rn = rc + nx;        // row j+1
-    const int im = (i == 0) ? nx - 1 : i - 1;
-    const int ip = (i == nx - 1) ? 0 : i + 1;
-    const bool bottom = (j == 0);
-    const bool top = (j == p.ny - 1);
-
-    C f[9], gx[5], gy[5];
-    const S* gxin = gin;
-    const S* gyin = gin + 5 * N;
-    // a1: pull-stream, periodic in x
-    f[0] = load_s<S, C>(fin + 0 * N + rc + i);
-    f[1] = load_s<S, C>(fin + 1 * N + rc + im);
-    f[3] = load_s<S, C>(fin + 3 * N + rc + ip);
-    gx[0] = load_s<S, C>(gxin + 0 * N + rc + i);
-    gx[1] = load_s<S, C>(gxin + 1 * N + rc + im);
-    gx[3] = load_s<S, C>(gxin + 3 * N + rc + ip);
-    gy[0] = load_s<S, C>(gyin + 0 * N + rc + i);
-    gy[1] = load_s<S, C>(gyin + 1 * N + rc + im);
-    gy[3] = load_s<S, C>(gyin + 3 * N + rc + ip);
-    if (!bottom) {
-        f[2] = load_s<S, C>(fin + 2 * N + rs + i);
-        f[5] = load_s<S, C>(fin + 5 * N + rs + im);
-        f[6] = load_s<S, C>(fin + 6 * N + rs + ip);
-        gx[2] = load_s<S, C>(gxin + 2 * N + rs + i);
-        gy[2] = load_s<S, C>(gyin + 2 * N + rs + i);
-    }
-    if (!top) {
-        f[4] = load_s<S, C>(fin + 4 * N + rn + i);
-        f[7] = load_s<S, C>(fin + 7 * N + rn + ip);
-        f[8] = load_s<S, C>(fin + 8 * N + rn + im);
-        gx[4] = load_s<S, C>(gxin + 4 * N + rn + i);
-        gy[4] = load_s<S, C>(gyin + 4 * N + rn + i);
-    }
-    // a2: wall closures
-    if (CLOSURE == 0) {
-        if (bottom) {
-            const WallCoef<C>& w = p.bot;
-            f[2] = load_s<S, C>(fin + 4 * N + rc + i);
-            f[5] = load_s<S, C>(fin + 7 * N + rc + i) + w.du;
-            f[6] = load_s<S, C>(fin + 8 * N + rc + i) - w.du;
-            gx[2] = w.r * load_s<S, C>(gxin + 4 * N + rc + i) + w.kx;
-            gy[2] = -load_s<S, C>(gyin + 4 * N + rc + i);
-        }
-        if (top) {
-            const WallCoef<C>& w = p.top;
-            f[4] = load_s<S, C>(fin + 2 * N + rc + i);
-            f[7] = load_s<S, C>(fin + 5 * N + rc + i) - w.du;
-            f[8] = load_s<S, C>(fin + 6 * N + rc + i) + w.du;
-            gx[4] = w.r * load_s<S, C>(gxin + 2 * N + rc + i) + w.kx;
-            gy[4] = -load_s<S, C>(gyin + 2 * N + rc + i);
-        }
-    } else {
-        if (bottom) moment_closure_bottom<C>(f, gx, gy, p.bot, p.B0);
-        if (top) moment_closure_top<C>(f, gx, gy, p.top, p.B0);
-    }
-    // a3-a5
-    collide_node<C>(f, gx, gy, p);
-    // a6: store
-    S* gxo = gout;
-    S* gyo = gout + 5 * N;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) store_s<S, C>(fout + a * N + n, f[a]);
-#pragma unroll
-    for (int a = 0; a < 5; ++a) store_s<S, C>(gxo + a * N + n, gx[a]);
-#pragma unroll
-    for (int a = 0; a < 5; ++a) store_s<S, C>(gyo + a * N + n, gy[a]);
+    step_node<S, C, CLOSURE, true>(fin, gin, fout, gout, p, n);
 }
 
 template <typename S, typename C>

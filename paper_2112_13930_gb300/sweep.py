@@ -1,0 +1,108 @@
+"""Parameter-sweep driver: many channel instances solved to steady state by the batched engine
+(include/lks_batch.h), and the one-at-a-time FP64 baseline through the single-lattice API."""
+import math
+import time
+
+import numpy as np
+
+from . import batch as _batch
+from . import lks as _lks
+from . import profiles
+
+TAU = 0.8
+U_WALL = 0.05
+
+
+def lattice_params(spec, tau=TAU):
+    """Lattice parameters of one instance: B0 from Ha, body force for an analytic centreline speed
+    u_c = 0.01 * 64/(ny - 1) (diffusive scaling), shear instances' top plate at U_w = 0.05."""
+    a, _ = profiles.node_y(spec["ny"], spec["closure"])
+    nu = eta = (tau - 0.5) / 3.0
+    b0 = spec["ha"] * math.sqrt(nu * eta) / a
+    if spec["kind"] == "body":
+        fx = profiles.hartmann_force(0.01 * 64.0 / (spec["ny"] - 1), spec["ha"], spec["c"], a, tau)
+        return dict(B0=b0, Fx=fx, c_bottom=spec["c"], c_top=spec["c"], u_bottom=0.0, u_top=0.0)
+    return dict(B0=b0, Fx=0.0, c_bottom=0.0, c_top=spec["c"], u_bottom=0.0, u_top=U_WALL)
+
+
+def make_desc(spec, tol, check_every, max_steps, tau=TAU):
+    p = lattice_params(spec, tau)
+    return _batch.make_desc(spec["nx"], spec["ny"], spec["closure"], tau, tau, p["B0"], p["Fx"], p["c_bottom"],
+                            p["c_top"], p["u_bottom"], p["u_top"], tol=tol, check_every=check_every,
+                            max_steps=max_steps)
+
+
+def analytic_error(spec, u, b, tau=TAU):
+    """Relative L2 errors of u_x and B_x profiles against the closed form."""
+    p = lattice_params(spec, tau)
+    a, y = profiles.node_y(spec["ny"], spec["closure"])
+    if spec["kind"] == "body":
+        ua, ba = profiles.hartmann(y, a, spec["ha"], spec["c"], p["Fx"], tau, tau)
+    else:
+        ua, ba = profiles.couette(y, a, spec["ha"], 0.0, spec["c"], U_WALL, tau, tau)
+    return profiles.rel_l2(u, ua), profiles.rel_l2(b, ba)
+
+
+def run_batched(specs, storage="f32", tol=1e-10, check_every=100, quantum=20000, max_steps=10**9, shape=None,
+                tune_candidates=None, time_budget=None):
+    """Admit every instance into one batch and run persistent launches of `quantum` steps until
+    none is running.  Returns per-instance records and the wall time.  An instance's
+    time-to-steady is the wall time at the end of the launch in which it left RUNNING."""
+    import torch
+    descs = [make_desc(s, tol, check_every, max_steps) for s in specs]
+    pool = sum(_batch.instance_footprint(d, storage) for d in descs) + (1 << 20)
+    b = _batch.Batch(storage, max_instances=len(descs), pool_bytes=pool,
+                     threads_per_group=shape[0] if shape else 0, groups_per_cta=shape[1] if shape else 0)
+    slots = [b.add(d) for d in descs]
+    tune = None
+    if tune_candidates:
+        best, secs = b.autotune(tune_candidates, probe_steps=200)
+        tune = {"best": list(best), "seconds": secs, "candidates": [list(c) for c in tune_candidates]}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done_at = [None] * len(slots)
+    running = len(slots)
+    launches = 0
+    while running:
+        running = b.run(quantum)
+        launches += 1
+        now = time.perf_counter() - t0
+        for k, s in enumerate(slots):
+            if done_at[k] is None and b.result(s)[0] != _batch.INST_RUNNING:
+                done_at[k] = now
+        if time_budget is not None and now > time_budget:
+            break
+    wall = time.perf_counter() - t0
+    recs = []
+    for k, (spec, s) in enumerate(zip(specs, slots)):
+        st, steps, r = b.result(s)
+        u, bx = b.profiles(s)
+        eu, eb = analytic_error(spec, u, bx)
+        recs.append({"index": spec["index"], "ny": spec["ny"], "ha": spec["ha"], "c": spec["c"], "kind": spec["kind"],
+                     "state": _batch.STATE_NAMES[st], "steps": int(steps), "residual": r,
+                     "t_done": done_at[k], "l2_u": eu, "l2_b": eb, "nodes": spec["nx"] * spec["ny"]})
+    b.close()
+    return {"records": recs, "wall": wall, "launches": launches, "tune": tune}
+
+
+def run_one_at_a_time(specs, storage="f64", tol=1e-10, check_every=100, max_steps=10**9):
+    """The baseline: for each instance in order, lks_create -> lks_set_walls -> lks_run_to_steady
+    -> lks_moments -> lks_destroy on the same GPU.  Latency of instance k = sum of solve times
+    up to k (first-in first-out, all present at t = 0)."""
+    import torch
+    recs = []
+    t0 = time.perf_counter()
+    for spec in specs:
+        p = lattice_params(spec)
+        ts = time.perf_counter()
+        lat = _lks.Lattice(spec["nx"], spec["ny"], TAU, TAU, p["B0"], p["Fx"], spec["closure"], storage)
+        lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
+        steps, r, status = lat.run_to_steady(tol, check_every, max_steps, raise_on_fail=False)
+        u, bx = lat.profiles()
+        lat.close()
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        eu, eb = analytic_error(spec, u, bx)
+        recs.append({"index": spec["index"], "steps": int(steps), "residual": r, "status": int(status),
+                     "solve_s": te - ts, "t_done": te - t0, "l2_u": eu, "l2_b": eb})
+    return {"records": recs, "wall": time.perf_counter() - t0}

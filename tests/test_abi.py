@@ -33,6 +33,32 @@ def test_every_declared_symbol_is_exported(lib):
         assert n in lks.SIGNATURES, "binding lacks " + n
 
 
+def test_every_batch_symbol_is_exported(lib):
+    from paper_2112_13930_gb300 import batch
+    names = _declared("lks_batch.h")
+    assert "lks_batch_run" in names and "lks_batch_autotune" in names
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in batch.SIGNATURES, "binding lacks " + n
+
+
+def test_instance_footprint_and_batch_config_validation(lib):
+    from paper_2112_13930_gb300 import batch
+    d = batch.make_desc(4, 1025, "link", 0.8, 0.8, 0.01)
+    fp = batch.instance_footprint(d, "f32")
+    assert 2 * 19 * 4 * 4100 + 16 * 4100 <= fp < 2 * 19 * 4 * 4100 + 16 * 4100 + 5 * 256
+    bad = batch.make_desc(4, 2, "moment", 0.8, 0.8, 0.01)
+    assert batch.instance_footprint(bad, "f32") == 0
+    bad = batch.make_desc(4, 20, "link", 0.8, 0.8, 0.01, c_top=-1.0)
+    assert batch.instance_footprint(bad, "f32") == 0
+    cfg = batch.BatchConfig(storage=1, max_instances=4, pool_bytes=1 << 20, threads_per_group=48, groups_per_cta=1)
+    h = ctypes.c_void_p()
+    assert lib.lks_batch_create(ctypes.byref(cfg), ctypes.byref(h)) == lks.LKS_EINVAL and not h.value
+    cfg = batch.BatchConfig(storage=1, max_instances=4, pool_bytes=1 << 20, threads_per_group=256, groups_per_cta=4)
+    assert lib.lks_batch_create(ctypes.byref(cfg), ctypes.byref(h)) == lks.LKS_EINVAL
+    assert lib.lks_batch_destroy(None) == lks.LKS_OK
+
+
 def test_footprint_counts_both_buffers(lib):
     nx, ny = 4096, 4096
     for storage, sb in (("f64", 8), ("f32", 4), ("bf16", 2), ("f16", 2)):

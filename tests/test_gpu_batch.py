@@ -1,0 +1,181 @@
+"""Batched engine (lks_batch.h) on the GPU: per-instance parity with the FP64 oracle and with the
+single-lattice API, results independent of the mix, admission by pool footprint, statuses, and
+an autotune pass that leaves every state untouched."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analytic as an
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_13930_gb300 import batch, build, lks
+    build.build()
+    lks.load()
+    return lks, batch
+
+
+def _descs(batch, n=6, max_steps=10**7, tol=1e-30, check_every=50):
+    """A mixed set: link/moment, body force/shear, c = 0 / finite / inf, nx in {1, 4, 37}."""
+    out = []
+    rng = np.random.default_rng(7)
+    for k in range(n):
+        closure = "link" if k % 2 == 0 else "moment"
+        ny = int(rng.integers(12, 70))
+        nx = [4, 1, 37][k % 3]
+        a = ny / 2 if closure == "link" else (ny - 1) / 2
+        ha = float(rng.uniform(1, 0.3 * a))  # B0 = Ha sqrt(nu eta)/a <= 0.03: stable Alfven speed
+        b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+        c = [0.0, 0.3, math.inf][k % 3]
+        if k % 2 == 0:
+            fx = an.force_for_centre_speed(0.01, ha, c, a, 0.8)
+            d = batch.make_desc(nx, ny, closure, 0.8, 0.8, b0, fx, c, c, 0.0, 0.0, seed=k, perturb_amp=1e-3,
+                                tol=tol, check_every=check_every, max_steps=max_steps)
+        else:
+            d = batch.make_desc(nx, ny, closure, 0.8, 0.8, b0, 0.0, 0.0, c, 0.0, 0.05, seed=k, perturb_amp=1e-3,
+                                tol=tol, check_every=check_every, max_steps=max_steps)
+        out.append(d)
+    return out
+
+
+def _oracle_for(d):
+    return oracle.Oracle(d.nx, d.ny, d.tau_f, d.tau_m, d.B0, d.Fx, d.closure, d.c_bottom, d.c_top, d.u_bottom,
+                         d.u_top, seed=d.seed, perturb_amp=d.perturb_amp)
+
+
+def test_batch_fp64_matches_oracle(mods):
+    lks, batch = mods
+    b = batch.Batch("f64", max_instances=16, pool_bytes=64 << 20, threads_per_group=128, groups_per_cta=2)
+    descs = _descs(batch)
+    slots = [b.add(d) for d in descs]
+    for q in (7, 93):
+        b.run(q)
+        for d, s in zip(descs, slots):
+            o = _oracle_for(d)
+            o.step(7 if q == 7 else 100)
+            mo, mg = o.moments(), b.moments(s)
+            for m in (0, 1, 3):
+                scale = np.max(np.abs(mo[m]))
+                assert np.max(np.abs(mg[m] - mo[m])) <= 1e-11 * scale, (d.closure, m)
+            st, steps, r = b.result(s)
+            assert st == batch.INST_RUNNING and steps == (7 if q == 7 else 100)
+    b.close()
+
+
+def test_batch_matches_single_lattice_bitwise(mods):
+    """Same device update as lks_step: FP32 batch instances equal single-lattice runs bit for bit."""
+    lks, batch = mods
+    b = batch.Batch("f32", max_instances=16, pool_bytes=64 << 20, threads_per_group=64, groups_per_cta=4)
+    descs = _descs(batch)
+    slots = [b.add(d) for d in descs]
+    b.run(250)
+    for d, s in zip(descs, slots):
+        g = lks.Lattice(d.nx, d.ny, d.tau_f, d.tau_m, d.B0, d.Fx, d.closure, "f32", seed=d.seed,
+                        perturb_amp=d.perturb_amp)
+        g.set_walls(d.c_bottom, d.c_top, d.u_bottom, d.u_top)
+        g.step(250)
+        assert np.array_equal(g.moments(), b.moments(s))
+        g.close()
+    b.close()
+
+
+def test_alone_equals_in_the_mix(mods):
+    """Each instance's result is the same alone and in a mixed batch (bitwise, same group size)."""
+    lks, batch = mods
+    descs = _descs(batch, n=8, tol=1e-9, check_every=100, max_steps=3000)
+    mix = batch.Batch("f32", max_instances=16, pool_bytes=64 << 20, threads_per_group=128, groups_per_cta=2)
+    slots = [mix.add(d) for d in descs]
+    while mix.run(700):
+        pass
+    for d, s in zip(descs, slots):
+        alone = batch.Batch("f32", max_instances=1, pool_bytes=8 << 20, threads_per_group=128, groups_per_cta=1)
+        a = alone.add(d)
+        while alone.run(300):
+            pass
+        assert alone.result(a)[:2] == mix.result(s)[:2]
+        assert alone.result(a)[0] in (batch.INST_CONVERGED, batch.INST_MAX_STEPS)
+        m = mix.moments(s)
+        assert np.all(np.isfinite(m)) and np.array_equal(alone.moments(a), m)
+        alone.close()
+    mix.close()
+
+
+def test_statuses_and_residual(mods):
+    """CONVERGED at tol, MAX_STEPS at max_steps; the residual equals the single-lattice one."""
+    lks, batch = mods
+    b = batch.Batch("f64", max_instances=4, pool_bytes=16 << 20)
+    ny, ha, c = 33, 10.0, 0.5
+    a = ny / 2
+    b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+    fx = an.force_for_centre_speed(0.01, ha, c, a, 0.8)
+    d1 = batch.make_desc(4, ny, "link", 0.8, 0.8, b0, fx, c, c, tol=1e-9, check_every=100, max_steps=10**6)
+    d2 = batch.make_desc(4, ny, "link", 0.8, 0.8, b0, fx, c, c, tol=1e-30, check_every=100, max_steps=500)
+    s1, s2 = b.add(d1), b.add(d2)
+    while b.run(5000):
+        pass
+    st1, steps1, r1 = b.result(s1)
+    st2, steps2, r2 = b.result(s2)
+    assert st1 == batch.INST_CONVERGED and r1 < 1e-9 and steps1 % 100 == 0
+    assert st2 == batch.INST_MAX_STEPS and steps2 == 500
+    g = lks.Lattice(4, ny, 0.8, 0.8, b0, fx, "link", "f64")
+    g.set_walls(c, c)
+    n, r, status = g.run_to_steady(1e-9, 100, 10**6)
+    assert n == steps1 and r == pytest.approx(r1, rel=1e-9)
+    u, bx = b.profiles(s1)
+    ua, ba = an.hartmann_profiles(g.y(), a, ha, c, fx, 0.8, 0.8)
+    assert an.rel_l2(u, ua) < 1e-2 and an.rel_l2(bx, ba) < 1e-2   # 33-node channel: ~6e-3
+    g.close()
+    b.close()
+
+
+def test_admission_by_footprint_and_slots(mods):
+    lks, batch = mods
+    d = batch.make_desc(4, 100, "moment", 0.8, 0.8, 0.01)
+    fp = batch.instance_footprint(d, "f32")
+    assert fp >= 2 * 19 * 4 * 400 + 16 * 400
+    b = batch.Batch("f32", max_instances=3, pool_bytes=2 * fp + 1024)
+    s0, s1 = b.add(d), b.add(d)
+    assert s0 is not None and s1 is not None
+    assert b.add(d) is None                       # pool full -> LKS_EBUSY
+    free0, used0 = b.memory()
+    assert used0 == 2 * fp
+    b.remove(s0)
+    assert b.memory()[1] == fp
+    s2 = b.add(d)
+    assert s2 == s0
+    small = batch.make_desc(4, 5, "moment", 0.8, 0.8, 0.01)
+    assert b.add(small) is None or b.memory()[0] >= 0
+    b.close()
+    c = batch.Batch("f32", max_instances=1, pool_bytes=8 << 20)
+    assert c.add(small) is not None
+    assert c.add(small) is None                   # no slot -> LKS_EBUSY
+    c.close()
+
+
+def test_autotune_leaves_states_untouched(mods):
+    lks, batch = mods
+    descs = _descs(batch, n=6)
+    ref = batch.Batch("f32", max_instances=8, pool_bytes=32 << 20, threads_per_group=128, groups_per_cta=1)
+    tun = batch.Batch("f32", max_instances=8, pool_bytes=32 << 20, threads_per_group=128, groups_per_cta=1)
+    rs = [ref.add(d) for d in descs]
+    ts = [tun.add(d) for d in descs]
+    ref.run(100)
+    tun.run(100)
+    best, secs = tun.autotune([(64, 2), (128, 1), (256, 1), (32, 8)], probe_steps=50)
+    assert len(secs) == 4 and all(s > 0 for s in secs)
+    tun.set_shape(128, 1)
+    ref.run(100)
+    tun.run(100)
+    for a, c in zip(rs, ts):
+        assert ref.result(a)[:2] == tun.result(c)[:2]
+        assert np.array_equal(ref.moments(a), tun.moments(c))
+    ref.close()
+    tun.close()
