@@ -446,6 +446,92 @@ def bench_precision(args):
     return 0
 
 
+def bench_sweep(args):
+    """Batched sweep: a seeded sample of the 4096-instance parameter-sweep set (nx = 4, ny in
+    33..1025, Ha log-uniform in [1, 200], c log-uniform in [1e-3, 1e3] plus 5% each of 0 and inf,
+    half body-force/link-based, half shear/moment-based), FP32, residual tolerance 1e-10, solved by
+    persistent launches of the batched engine; the one-at-a-time FP64 baseline solves the first
+    instances of the same sample through the single-lattice API."""
+    import numpy as np
+    import torch
+    from paper_2112_13930_gb300 import build, lks, sweep, workloads
+    torch.cuda.set_device(0)
+    build.build()
+    lks.load()
+    specs = workloads.sweep_instances(4096, seed=4096)
+    sample = specs[: args.sweep_sample]
+    cands = [(64, 8), (128, 4), (256, 2), (512, 1), (128, 2), (256, 1)]
+    res = sweep.run_batched(sample, "f32", tol=1e-10, check_every=100, quantum=args.sweep_quantum,
+                            max_steps=args.sweep_max_steps, tune_candidates=cands, time_budget=args.sweep_time)
+    recs = res["records"]
+    done = [r for r in recs if r["t_done"] is not None]
+    t_done = np.array([r["t_done"] for r in done]) if done else np.array([np.nan])
+    node_updates = sum(r["nodes"] * r["steps"] for r in recs)
+    states = {}
+    for r in recs:
+        states[r["state"]] = states.get(r["state"], 0) + 1
+    resolved = [r for r in recs if r["state"] in ("converged", "stalled") and r["ny"] / 2 / r["ha"] >= 3.0]
+    gate = [max(r["l2_u"], r["l2_b"]) for r in resolved]
+    base = sweep.run_one_at_a_time(sample[: args.sweep_baseline], "f64", tol=1e-10, check_every=100,
+                                   max_steps=args.sweep_max_steps)
+    brecs = base["records"]
+    blat = np.array([r["t_done"] for r in brecs])
+    same = [r for r in recs[: len(brecs)]]
+    out = {"workload": "sweep", "metric": "sweep solves/s", "unit": "solves/s", "higher_is_better": True,
+           "sample": len(sample), "of": len(specs), "dtype": "f32",
+           "value": round(len(done) / res["wall"], 3), "wall_s": round(res["wall"], 3),
+           "time_to_steady_p50_s": float(np.percentile(t_done, 50)),
+           "time_to_steady_p99_s": float(np.percentile(t_done, 99)),
+           "states": states, "glups": round(node_updates / res["wall"] / 1e9, 2), "launches": res["launches"],
+           "autotune": res["tune"],
+           "gate_l2_le_1e-4": {"resolved_instances": len(resolved), "pass": int(sum(g <= 1e-4 for g in gate)),
+                               "median_l2": float(np.median(gate)) if gate else None},
+           "baseline_fp64_one_at_a_time": {
+               "instances": len(brecs), "solves_per_s": round(len(brecs) / base["wall"], 4),
+               "latency_p50_s": float(np.percentile(blat, 50)), "latency_p99_s": float(np.percentile(blat, 99)),
+               "steps": [r["steps"] for r in brecs], "solve_s": [round(r["solve_s"], 3) for r in brecs],
+               "batched_steps_same_instances": [r["steps"] for r in same]},
+           "settings": {"quantum": args.sweep_quantum, "max_steps": args.sweep_max_steps, "check_every": 100,
+                        "time_budget_s": args.sweep_time}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def bench_serve(args):
+    """Serving stream: Poisson arrivals at 2000 req/s (seed 5) of Hartmann / Hartmann-Couette
+    solves, nx in {4, 256}, ny lognormal (median 256, sigma 1, clamp 33..4096), Ha and c as in the
+    sweep, FP32 storage, residual tolerance 1e-9, a 120 GB device-memory budget.  A finite prefix of
+    the trace is replayed with a per-request step cap; the FIFO one-at-a-time FP64 baseline replays
+    the first requests of the same prefix."""
+    import numpy as np
+    import torch
+    from paper_2112_13930_gb300 import build, lks, serve, workloads
+    torch.cuda.set_device(0)
+    build.build()
+    lks.load()
+    trace = workloads.serve_trace(args.serve_requests, rate=2000.0, seed=5)
+    srv = serve.Server("f32", budget_bytes=120 << 30, small_pool_bytes=16 << 30, small_max_nodes=32768,
+                       large_workers=args.serve_workers, tol=1e-9, check_every=100, quantum=args.serve_quantum,
+                       max_steps=args.serve_max_steps)
+    recs = srv.serve(trace, time_limit=args.serve_time)
+    srv.close()
+    summ = serve.summarize(recs, len(trace))
+    base = serve.serve_one_at_a_time(trace[: args.serve_baseline], "f64", tol=1e-9, check_every=100,
+                                     max_steps=args.serve_max_steps, time_limit=args.serve_time)
+    bsum = serve.summarize(base, args.serve_baseline)
+    lanes = {}
+    for r in recs:
+        lanes[r["lane"]] = lanes.get(r["lane"], 0) + 1
+    out = {"workload": "serve", "metric": "served solves/s", "unit": "solves/s", "higher_is_better": True,
+           "dtype": "f32", "value": round(summ["solves_per_s"], 3), "summary": summ, "lanes": lanes,
+           "offered_rate_per_s": 2000.0, "baseline_fp64_fifo": bsum,
+           "settings": {"requests": args.serve_requests, "max_steps": args.serve_max_steps,
+                        "quantum": args.serve_quantum, "large_workers": args.serve_workers,
+                        "time_limit_s": args.serve_time}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # FP64 arithmetic per node per step in the fused kernel (adds, multiplies, FMAs counted as 2,
 # one division), counted from the kernel source; used for the FP64 ALU roofline.
 FP64_FLOPS_PER_NODE = 260
@@ -459,7 +545,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f64", "bf16", "f16"], default="f32")
     ap.add_argument("--n", type=int, default=4096)
-    ap.add_argument("--fp64-steps", type=int, default=300)
+    ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--skip-e2e", action="store_true")
@@ -468,6 +554,17 @@ def main():
     ap.add_argument("--workload", choices=["main", "precision", "sweep", "serve"], default="main")
     ap.add_argument("--precision-steps", type=int, default=1000)
     ap.add_argument("--precision-max-steps", type=int, default=3_000_000)
+    ap.add_argument("--sweep-sample", type=int, default=512)
+    ap.add_argument("--sweep-baseline", type=int, default=8)
+    ap.add_argument("--sweep-quantum", type=int, default=20000)
+    ap.add_argument("--sweep-max-steps", type=int, default=2_000_000)
+    ap.add_argument("--sweep-time", type=float, default=600.0)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-baseline", type=int, default=20)
+    ap.add_argument("--serve-quantum", type=int, default=2000)
+    ap.add_argument("--serve-max-steps", type=int, default=200_000)
+    ap.add_argument("--serve-workers", type=int, default=6)
+    ap.add_argument("--serve-time", type=float, default=600.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -475,6 +572,10 @@ def main():
         return bench_reference(args)
     if args.workload == "precision":
         return bench_precision(args)
+    if args.workload == "sweep":
+        return bench_sweep(args)
+    if args.workload == "serve":
+        return bench_serve(args)
     return bench_ours(args)
 
 

@@ -26,7 +26,12 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kMaxGroups = 15;  // named barriers 1..15 (0 is __syncthreads)
-constexpr int kStallChecks = 10;
+// An instance is declared STALLED when its residual has not reached a new minimum for kStallChecks
+// checks in a row while already below kStallBelow: the rounding floor of the storage type.  A long
+// window keeps slowly converging instances (diffusive times of 1e6+ steps, residual falling by
+// well under 1 % per check and jittering) from being stopped early.
+constexpr int kStallChecks = 1000;
+constexpr double kStallBelow = 1e-4;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(512) batch_kernel(InstDev* tab, const int32_t*
                         if (r < best) {
                             best = r;
                             stall = 0;
-                        } else if (++stall >= kStallChecks) {
+                        } else if (++stall >= kStallChecks && best < kStallBelow) {
                             st = LKS_INST_STALLED;
                         }
                         if (st == LKS_INST_RUNNING && steps >= max_steps) st = LKS_INST_MAX_STEPS;

@@ -1,0 +1,186 @@
+"""Continuous-batching solve server for channel requests.
+
+Requests (one channel problem each: size, Ha, c, forcing kind) arrive over time.  Two lanes share
+the GPU:
+
+- small lane: requests of at most `small_max_nodes` nodes are admitted into one lks_batch pool
+  (admission by device-memory footprint and free slots, done natively by lks_batch_add) and
+  advanced together by persistent launches of `quantum` steps; a request that arrives while others
+  are on the GPU joins at the next launch, and a finished one leaves the pool at once;
+- large lane: bigger requests each run as their own lattice (lks_create / lks_run_to_steady with
+  CUDA-graph stepping) on their own CUDA stream in a worker thread, up to `large_workers` at a
+  time, admitted while the large-lane share of the memory budget allows.
+
+Every result is the same as the request solved alone: the per-node update and the per-instance
+residual reduction do not depend on what else is resident.
+"""
+import collections
+import concurrent.futures
+import math
+import threading
+import time
+
+import numpy as np
+
+from . import batch as _batch
+from . import lks as _lks
+from . import sweep as _sweep
+
+TAU = _sweep.TAU
+
+
+class Server:
+    def __init__(self, storage="f32", budget_bytes=120 << 30, small_pool_bytes=8 << 30, small_max_nodes=32768,
+                 max_small=8192, large_workers=6, tol=1e-9, check_every=100, quantum=2000, max_steps=10**9,
+                 shape=None):
+        import torch
+        self.storage = storage
+        self.tol, self.check_every, self.quantum, self.max_steps = tol, check_every, quantum, max_steps
+        self.small_max_nodes = small_max_nodes
+        small_pool_bytes = min(small_pool_bytes, budget_bytes // 2)
+        self.large_budget = budget_bytes - small_pool_bytes
+        self.large_used = 0
+        self.batch = _batch.Batch(storage, max_instances=max_small, pool_bytes=small_pool_bytes,
+                                  threads_per_group=shape[0] if shape else 0, groups_per_cta=shape[1] if shape else 0)
+        self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=large_workers)
+        self.large_workers = large_workers
+        self.large_active = {}
+        self.streams = [torch.cuda.Stream() for _ in range(large_workers)]
+        self.free_streams = list(range(large_workers))
+        self.lock = threading.Lock()
+        self.small_slots = {}  # slot -> request record
+
+    def is_small(self, req):
+        return req["nx"] * req["ny"] <= self.small_max_nodes
+
+    def footprint(self, req):
+        d = _sweep.make_desc(req, self.tol, self.check_every, self.max_steps)
+        if self.is_small(req):
+            return _batch.instance_footprint(d, self.storage)
+        return _lks.footprint_bytes(req["nx"], req["ny"], req["closure"], self.storage)
+
+    # -- small lane ------------------------------------------------------------------------
+    def try_admit_small(self, req, now):
+        d = _sweep.make_desc(req, self.tol, self.check_every, self.max_steps)
+        slot = self.batch.add(d)
+        if slot is None:
+            return False
+        rec = {"req": req, "t_admit": now, "lane": "small"}
+        self.small_slots[slot] = rec
+        return True
+
+    def collect_small(self, now, out):
+        for slot in list(self.small_slots):
+            st, steps, r = self.batch.result(slot)
+            if st == _batch.INST_RUNNING:
+                continue
+            rec = self.small_slots.pop(slot)
+            u, b = self.batch.profiles(slot)
+            self.batch.remove(slot)
+            rec.update({"state": _batch.STATE_NAMES[st], "steps": int(steps), "residual": r, "t_done": now,
+                        "u": u, "b": b})
+            out.append(rec)
+
+    # -- large lane ------------------------------------------------------------------------
+    def _solve_large(self, req, sidx):
+        p = _sweep.lattice_params(req)
+        lat = _lks.Lattice(req["nx"], req["ny"], TAU, TAU, p["B0"], p["Fx"], req["closure"], self.storage,
+                           stream=self.streams[sidx])
+        lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
+        steps, r, status = lat.run_to_steady(self.tol, self.check_every, self.max_steps, raise_on_fail=False)
+        u, b = lat.profiles()
+        lat.close()
+        state = {_lks.LKS_OK: "converged", _lks.LKS_ENOTCONVERGED: "max_steps",
+                 _lks.LKS_EUNSTABLE: "unstable"}.get(status, "error")
+        return {"state": state, "steps": int(steps), "residual": r, "u": u, "b": b}
+
+    def try_admit_large(self, req, now):
+        fp = self.footprint(req)
+        if not self.free_streams or self.large_used + fp > self.large_budget:
+            return False
+        sidx = self.free_streams.pop()
+        self.large_used += fp
+        fut = self.pool.submit(self._solve_large, req, sidx)
+        self.large_active[fut] = ({"req": req, "t_admit": now, "lane": "large"}, sidx, fp)
+        return True
+
+    def collect_large(self, now, out):
+        for fut in [f for f in self.large_active if f.done()]:
+            rec, sidx, fp = self.large_active.pop(fut)
+            rec.update(fut.result())
+            rec["t_done"] = now
+            self.large_used -= fp
+            self.free_streams.append(sidx)
+            out.append(rec)
+
+    # -- the loop ----------------------------------------------------------------------------
+    def serve(self, trace, time_limit=None):
+        """Replay a trace (requests with t_arrival in seconds, sorted).  Returns one record per
+        finished request with arrival, admission and completion times (seconds from the start)."""
+        t0 = time.perf_counter()
+        q_small, q_large = collections.deque(), collections.deque()
+        out = []
+        i = 0
+        n = len(trace)
+        while len(out) < n:
+            now = time.perf_counter() - t0
+            while i < n and trace[i]["t_arrival"] <= now:
+                (q_small if self.is_small(trace[i]) else q_large).append(trace[i])
+                i += 1
+            while q_small and self.try_admit_small(q_small[0], now):
+                q_small.popleft()
+            while q_large and self.try_admit_large(q_large[0], now):
+                q_large.popleft()
+            if self.small_slots:
+                self.batch.run(self.quantum)
+            else:
+                time.sleep(0.0005)
+            now = time.perf_counter() - t0
+            self.collect_small(now, out)
+            self.collect_large(now, out)
+            if time_limit is not None and now > time_limit:
+                break
+        for rec in out:
+            rec["t_arrival"] = rec["req"]["t_arrival"]
+            rec["latency"] = rec["t_done"] - rec["t_arrival"]
+        return out
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+        self.batch.close()
+
+
+def serve_one_at_a_time(trace, storage="f64", tol=1e-9, check_every=100, max_steps=10**9, time_limit=None):
+    """Baseline: the same trace solved first-in first-out, one request at a time, through
+    lks_create / lks_run_to_steady / lks_destroy."""
+    import torch
+    t0 = time.perf_counter()
+    out = []
+    for req in trace:
+        now = time.perf_counter() - t0
+        if now < req["t_arrival"]:
+            time.sleep(req["t_arrival"] - now)
+        p = _sweep.lattice_params(req)
+        lat = _lks.Lattice(req["nx"], req["ny"], TAU, TAU, p["B0"], p["Fx"], req["closure"], storage)
+        lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
+        steps, r, status = lat.run_to_steady(tol, check_every, max_steps, raise_on_fail=False)
+        u, b = lat.profiles()
+        lat.close()
+        torch.cuda.synchronize()
+        t_done = time.perf_counter() - t0
+        out.append({"req": req, "t_arrival": req["t_arrival"], "t_done": t_done, "latency": t_done - req["t_arrival"],
+                    "steps": int(steps), "residual": r, "status": int(status), "u": u, "b": b})
+        if time_limit is not None and t_done > time_limit:
+            break
+    return out
+
+
+def summarize(records, n_offered):
+    lat = np.array([r["latency"] for r in records]) if records else np.array([np.nan])
+    t_first = min(r["t_arrival"] for r in records) if records else 0.0
+    t_last = max(r["t_done"] for r in records) if records else 0.0
+    states = collections.Counter(r.get("state", "done") for r in records)
+    return {"offered": n_offered, "completed": len(records),
+            "solves_per_s": len(records) / max(1e-9, t_last - t_first),
+            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "makespan_s": t_last - t_first, "states": dict(states)}
