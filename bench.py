@@ -196,6 +196,23 @@ def bench_reference(args):
     return 0
 
 
+def replica_max(x, world_size, device):
+    """Max of a per-rank time over the process group (the slowest replica sets the job time)."""
+    if world_size <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world_size, max_seconds):
+    """Whole-job throughput of independent replicas: every rank processed units_per_rank units in at
+    most max_seconds."""
+    return units_per_rank * world_size / max_seconds
+
+
 def _time_steps(lat, steps, stream):
     import torch
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -234,11 +251,7 @@ def bench_ours(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if ws > 1:
-            t = torch.tensor([x], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            return float(t.item())
-        return x
+        return replica_max(x, ws, "cuda")
 
     # --- main measurement -------------------------------------------------------------------
     lat = make(args.storage)
@@ -252,7 +265,7 @@ def bench_ours(args):
     clocks = sampler.stop()
     t = max_over_ranks(t)
     nodes = n * n
-    value = nodes * args.steps * ws / t / 1e6
+    value = replica_throughput(nodes * args.steps, ws, t) / 1e6
     per_launch = t / args.steps
     peak, peak_kind = _peaks()
     bpn = BYTES_PER_NODE[args.storage]
@@ -460,7 +473,8 @@ def bench_sweep(args):
     lks.load()
     specs = workloads.sweep_instances(4096, seed=4096)
     sample = specs[: args.sweep_sample]
-    cands = [(64, 8), (128, 4), (256, 2), (512, 1), (128, 2), (256, 1)]
+    cands = [(64, 8, 1), (128, 4, 1), (256, 2, 1), (512, 1, 1), (256, 1, 2), (512, 1, 2), (256, 1, 4),
+             (512, 1, 4), (128, 1, 8), (256, 1, 8)]
     res = sweep.run_batched(sample, "f32", tol=1e-10, check_every=100, quantum=args.sweep_quantum,
                             max_steps=args.sweep_max_steps, tune_candidates=cands, time_budget=args.sweep_time)
     recs = res["records"]
@@ -477,6 +491,14 @@ def bench_sweep(args):
     brecs = base["records"]
     blat = np.array([r["t_done"] for r in brecs])
     same = [r for r in recs[: len(brecs)]]
+    # FP32 batched result against the FP64 solve of the same instance on the same grid
+    vs64 = []
+    for r32, r64 in zip(same, brecs):
+        if r32["state"] == "unstable" or r64["status"] == 4:
+            continue
+        eu = float(np.sqrt(np.mean((r32["u"] - r64["u"]) ** 2)) / max(1e-300, np.max(np.abs(r64["u"]))))
+        eb = float(np.sqrt(np.mean((r32["b"] - r64["b"]) ** 2)) / max(1e-300, np.max(np.abs(r64["b"]))))
+        vs64.append(max(eu, eb))
     out = {"workload": "sweep", "metric": "sweep solves/s", "unit": "solves/s", "higher_is_better": True,
            "sample": len(sample), "of": len(specs), "dtype": "f32",
            "value": round(len(done) / res["wall"], 3), "wall_s": round(res["wall"], 3),
@@ -490,7 +512,9 @@ def bench_sweep(args):
                "instances": len(brecs), "solves_per_s": round(len(brecs) / base["wall"], 4),
                "latency_p50_s": float(np.percentile(blat, 50)), "latency_p99_s": float(np.percentile(blat, 99)),
                "steps": [r["steps"] for r in brecs], "solve_s": [round(r["solve_s"], 3) for r in brecs],
-               "batched_steps_same_instances": [r["steps"] for r in same]},
+               "batched_steps_same_instances": [r["steps"] for r in same],
+               "fp32_batched_vs_fp64_rel_l2": vs64,
+               "fp64_vs_analytic_rel_l2": [max(r["l2_u"], r["l2_b"]) for r in brecs]},
            "settings": {"quantum": args.sweep_quantum, "max_steps": args.sweep_max_steps, "check_every": 100,
                         "time_budget_s": args.sweep_time}}
     print(json.dumps(out), flush=True)
@@ -532,9 +556,9 @@ def bench_serve(args):
     return 0
 
 
-# FP64 arithmetic per node per step in the fused kernel (adds, multiplies, FMAs counted as 2,
-# one division), counted from the kernel source; used for the FP64 ALU roofline.
-FP64_FLOPS_PER_NODE = 260
+# FP64 arithmetic per bulk node per step in collide_node, counted from the source with an FMA as
+# 2 flops: moments and 1/rho (Newton) 40, equilibrium set-up 23, nine directions 116, g 33.
+FP64_FLOPS_PER_NODE = 212
 
 
 def main():

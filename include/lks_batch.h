@@ -15,8 +15,10 @@
  * CTA is split into groups_per_cta groups of threads_per_group threads; a group takes the next
  * running instance from a work list (one atomic add, no waiting), advances it by up to quantum
  * steps (synchronising only its own threads between steps), checks the steady-state residual
- * every check_every steps, writes its status, and takes the next instance.  The launch (counter
- * reset, kernel, status copy) is a captured CUDA graph.  There are no spin-waits.
+ * every check_every steps, writes its status, and takes the next instance.  With cluster_ctas > 1
+ * the worker is instead a thread-block cluster of that many CTAs on as many SMs, synchronised by
+ * the hardware cluster barrier between steps, so one large instance advances faster.  The launch
+ * (counter reset, kernel, status copy) is a captured CUDA graph.  There are no spin-waits.
  *
  * Memory: instance states live in one device pool (caller memory or allocated at create) that
  * a host-side first-fit allocator carves; lks_batch_add returns LKS_EBUSY when no slot is free
@@ -54,6 +56,9 @@ typedef struct lks_batch_config {
     size_t dev_buffer_bytes;    /* must be >= pool_bytes when dev_buffer is given */
     int32_t threads_per_group;  /* power of two in [32, 512]; 0 = 256 */
     int32_t groups_per_cta;     /* 1..15, threads_per_group * groups_per_cta <= 512; 0 = 1 */
+    int32_t cluster_ctas;       /* 1, 2, 4 or 8 CTAs (one per SM) per instance; > 1 needs groups_per_cta = 1;
+                                   0 = 1 */
+    int32_t pad;
 } lks_batch_config;
 
 typedef struct lks_instance_desc {
@@ -113,15 +118,16 @@ lks_status lks_batch_moments(lks_batch* b, int32_t slot, int what, double* host_
 /* Free a slot and its pool memory (the instance may be in any state).  Synchronises. */
 lks_status lks_batch_remove(lks_batch* b, int32_t slot);
 
-/* Change the thread-group shape used by later lks_batch_run calls. */
-lks_status lks_batch_set_shape(lks_batch* b, int32_t threads_per_group, int32_t groups_per_cta);
+/* Change the thread-group shape used by later lks_batch_run calls (see lks_batch_config). */
+lks_status lks_batch_set_shape(lks_batch* b, int32_t threads_per_group, int32_t groups_per_cta, int32_t cluster_ctas);
 
 /* Time one lks_batch_run of probe_steps on the current instances for each candidate shape
- * (threads_per_group x groups_per_cta given as parallel arrays of length n), restoring every
- * instance's state after each candidate, then keep the fastest shape.  seconds_out (nullable,
- * length n) gets each candidate's time.  Synchronises. */
+ * (threads_per_group, groups_per_cta, cluster_ctas given as parallel arrays of length n), restoring
+ * every instance's state after each candidate, then keep the fastest shape.  seconds_out
+ * (nullable, length n) gets each candidate's time.  Synchronises. */
 lks_status lks_batch_autotune(lks_batch* b, int64_t probe_steps, const int32_t* threads_per_group,
-                              const int32_t* groups_per_cta, int32_t n, double* seconds_out, int32_t* best_index);
+                              const int32_t* groups_per_cta, const int32_t* cluster_ctas, int32_t n,
+                              double* seconds_out, int32_t* best_index);
 
 /* Pool bytes currently free, and in use. */
 lks_status lks_batch_memory(const lks_batch* b, size_t* free_bytes, size_t* used_bytes);

@@ -24,6 +24,8 @@ class BatchConfig(ctypes.Structure):
         ("dev_buffer_bytes", ctypes.c_size_t),
         ("threads_per_group", ctypes.c_int32),
         ("groups_per_cta", ctypes.c_int32),
+        ("cluster_ctas", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -66,8 +68,8 @@ SIGNATURES = {
     "lks_batch_result": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(InstanceResult)]),
     "lks_batch_moments": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int, _DP]),
     "lks_batch_remove": (ctypes.c_int, [_VP, ctypes.c_int32]),
-    "lks_batch_set_shape": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
-    "lks_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int64, _I32P, _I32P, ctypes.c_int32, _DP, _I32P]),
+    "lks_batch_set_shape": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "lks_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int64, _I32P, _I32P, _I32P, ctypes.c_int32, _DP, _I32P]),
     "lks_batch_memory": (ctypes.c_int, [_VP, _SZP, _SZP]),
     "lks_batch_destroy": (ctypes.c_int, [_VP]),
     "lks_batch_last_error": (ctypes.c_char_p, [_VP]),
@@ -102,7 +104,7 @@ class Batch:
     """A pool of resident channel instances (wrapped lks_batch)."""
 
     def __init__(self, storage="f32", max_instances=4096, pool_bytes=1 << 30, threads_per_group=0,
-                 groups_per_cta=0, stream=None, torch_memory=True):
+                 groups_per_cta=0, cluster_ctas=0, stream=None, torch_memory=True):
         import torch
         L = lib()
         if stream is None:
@@ -112,7 +114,8 @@ class Batch:
         self._pool = None
         cfg = BatchConfig(storage=self.storage, max_instances=max_instances, pool_bytes=pool_bytes,
                           cuda_stream=stream.cuda_stream or None, dev_buffer=None, dev_buffer_bytes=0,
-                          threads_per_group=threads_per_group, groups_per_cta=groups_per_cta)
+                          threads_per_group=threads_per_group, groups_per_cta=groups_per_cta,
+                          cluster_ctas=cluster_ctas, pad=0)
         if torch_memory:
             self._pool = torch.empty(pool_bytes, dtype=torch.uint8, device=stream.device)
             cfg.dev_buffer = self._pool.data_ptr()
@@ -164,18 +167,19 @@ class Batch:
         self._check(lib().lks_batch_remove(self._h, slot))
         self.shapes.pop(slot, None)
 
-    def set_shape(self, threads_per_group, groups_per_cta):
-        self._check(lib().lks_batch_set_shape(self._h, threads_per_group, groups_per_cta))
+    def set_shape(self, threads_per_group, groups_per_cta, cluster_ctas=1):
+        self._check(lib().lks_batch_set_shape(self._h, threads_per_group, groups_per_cta, cluster_ctas))
 
     def autotune(self, candidates, probe_steps=200):
-        """Time each (threads_per_group, groups_per_cta) candidate on the current instances (state is
-        restored after each); keeps and returns the fastest plus all timings."""
+        """Time each (threads_per_group, groups_per_cta[, cluster_ctas]) candidate on the current
+        instances (state is restored after each); keeps and returns the fastest plus all timings."""
         n = len(candidates)
         T = (ctypes.c_int32 * n)(*[c[0] for c in candidates])
         G = (ctypes.c_int32 * n)(*[c[1] for c in candidates])
+        C = (ctypes.c_int32 * n)(*[(c[2] if len(c) > 2 else 1) for c in candidates])
         secs = (ctypes.c_double * n)()
         best = ctypes.c_int32(-1)
-        self._check(lib().lks_batch_autotune(self._h, int(probe_steps), T, G, n, secs, ctypes.byref(best)))
+        self._check(lib().lks_batch_autotune(self._h, int(probe_steps), T, G, C, n, secs, ctypes.byref(best)))
         return candidates[best.value], list(secs)
 
     def memory(self):
@@ -196,8 +200,9 @@ class Batch:
             pass
 
 
-# Shapes the autotuner tries (threads per instance group, groups per CTA).
-DEFAULT_CANDIDATES = [(64, 8), (128, 4), (256, 2), (512, 1), (128, 2), (256, 1), (64, 4), (32, 8)]
+# Shapes the autotuner tries (threads per instance group, groups per CTA, CTAs per cluster).
+DEFAULT_CANDIDATES = [(64, 8, 1), (128, 4, 1), (256, 2, 1), (512, 1, 1), (128, 2, 1), (256, 1, 1), (64, 4, 1),
+                      (32, 8, 1), (256, 1, 2), (512, 1, 2), (256, 1, 4), (512, 1, 4), (128, 1, 8), (256, 1, 8)]
 
 
 def tuned_shape(batch, cache_path, key, probe_steps=200, candidates=None):
@@ -210,9 +215,9 @@ def tuned_shape(batch, cache_path, key, probe_steps=200, candidates=None):
         except Exception:
             cache = {}
     if key in cache:
-        t, g = cache[key]["shape"]
-        batch.set_shape(t, g)
-        return (t, g), cache[key]
+        shape = cache[key]["shape"]
+        batch.set_shape(*shape)
+        return tuple(shape), cache[key]
     best, secs = batch.autotune(candidates or DEFAULT_CANDIDATES, probe_steps)
     entry = {"shape": list(best), "candidates": [list(c) for c in (candidates or DEFAULT_CANDIDATES)],
              "seconds": secs, "probe_steps": probe_steps}

@@ -118,6 +118,16 @@ StepParams<double> make_step_params(int nx, int ny, int closure, double tau_f, d
     s.src_coef = 1.0 - 0.5 / tau_f;
     s.Fx = Fx;
     s.B0 = B0;
+    s.om1f = 1.0 - s.omega_f;
+    s.om1m = 1.0 - s.omega_m;
+    s.owf0 = s.omega_f * (4.0 / 9.0);
+    s.owf1 = s.omega_f * (1.0 / 9.0);
+    s.owf5 = s.omega_f * (1.0 / 36.0);
+    s.owm0 = s.omega_m * (1.0 / 3.0);
+    s.owm1 = s.omega_m * (1.0 / 6.0);
+    s.sw0 = s.src_coef * 3.0 * Fx * (4.0 / 9.0);
+    s.sw1 = s.src_coef * 3.0 * Fx * (1.0 / 9.0);
+    s.sw5 = s.src_coef * 3.0 * Fx * (1.0 / 36.0);
     s.bot = wall_coef(closure, a, tau_m, B0, c_bot, u_bot, +1.0);
     s.top = wall_coef(closure, a, tau_m, B0, c_top, u_top, -1.0);
     return s;

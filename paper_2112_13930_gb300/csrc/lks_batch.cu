@@ -8,6 +8,7 @@
 // fixed-order reduction.  An instance's state (two population buffers + residual snapshot, about
 // 170 B per FP32 node) stays in L2 while its group works on it, so the per-step traffic is served
 // from L2 rather than HBM.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -74,6 +75,10 @@ __device__ __forceinline__ StepParams<C> to_compute(const StepParams<double>& d)
     o.src_coef = (C)d.src_coef;
     o.Fx = (C)d.Fx;
     o.B0 = (C)d.B0;
+    o.om1f = (C)d.om1f; o.om1m = (C)d.om1m;
+    o.owf0 = (C)d.owf0; o.owf1 = (C)d.owf1; o.owf5 = (C)d.owf5;
+    o.owm0 = (C)d.owm0; o.owm1 = (C)d.owm1;
+    o.sw0 = (C)d.sw0; o.sw1 = (C)d.sw1; o.sw5 = (C)d.sw5;
     o.bot.r = (C)d.bot.r; o.bot.bc = (C)d.bot.bc; o.bot.kx = (C)d.bot.kx; o.bot.du = (C)d.bot.du; o.bot.U = (C)d.bot.U;
     o.top.r = (C)d.top.r; o.top.bc = (C)d.top.bc; o.top.kx = (C)d.top.kx; o.top.du = (C)d.top.du; o.top.U = (C)d.top.U;
     return o;
@@ -203,6 +208,174 @@ __global__ void __launch_bounds__(512) batch_kernel(InstDev* tab, const int32_t*
     }
 }
 
+// Loads that bypass L1 (ld.global.cg): in cluster mode a node's neighbours may have been written
+// by a CTA on another SM, whose stores L1 of this SM does not see.
+template <typename S, typename C> struct CgLoader;
+template <> struct CgLoader<double, double> {
+    static __device__ __forceinline__ double ld(const double* p) { return __ldcg(p); }
+};
+template <> struct CgLoader<float, float> {
+    static __device__ __forceinline__ float ld(const float* p) { return __ldcg(p); }
+};
+template <> struct CgLoader<__nv_bfloat16, float> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+    }
+};
+template <> struct CgLoader<__half, float> {
+    static __device__ __forceinline__ float ld(const __half* p) {
+        return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+    }
+};
+
+// Cluster mode: the CS CTAs of one thread-block cluster (on CS SMs) work on one instance together,
+// CTA r updating nodes r*T + t, r*T + t + CS*T, ...; one cluster barrier (release/acquire at cluster
+// scope) separates the steps, and the residual partials of the CTAs are summed by CTA 0 in rank
+// order through distributed shared memory.  Large instances then advance CS times faster per step
+// than with one CTA.
+template <typename S, typename C>
+__global__ void __launch_bounds__(512) batch_cluster_kernel(InstDev* tab, const int32_t* work, const Ctl* ctl,
+                                                             int32_t* counter, ResultDev* res, int T) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double red[];
+    __shared__ int32_t pick;
+    __shared__ int32_t flag;
+    __shared__ double cpart[4 * 8];
+    const int CS = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int lt = threadIdx.x;
+    const int nwork = ctl->nwork;
+    const int64_t quantum = ctl->quantum;
+    int32_t* pick0 = cl.map_shared_rank(&pick, 0);
+    int32_t* flag0 = cl.map_shared_rank(&flag, 0);
+    double* cpart0 = cl.map_shared_rank(cpart, 0);
+    const int64_t stride = (int64_t)CS * T;
+    for (;;) {
+        if (rank == 0 && lt == 0) pick = atomicAdd(counter, 1);
+        cl.sync();
+        const int w = *pick0;
+        // Every CTA must have read CTA 0's shared `pick` before CTA 0 can overwrite it or exit
+        // (reading the shared memory of a CTA that has exited is an invalid access).
+        cl.sync();
+        if (w >= nwork) break;
+        const int slot = work[w];
+        InstDev* I = tab + slot;
+        const StepParams<C> p = to_compute<C>(I->pd);
+        const int64_t N = p.N;
+        const int closure = I->closure;
+        const int64_t check_every = I->check_every, max_steps = I->max_steps;
+        int cur = I->cur;
+        int64_t steps = I->steps;
+        int state = LKS_INST_RUNNING;
+        double r = I->residual, best = I->best_r;
+        int stall = I->stall;
+        const int64_t first = (int64_t)rank * T + lt;
+        for (int64_t s = 0; s < quantum; ++s) {
+            const S* fi = (const S*)I->f[cur];
+            const S* gi = (const S*)I->g[cur];
+            S* fo = (S*)I->f[cur ^ 1];
+            S* go = (S*)I->g[cur ^ 1];
+            if (closure == 0) {
+                for (int64_t n = first; n < N; n += stride) lks::step_node_with<S, C, 0, CgLoader<S, C>>(fi, gi, fo, go, p, n);
+            } else {
+                for (int64_t n = first; n < N; n += stride) lks::step_node_with<S, C, 1, CgLoader<S, C>>(fi, gi, fo, go, p, n);
+            }
+            cur ^= 1;
+            ++steps;
+            cl.sync();
+            if (steps % check_every == 0 || steps >= max_steps) {
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                const S* fc = (const S*)I->f[cur];
+                const S* gc = (const S*)I->g[cur];
+                double* snap = I->snap;
+                for (int64_t n = first; n < N; n += stride) {
+                    double v[9];
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) v[a] = (double)CgLoader<S, C>::ld(fc + a * N + n);
+                    const double drho = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+                    const double jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+                    const double ux = (jx - 0.5 * (double)I->pd.Fx) / (1.0 + drho);
+                    double bx = 0.0;
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) bx += (double)CgLoader<S, C>::ld(gc + a * N + n);
+                    const double du = ux - snap[n], db = bx - snap[N + n];
+                    acc[0] += du * du;
+                    acc[1] += ux * ux;
+                    acc[2] += db * db;
+                    acc[3] += bx * bx;
+                    snap[n] = ux;
+                    snap[N + n] = bx;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) red[k * T + lt] = acc[k];
+                __syncthreads();
+                for (int h = T / 2; h > 0; h >>= 1) {
+                    if (lt < h)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) red[k * T + lt] += red[k * T + lt + h];
+                    __syncthreads();
+                }
+                if (lt == 0)
+                    for (int k = 0; k < 4; ++k) cpart0[4 * rank + k] = red[k * T];
+                cl.sync();
+                if (rank == 0 && lt == 0) {
+                    double t[4] = {0.0, 0.0, 0.0, 0.0};
+                    for (int q = 0; q < CS; ++q)
+                        for (int k = 0; k < 4; ++k) t[k] += cpart[4 * q + k];
+                    const double ru = t[1] > 1e-60 ? sqrt(t[0] / t[1]) : 0.0;
+                    const double rb = t[3] > 1e-60 ? sqrt(t[2] / t[3]) : 0.0;
+                    r = ru > rb ? ru : rb;
+                    int st = LKS_INST_RUNNING;
+                    if (!isfinite(r) || !isfinite(t[1]) || !isfinite(t[3])) {
+                        st = LKS_INST_UNSTABLE;
+                    } else if (r < I->tol) {
+                        st = LKS_INST_CONVERGED;
+                    } else {
+                        if (r < best) {
+                            best = r;
+                            stall = 0;
+                        } else if (++stall >= kStallChecks && best < kStallBelow) {
+                            st = LKS_INST_STALLED;
+                        }
+                        if (st == LKS_INST_RUNNING && steps >= max_steps) st = LKS_INST_MAX_STEPS;
+                    }
+                    flag = st;
+                }
+                cl.sync();
+                // CTA 0 writes `flag` again only at the next check, after at least one more
+                // cluster barrier, and leaves the kernel only after the next pick's barriers.
+                state = *flag0;
+                if (state != LKS_INST_RUNNING) break;
+            }
+        }
+        if (rank == 0 && lt == 0) {
+            I->cur = cur;
+            I->steps = steps;
+            I->state = state;
+            I->residual = r;
+            I->best_r = best;
+            I->stall = stall;
+            res[slot].state = state;
+            res[slot].cur = cur;
+            res[slot].steps = steps;
+            res[slot].residual = r;
+        }
+        cl.sync();
+    }
+}
+
+typedef void (*BatchClusterFn)(InstDev*, const int32_t*, const Ctl*, int32_t*, ResultDev*, int);
+
+BatchClusterFn cluster_kernel_for(int storage) {
+    switch (storage) {
+        case 0: return batch_cluster_kernel<double, double>;
+        case 1: return batch_cluster_kernel<float, float>;
+        case 2: return batch_cluster_kernel<__nv_bfloat16, float>;
+        default: return batch_cluster_kernel<__half, float>;
+    }
+}
+
 typedef void (*BatchKernelFn)(InstDev*, const int32_t*, const Ctl*, int32_t*, ResultDev*, int);
 
 BatchKernelFn kernel_for(int storage) {
@@ -237,9 +410,11 @@ size_t inst_bytes(int nx, int ny, int storage) {
     return 2 * align_up(9 * N * sb) + 2 * align_up(10 * N * sb) + align_up(2 * N * sizeof(double));
 }
 
-bool valid_shape(int T, int G) {
+bool valid_shape(int T, int G, int CS) {
     if (T < 32 || T > 512 || (T & (T - 1)) != 0) return false;
     if (G < 1 || G > kMaxGroups || T * G > 512) return false;
+    if (CS != 1 && CS != 2 && CS != 4 && CS != 8) return false;
+    if (CS > 1 && G != 1) return false;
     return true;
 }
 
@@ -269,9 +444,9 @@ struct lks_batch {
     Ctl* d_ctl = nullptr;
     Ctl* h_ctl = nullptr;        // pinned
     int32_t* d_counter = nullptr;
-    int T = 256, G = 1;
+    int T = 256, G = 1, CS = 1;
     cudaGraphExec_t graph = nullptr;
-    int graph_T = 0, graph_G = 0;
+    int graph_T = 0, graph_G = 0, graph_CS = 0;
     std::string err;
 };
 
@@ -333,19 +508,43 @@ int blocks_per_sm(lks_batch* b, int T, int G) {
 }
 
 cudaError_t enqueue_launch(lks_batch* b, cudaStream_t st) {
-    const int T = b->T, G = b->G;
+    const int T = b->T, G = b->G, CS = b->CS;
     const size_t smem = (size_t)G * 4 * T * sizeof(double);
-    const int grid = blocks_per_sm(b, T, G) * b->nsm;
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    kernel_for(b->cfg.storage)<<<grid, T * G, smem, st>>>(b->d_tab, b->d_work, b->d_ctl, b->d_counter, b->d_res, T);
+    if (CS == 1) {
+        const int grid = blocks_per_sm(b, T, G) * b->nsm;
+        kernel_for(b->cfg.storage)<<<grid, T * G, smem, st>>>(b->d_tab, b->d_work, b->d_ctl, b->d_counter, b->d_res,
+                                                              T);
+    } else {
+        cudaLaunchConfig_t lc = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        lc.blockDim = dim3(T);
+        lc.dynamicSmemBytes = smem;
+        lc.stream = st;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        lc.gridDim = dim3(CS * b->nsm);
+        int clusters = 0;
+        e = cudaOccupancyMaxActiveClusters(&clusters, cluster_kernel_for(b->cfg.storage), &lc);
+        if (e != cudaSuccess) return e;
+        if (clusters < 1) clusters = 1;
+        lc.gridDim = dim3(clusters * CS);
+        e = cudaLaunchKernelEx(&lc, cluster_kernel_for(b->cfg.storage), b->d_tab, (const int32_t*)b->d_work,
+                               (const Ctl*)b->d_ctl, b->d_counter, b->d_res, T);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(b->h_res, b->d_res, b->slots.size() * sizeof(ResultDev), cudaMemcpyDeviceToHost, st);
 }
 
 cudaError_t ensure_graph(lks_batch* b) {
-    if (b->graph && b->graph_T == b->T && b->graph_G == b->G) return cudaSuccess;
+    if (b->graph && b->graph_T == b->T && b->graph_G == b->G && b->graph_CS == b->CS) return cudaSuccess;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -371,6 +570,7 @@ cudaError_t ensure_graph(lks_batch* b) {
     if (e == cudaSuccess) {
         b->graph_T = b->T;
         b->graph_G = b->G;
+        b->graph_CS = b->CS;
     }
     return e;
 }
@@ -393,13 +593,17 @@ lks_status lks_batch_create(const lks_batch_config* cfg, lks_batch** out) {
     if (cfg->pool_bytes < kAlign) return bfail(nullptr, LKS_EINVAL, "pool_bytes too small");
     const int T = cfg->threads_per_group ? cfg->threads_per_group : 256;
     const int G = cfg->groups_per_cta ? cfg->groups_per_cta : 1;
-    if (!valid_shape(T, G))
-        return bfail(nullptr, LKS_EINVAL, "threads_per_group must be a power of two in [32,512], groups 1..15, product <= 512");
+    const int CS = cfg->cluster_ctas ? cfg->cluster_ctas : 1;
+    if (!valid_shape(T, G, CS))
+        return bfail(nullptr, LKS_EINVAL,
+                     "threads_per_group must be a power of two in [32,512], groups 1..15, product <= 512, "
+                     "cluster_ctas 1/2/4/8 (groups 1 when > 1)");
     lks_batch* b = new (std::nothrow) lks_batch();
     if (!b) return bfail(nullptr, LKS_ENOMEM, "host allocation failed");
     b->cfg = *cfg;
     b->T = T;
     b->G = G;
+    b->CS = CS;
     b->stream = (cudaStream_t)cfg->cuda_stream;
     b->slots.resize(cfg->max_instances);
     cudaError_t e = cudaGetDevice(&b->device);
@@ -602,20 +806,21 @@ lks_status lks_batch_remove(lks_batch* b, int32_t slot) {
     return LKS_OK;
 }
 
-lks_status lks_batch_set_shape(lks_batch* b, int32_t T, int32_t G) {
+lks_status lks_batch_set_shape(lks_batch* b, int32_t T, int32_t G, int32_t CS) {
     if (!b) return bfail(nullptr, LKS_EINVAL, "batch is NULL");
-    if (!valid_shape(T, G)) return bfail(b, LKS_EINVAL, "invalid thread-group shape");
+    if (!valid_shape(T, G, CS)) return bfail(b, LKS_EINVAL, "invalid thread-group shape");
     b->T = T;
     b->G = G;
+    b->CS = CS;
     return LKS_OK;
 }
 
-lks_status lks_batch_autotune(lks_batch* b, int64_t probe_steps, const int32_t* Ts, const int32_t* Gs, int32_t n,
-                              double* seconds_out, int32_t* best_index) {
+lks_status lks_batch_autotune(lks_batch* b, int64_t probe_steps, const int32_t* Ts, const int32_t* Gs,
+                              const int32_t* Cs, int32_t n, double* seconds_out, int32_t* best_index) {
     if (!b) return bfail(nullptr, LKS_EINVAL, "batch is NULL");
-    if (!Ts || !Gs || n < 1 || probe_steps < 1) return bfail(b, LKS_EINVAL, "bad autotune arguments");
+    if (!Ts || !Gs || !Cs || n < 1 || probe_steps < 1) return bfail(b, LKS_EINVAL, "bad autotune arguments");
     for (int k = 0; k < n; ++k)
-        if (!valid_shape(Ts[k], Gs[k])) return bfail(b, LKS_EINVAL, "invalid candidate shape");
+        if (!valid_shape(Ts[k], Gs[k], Cs[k])) return bfail(b, LKS_EINVAL, "invalid candidate shape");
     // save every used instance's state, the table and the results
     const size_t M = b->slots.size();
     size_t total = 0;
@@ -650,13 +855,14 @@ lks_status lks_batch_autotune(lks_batch* b, int64_t probe_steps, const int32_t* 
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    const int T0 = b->T, G0 = b->G;
+    const int T0 = b->T, G0 = b->G, C0 = b->CS;
     int best = -1;
     double best_t = INFINITY;
     lks_status st = LKS_OK;
     for (int k = 0; k < n && e == cudaSuccess && st == LKS_OK; ++k) {
         b->T = Ts[k];
         b->G = Gs[k];
+        b->CS = Cs[k];
         e = cudaEventRecord(e0, b->stream);
         if (e != cudaSuccess) break;
         st = lks_batch_run(b, probe_steps, nullptr);
@@ -683,11 +889,13 @@ lks_status lks_batch_autotune(lks_batch* b, int64_t probe_steps, const int32_t* 
     if (st != LKS_OK || e != cudaSuccess || best < 0) {
         b->T = T0;
         b->G = G0;
+        b->CS = C0;
         if (st != LKS_OK) return st;
         return bcuda(b, e == cudaSuccess ? cudaErrorUnknown : e, "lks_batch_autotune");
     }
     b->T = Ts[best];
     b->G = Gs[best];
+    b->CS = Cs[best];
     if (best_index) *best_index = best;
     return LKS_OK;
 }

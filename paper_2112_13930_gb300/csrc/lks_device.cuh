@@ -34,6 +34,11 @@ struct StepParams {
     C src_coef;           // 1 - 1/(2 tau_f)
     C Fx;                 // body force along x
     C B0;                 // applied field along y
+    // products of the above folded on the host, so the collision needs fewer operations:
+    C om1f, om1m;         // 1 - omega_f, 1 - omega_m
+    C owf0, owf1, owf5;   // omega_f * w_a for |e_a|^2 = 0, 1, 2
+    C owm0, owm1;         // omega_m * W_a for a = 0 and a = 1..4
+    C sw0, sw1, sw5;      // (1 - 1/(2 tau_f)) * 3 Fx * w_a   (source-term prefactor)
     WallCoef<C> bot, top;
 };
 
@@ -63,6 +68,18 @@ template <> __device__ __forceinline__ void store_s<__nv_bfloat16, float>(__nv_b
 }
 template <> __device__ __forceinline__ void store_s<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
 
+// 1/rho.  FP64: Newton-Raphson iteration for the reciprocal, r <- r + r (1 - rho r), started from
+// the correctly rounded FP32 reciprocal (relative error <= 2^-24); two iterations square the error
+// twice (<= 2^-96 before rounding), far below FP64's resolution.  FP32: the correctly rounded
+// reciprocal.
+__device__ __forceinline__ double recip(double rho) {
+    double r = (double)__frcp_rn((float)rho);
+    r = fma(r, fma(-rho, r, 1.0), r);
+    r = fma(r, fma(-rho, r, 1.0), r);
+    return r;
+}
+__device__ __forceinline__ float recip(float rho) { return __frcp_rn(rho); }
+
 // Equilibrium deviations and the collision, for one node whose post-stream, post-closure
 // populations are in f[9], gx[5], gy[5] (deviation form).  Overwrites them with the
 // post-collision deviations.  Returns nothing; moments are recomputed by callers that need them.
@@ -75,67 +92,69 @@ template <> __device__ __forceinline__ void store_s<__half, float>(__half* p, fl
 //   E = u_x B_y - u_y B_x.
 template <typename C>
 __device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const StepParams<C>& p) {
-    const C one = C(1), half = C(0.5), three = C(3), four5 = C(4.5), one5 = C(1.5);
-    const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w5 = C(1.0 / 36.0);
-    const C W0 = C(1.0 / 3.0), W1 = C(1.0 / 6.0);
+    const C half = C(0.5), three = C(3), four5 = C(4.5), one5 = C(1.5);
 
     // a3: moments
     const C drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    const C rho = one + drho;
+    const C rho = C(1) + drho;
     const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const C inv_rho = one / rho;
+    const C inv_rho = recip(rho);
     const C ux = (jx + half * p.Fx) * inv_rho;
     const C uy = jy * inv_rho;
     const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
     const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
     const C by = p.B0 + dby;
 
-    // a4: equilibria.  Magnetic part with q = B_y^2 - B0^2 = dby (2 B0 + dby):
-    //   a=1,3: (q - Bx^2)/2   a=2,4: (Bx^2 - q)/2   a=5,7: -2 Bx By   a=6,8: +2 Bx By
+    // a4-a5 for f.  Post-collision deviation:
+    //   f' = (1 - w) f + w f^eq,dev + (1 - 1/(2 tau)) S
+    //   f^eq,dev_a = w_a (drho + rho bm1_a) + M_a,  bm1_a = 3 eu + 4.5 eu^2 - 1.5 u^2
+    //   S_a = 3 (e_ax - u_x) F_x w_a (1 + bm1_a)
+    // Maxwell-stress part M_a with q = B_y^2 - B0^2 = dby (2 B0 + dby):
+    //   a=1,3: 2.25 w1 (q - Bx^2)   a=2,4: -2.25 w1 (q - Bx^2)   a=5,7: -9 w5 Bx By   a=6,8: +9 w5 Bx By
     const C q = dby * (p.B0 + by);
-    const C bx2 = bx * bx;
-    const C m13 = four5 * w1 * half * (q - bx2);
-    const C m24 = -m13;
-    const C mxy = four5 * w5 * C(2) * bx * by;
+    const C om13 = p.owf1 * (C(2.25) * (q - bx * bx));   // omega * M_1 = omega * M_3 = -omega * M_2
+    const C omxy = p.owf5 * (C(9) * bx * by);            // omega * M_6 = omega * M_8 = -omega * M_5
     const C usq = one5 * (ux * ux + uy * uy);
-
-    const C omega = p.omega_f, sc = p.src_coef * three * p.Fx;
-    // per direction: bm1 = 3 eu + 4.5 eu^2 - 1.5 u^2, so f^eq,hyd = w rho (1 + bm1) and its
-    // deviation from the rest state is w (drho + rho bm1); bm1 is formed without the leading 1
-    // so that FP32 keeps its relative precision.
-#define LKS_DIR(A, EXA, EU, W, MAG)                                                     \
+    const C s0 = p.sw0 * (-ux);                            // source prefactors per e_x and weight
+    const C s1p = p.sw1 * (C(1) - ux), s1z = p.sw1 * (-ux), s1m = p.sw1 * (C(-1) - ux);
+    const C s5p = p.sw5 * (C(1) - ux), s5m = p.sw5 * (C(-1) - ux);
+    const C om1 = p.om1f;
+#define LKS_DIR(A, EU, OW, OMAG, SA)                                                    \
     {                                                                                   \
         const C eu = (EU);                                                              \
-        const C bm1 = three * eu + four5 * eu * eu - usq;                               \
-        const C feq = (W) * (drho + rho * bm1) + (MAG);                                 \
-        const C S = (W) * (C(EXA) - ux) * (one + bm1);                                  \
-        f[A] = f[A] - omega * (f[A] - feq) + sc * S;                                    \
+        const C bm1 = (three + four5 * eu) * eu - usq;                                  \
+        const C ofeq = (OW) * (drho + rho * bm1) + (OMAG);                              \
+        const C src = (SA) + (SA) * bm1;                                                \
+        f[A] = om1 * f[A] + (ofeq + src);                                               \
     }
-    LKS_DIR(0, 0, C(0), w0, C(0))
-    LKS_DIR(1, 1, ux, w1, m13)
-    LKS_DIR(2, 0, uy, w1, m24)
-    LKS_DIR(3, -1, -ux, w1, m13)
-    LKS_DIR(4, 0, -uy, w1, m24)
-    LKS_DIR(5, 1, ux + uy, w5, -mxy)
-    LKS_DIR(6, -1, uy - ux, w5, mxy)
-    LKS_DIR(7, -1, -ux - uy, w5, -mxy)
-    LKS_DIR(8, 1, ux - uy, w5, mxy)
+    LKS_DIR(0, C(0), p.owf0, C(0), s0)
+    LKS_DIR(1, ux, p.owf1, om13, s1p)
+    LKS_DIR(2, uy, p.owf1, -om13, s1z)
+    LKS_DIR(3, -ux, p.owf1, om13, s1m)
+    LKS_DIR(4, -uy, p.owf1, -om13, s1z)
+    LKS_DIR(5, ux + uy, p.owf5, -omxy, s5p)
+    LKS_DIR(6, uy - ux, p.owf5, omxy, s5m)
+    LKS_DIR(7, -ux - uy, p.owf5, -omxy, s5m)
+    LKS_DIR(8, ux - uy, p.owf5, omxy, s5p)
 #undef LKS_DIR
 
-    // a5 for g (Eq. LKSformagneticfield)
-    const C E3 = three * (ux * by - uy * bx);
-    const C om = p.omega_m;
-    gx[0] = gx[0] - om * (gx[0] - W0 * bx);
-    gx[1] = gx[1] - om * (gx[1] - W1 * bx);
-    gx[2] = gx[2] - om * (gx[2] - W1 * (bx - E3));
-    gx[3] = gx[3] - om * (gx[3] - W1 * bx);
-    gx[4] = gx[4] - om * (gx[4] - W1 * (bx + E3));
-    gy[0] = gy[0] - om * (gy[0] - W0 * dby);
-    gy[1] = gy[1] - om * (gy[1] - W1 * (dby + E3));
-    gy[2] = gy[2] - om * (gy[2] - W1 * dby);
-    gy[3] = gy[3] - om * (gy[3] - W1 * (dby - E3));
-    gy[4] = gy[4] - om * (gy[4] - W1 * dby);
+    // a4-a5 for g (Eqs. geqmagneticfield, LKSformagneticfield): g' = (1 - w_m) g + w_m g^eq,dev with
+    //   g^eq_x = W (Bx - 3 e_y E),  g^eq,dev_y = W (dBy + 3 e_x E),  E = u_x B_y - u_y B_x.
+    const C om1m = p.om1m;
+    const C ce = p.owm1 * (three * (ux * by - uy * bx));
+    const C cb0 = p.owm0 * bx, cb1 = p.owm1 * bx;
+    const C cd0 = p.owm0 * dby, cd1 = p.owm1 * dby;
+    gx[0] = om1m * gx[0] + cb0;
+    gx[1] = om1m * gx[1] + cb1;
+    gx[2] = om1m * gx[2] + (cb1 - ce);
+    gx[3] = om1m * gx[3] + cb1;
+    gx[4] = om1m * gx[4] + (cb1 + ce);
+    gy[0] = om1m * gy[0] + cd0;
+    gy[1] = om1m * gy[1] + (cd1 + ce);
+    gy[2] = om1m * gy[2] + cd1;
+    gy[3] = om1m * gy[3] + (cd1 - ce);
+    gy[4] = om1m * gy[4] + cd1;
 }
 
 // Moment-based closures at a wet wall node (Sec. VII, App. A, App. B.2), deviation form.
@@ -183,10 +202,9 @@ __device__ __forceinline__ void moment_closure_top(C f[9], C gx[5], C gy[5], con
 // link-based wall rows take the unknown incoming populations from the same node's outgoing ones
 // (Sec. VI, App. B.1), which nobody else reads; moment-based wall rows reconstruct them from the
 // pulled ones (Sec. VII, App. A, App. B.2).
-template <typename S, typename C, int CLOSURE, bool RO>
-__device__ __forceinline__ void step_node(const S* fin, const S* gin, S* fout, S* gout, const StepParams<C>& p,
-                                          int64_t n) {
-    typedef Loader<S, C, RO> L;
+template <typename S, typename C, int CLOSURE, typename L>
+__device__ __forceinline__ void step_node_with(const S* fin, const S* gin, S* fout, S* gout, const StepParams<C>& p,
+                                               int64_t n) {
     const int nx = p.nx;
     const int j = (int)(n / nx);
     const int i = (int)(n - (int64_t)j * nx);
@@ -259,6 +277,13 @@ __device__ __forceinline__ void step_node(const S* fin, const S* gin, S* fout, S
     for (int a = 0; a < 5; ++a) store_s<S, C>(gxo + a * N + n, gx[a]);
 #pragma unroll
     for (int a = 0; a < 5; ++a) store_s<S, C>(gyo + a * N + n, gy[a]);
+}
+
+// step_node with the read-only loads (RO) or plain coherent loads.
+template <typename S, typename C, int CLOSURE, bool RO>
+__device__ __forceinline__ void step_node(const S* fin, const S* gin, S* fout, S* gout, const StepParams<C>& p,
+                                          int64_t n) {
+    step_node_with<S, C, CLOSURE, Loader<S, C, RO>>(fin, gin, fout, gout, p, n);
 }
 
 }  // namespace lks

@@ -19,6 +19,16 @@ inline StepParams<C> convert_params(const StepParams<double>& d) {
     o.src_coef = (C)d.src_coef;
     o.Fx = (C)d.Fx;
     o.B0 = (C)d.B0;
+    o.om1f = (C)d.om1f;
+    o.om1m = (C)d.om1m;
+    o.owf0 = (C)d.owf0;
+    o.owf1 = (C)d.owf1;
+    o.owf5 = (C)d.owf5;
+    o.owm0 = (C)d.owm0;
+    o.owm1 = (C)d.owm1;
+    o.sw0 = (C)d.sw0;
+    o.sw1 = (C)d.sw1;
+    o.sw5 = (C)d.sw5;
     const WallCoef<double>* src[2] = {&d.bot, &d.top};
     WallCoef<C>* dst[2] = {&o.bot, &o.top};
     for (int k = 0; k < 2; ++k) {

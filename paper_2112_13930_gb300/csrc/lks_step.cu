@@ -23,6 +23,173 @@ __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ fin, co
     step_node<S, C, CLOSURE, true>(fin, gin, fout, gout, p, n);
 }
 
+// 16-bit storage moves 2 bytes per population, so the one-node kernel issues twice the load/store
+// instructions per byte of the FP32 one and becomes instruction-bound.  This variant gives each
+// thread the two nodes (x0, x0+1), x0 even, and moves every population plane as one 32-bit word
+// holding both nodes (nx must be even).  A pull from x-1 needs (x0-1, x0): the word of the lane to
+// the left supplies x0-1 through a warp shuffle (a direct 16-bit load at a warp or row edge,
+// wrapping periodically); a pull from x+1 needs (x0+1, x0+2) likewise from the lane to the right.
+// Per node the arithmetic is exactly that of step_node, so results are bit-identical to it.
+template <typename S>
+struct Packed;
+template <>
+struct Packed<__nv_bfloat16> {
+    static __device__ __forceinline__ float lo(uint32_t w) { return __uint_as_float(w << 16); }
+    static __device__ __forceinline__ float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&v);
+    }
+};
+template <>
+struct Packed<__half> {
+    static __device__ __forceinline__ float lo(uint32_t w) {
+        return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
+    }
+    static __device__ __forceinline__ float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
+    static __device__ __forceinline__ uint32_t pack(float a, float b) {
+        __half2 v = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&v);
+    }
+};
+
+template <typename S, int CLOSURE>
+__global__ void __launch_bounds__(256) step_kernel_pair(const S* __restrict__ fin, const S* __restrict__ gin,
+                                                        S* __restrict__ fout, S* __restrict__ gout,
+                                                        const StepParams<float> p) {
+    typedef Packed<S> P;
+    const unsigned FULL = 0xffffffffu;
+    const int nx = p.nx, npr = nx >> 1;
+    const int64_t N = p.N, NP = N >> 1;
+    const int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = q0 < NP;
+    const int64_t q = active ? q0 : NP - 1;      // inactive lanes still take part in the shuffles
+    const int lane = threadIdx.x & 31;
+    const int j = (int)(q / npr);
+    const int ip = (int)(q - (int64_t)j * npr);
+    const int x0 = ip << 1;
+    const int64_t rc = (int64_t)j * npr;         // row starts, in pairs
+    const int64_t rs = rc - npr, rn = rc + npr;
+    const bool bottom = (j == 0), top = (j == p.ny - 1);
+    const bool left_edge = (lane == 0) || (ip == 0);
+    const bool right_edge = (lane == 31) || (ip == npr - 1);
+    const int xm = (x0 == 0) ? nx - 1 : x0 - 1;  // element pulled by node x0 from the left
+    const int xp = (x0 + 2 == nx) ? 0 : x0 + 2;  // element pulled by node x0+1 from the right
+
+    const uint32_t* fw = reinterpret_cast<const uint32_t*>(fin);
+    const uint32_t* gw = reinterpret_cast<const uint32_t*>(gin);
+    // word of plane `a` (of NP words) at pair row r
+    auto W = [&](const uint32_t* base, int a, int64_t r) -> uint32_t { return __ldg(base + a * NP + r + ip); };
+    // single element of plane `a` at element row re (= row * nx), column x
+    auto E = [&](const S* base, int a, int64_t re, int x) -> float { return load_s<S, float>(base + a * N + re + x); };
+
+    float fA[9], fB[9], gxA[5], gxB[5], gyA[5], gyB[5];
+    const S* gxs = gin;
+    const S* gys = gin + 5 * N;
+    const uint32_t* gxw = gw;
+    const uint32_t* gyw = gw + 5 * NP;
+
+    // pull from x-1 in plane a of source pair row r (element row re): node A <- x0-1, node B <- x0
+    auto pull_left = [&](const uint32_t* base, const S* ebase, int a, int64_t r, int64_t re, bool valid, float& A,
+                         float& B) {
+        const uint32_t w = valid ? W(base, a, r) : 0u;
+        const uint32_t wl = __shfl_up_sync(FULL, w, 1);
+        B = P::lo(w);
+        A = P::hi(wl);
+        if (valid && left_edge) A = E(ebase, a, re, xm);
+    };
+    // pull from x+1: node A <- x0+1, node B <- x0+2
+    auto pull_right = [&](const uint32_t* base, const S* ebase, int a, int64_t r, int64_t re, bool valid, float& A,
+                          float& B) {
+        const uint32_t w = valid ? W(base, a, r) : 0u;
+        const uint32_t wr = __shfl_down_sync(FULL, w, 1);
+        A = P::hi(w);
+        B = P::lo(wr);
+        if (valid && right_edge) B = E(ebase, a, re, xp);
+    };
+    auto pull_same = [&](const uint32_t* base, int a, int64_t r, bool valid, float& A, float& B) {
+        const uint32_t w = valid ? W(base, a, r) : 0u;
+        A = P::lo(w);
+        B = P::hi(w);
+    };
+    const int64_t ec = (int64_t)j * nx, es = ec - nx, en = ec + nx;   // element row starts
+    // a1: pull-stream (rows y-1 / y / y+1), periodic in x
+    pull_same(fw, 0, rc, true, fA[0], fB[0]);
+    pull_left(fw, fin, 1, rc, ec, true, fA[1], fB[1]);
+    pull_right(fw, fin, 3, rc, ec, true, fA[3], fB[3]);
+    pull_same(fw, 2, rs, !bottom, fA[2], fB[2]);
+    pull_left(fw, fin, 5, rs, es, !bottom, fA[5], fB[5]);
+    pull_right(fw, fin, 6, rs, es, !bottom, fA[6], fB[6]);
+    pull_same(fw, 4, rn, !top, fA[4], fB[4]);
+    pull_right(fw, fin, 7, rn, en, !top, fA[7], fB[7]);
+    pull_left(fw, fin, 8, rn, en, !top, fA[8], fB[8]);
+    pull_same(gxw, 0, rc, true, gxA[0], gxB[0]);
+    pull_left(gxw, gxs, 1, rc, ec, true, gxA[1], gxB[1]);
+    pull_right(gxw, gxs, 3, rc, ec, true, gxA[3], gxB[3]);
+    pull_same(gxw, 2, rs, !bottom, gxA[2], gxB[2]);
+    pull_same(gxw, 4, rn, !top, gxA[4], gxB[4]);
+    pull_same(gyw, 0, rc, true, gyA[0], gyB[0]);
+    pull_left(gyw, gys, 1, rc, ec, true, gyA[1], gyB[1]);
+    pull_right(gyw, gys, 3, rc, ec, true, gyA[3], gyB[3]);
+    pull_same(gyw, 2, rs, !bottom, gyA[2], gyB[2]);
+    pull_same(gyw, 4, rn, !top, gyA[4], gyB[4]);
+    // a2: wall closures
+    if (CLOSURE == 0) {
+        if (bottom) {
+            const WallCoef<float>& w = p.bot;
+            float a, b;
+            pull_same(fw, 4, rc, true, a, b); fA[2] = a; fB[2] = b;
+            pull_same(fw, 7, rc, true, a, b); fA[5] = a + w.du; fB[5] = b + w.du;
+            pull_same(fw, 8, rc, true, a, b); fA[6] = a - w.du; fB[6] = b - w.du;
+            pull_same(gxw, 4, rc, true, a, b); gxA[2] = w.r * a + w.kx; gxB[2] = w.r * b + w.kx;
+            pull_same(gyw, 4, rc, true, a, b); gyA[2] = -a; gyB[2] = -b;
+        }
+        if (top) {
+            const WallCoef<float>& w = p.top;
+            float a, b;
+            pull_same(fw, 2, rc, true, a, b); fA[4] = a; fB[4] = b;
+            pull_same(fw, 5, rc, true, a, b); fA[7] = a - w.du; fB[7] = b - w.du;
+            pull_same(fw, 6, rc, true, a, b); fA[8] = a + w.du; fB[8] = b + w.du;
+            pull_same(gxw, 2, rc, true, a, b); gxA[4] = w.r * a + w.kx; gxB[4] = w.r * b + w.kx;
+            pull_same(gyw, 2, rc, true, a, b); gyA[4] = -a; gyB[4] = -b;
+        }
+    } else {
+        if (bottom) {
+            moment_closure_bottom<float>(fA, gxA, gyA, p.bot, p.B0);
+            moment_closure_bottom<float>(fB, gxB, gyB, p.bot, p.B0);
+        }
+        if (top) {
+            moment_closure_top<float>(fA, gxA, gyA, p.top, p.B0);
+            moment_closure_top<float>(fB, gxB, gyB, p.top, p.B0);
+        }
+    }
+    // a3-a5
+    collide_node<float>(fA, gxA, gyA, p);
+    collide_node<float>(fB, gxB, gyB, p);
+    // a6: store both nodes of each plane as one word
+    if (!active) return;
+    uint32_t* fo = reinterpret_cast<uint32_t*>(fout);
+    uint32_t* go = reinterpret_cast<uint32_t*>(gout);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) fo[a * NP + q] = P::pack(fA[a], fB[a]);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) go[a * NP + q] = P::pack(gxA[a], gxB[a]);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) go[(5 + a) * NP + q] = P::pack(gyA[a], gyB[a]);
+}
+
+template <typename S>
+static cudaError_t launch_pair(const void* fin, const void* gin, void* fout, void* gout, const StepParams<float>& p,
+                               int closure, cudaStream_t st) {
+    const int threads = 256;
+    const int64_t blocks = (p.N / 2 + threads - 1) / threads;
+    if (closure == 0)
+        step_kernel_pair<S, 0><<<(unsigned)blocks, threads, 0, st>>>((const S*)fin, (const S*)gin, (S*)fout, (S*)gout, p);
+    else
+        step_kernel_pair<S, 1><<<(unsigned)blocks, threads, 0, st>>>((const S*)fin, (const S*)gin, (S*)fout, (S*)gout, p);
+    return cudaGetLastError();
+}
+
 template <typename S, typename C>
 static cudaError_t launch_typed(const void* fin, const void* gin, void* fout, void* gout, const StepParams<C>& p,
                                 int closure, cudaStream_t st) {
@@ -42,8 +209,12 @@ cudaError_t launch_step(int storage, int closure, const void* fin, const void* g
     if (storage == 0) return launch_typed<double, double>(fin, gin, fout, gout, pd, closure, st);
     StepParams<float> pf = convert_params<float>(pd);
     if (storage == 1) return launch_typed<float, float>(fin, gin, fout, gout, pf, closure, st);
-    if (storage == 2) return launch_typed<__nv_bfloat16, float>(fin, gin, fout, gout, pf, closure, st);
-    return launch_typed<__half, float>(fin, gin, fout, gout, pf, closure, st);
+    const bool pairs = (pd.nx % 2) == 0;  // two nodes per thread need whole pairs in every row
+    if (storage == 2)
+        return pairs ? launch_pair<__nv_bfloat16>(fin, gin, fout, gout, pf, closure, st)
+                     : launch_typed<__nv_bfloat16, float>(fin, gin, fout, gout, pf, closure, st);
+    return pairs ? launch_pair<__half>(fin, gin, fout, gout, pf, closure, st)
+                 : launch_typed<__half, float>(fin, gin, fout, gout, pf, closure, st);
 }
 
 }  // namespace lks

@@ -80,7 +80,8 @@ def run_batched(specs, storage="f32", tol=1e-10, check_every=100, quantum=20000,
         eu, eb = analytic_error(spec, u, bx)
         recs.append({"index": spec["index"], "ny": spec["ny"], "ha": spec["ha"], "c": spec["c"], "kind": spec["kind"],
                      "state": _batch.STATE_NAMES[st], "steps": int(steps), "residual": r,
-                     "t_done": done_at[k], "l2_u": eu, "l2_b": eb, "nodes": spec["nx"] * spec["ny"]})
+                     "t_done": done_at[k], "l2_u": eu, "l2_b": eb, "nodes": spec["nx"] * spec["ny"],
+                     "u": u, "b": bx})
     b.close()
     return {"records": recs, "wall": wall, "launches": launches, "tune": tune}
 
@@ -104,5 +105,5 @@ def run_one_at_a_time(specs, storage="f64", tol=1e-10, check_every=100, max_step
         te = time.perf_counter()
         eu, eb = analytic_error(spec, u, bx)
         recs.append({"index": spec["index"], "steps": int(steps), "residual": r, "status": int(status),
-                     "solve_s": te - ts, "t_done": te - t0, "l2_u": eu, "l2_b": eb})
+                     "solve_s": te - ts, "t_done": te - t0, "l2_u": eu, "l2_b": eb, "u": u, "b": bx})
     return {"records": recs, "wall": time.perf_counter() - t0}

@@ -56,6 +56,12 @@ def test_instance_footprint_and_batch_config_validation(lib):
     assert lib.lks_batch_create(ctypes.byref(cfg), ctypes.byref(h)) == lks.LKS_EINVAL and not h.value
     cfg = batch.BatchConfig(storage=1, max_instances=4, pool_bytes=1 << 20, threads_per_group=256, groups_per_cta=4)
     assert lib.lks_batch_create(ctypes.byref(cfg), ctypes.byref(h)) == lks.LKS_EINVAL
+    cfg = batch.BatchConfig(storage=1, max_instances=4, pool_bytes=1 << 20, threads_per_group=128, groups_per_cta=2,
+                            cluster_ctas=2)
+    assert lib.lks_batch_create(ctypes.byref(cfg), ctypes.byref(h)) == lks.LKS_EINVAL
+    cfg = batch.BatchConfig(storage=1, max_instances=4, pool_bytes=1 << 20, threads_per_group=128, groups_per_cta=1,
+                            cluster_ctas=3)
+    assert lib.lks_batch_create(ctypes.byref(cfg), ctypes.byref(h)) == lks.LKS_EINVAL
     assert lib.lks_batch_destroy(None) == lks.LKS_OK
 
 

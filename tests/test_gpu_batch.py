@@ -51,9 +51,11 @@ def _oracle_for(d):
                          d.u_top, seed=d.seed, perturb_amp=d.perturb_amp)
 
 
-def test_batch_fp64_matches_oracle(mods):
+@pytest.mark.parametrize("shape", [(128, 2, 1), (128, 1, 4)])
+def test_batch_fp64_matches_oracle(mods, shape):
     lks, batch = mods
-    b = batch.Batch("f64", max_instances=16, pool_bytes=64 << 20, threads_per_group=128, groups_per_cta=2)
+    b = batch.Batch("f64", max_instances=16, pool_bytes=64 << 20, threads_per_group=shape[0], groups_per_cta=shape[1],
+                    cluster_ctas=shape[2])
     descs = _descs(batch)
     slots = [b.add(d) for d in descs]
     for q in (7, 93):
@@ -70,10 +72,13 @@ def test_batch_fp64_matches_oracle(mods):
     b.close()
 
 
-def test_batch_matches_single_lattice_bitwise(mods):
-    """Same device update as lks_step: FP32 batch instances equal single-lattice runs bit for bit."""
+@pytest.mark.parametrize("shape", [(64, 4, 1), (128, 1, 2), (64, 1, 8)])
+def test_batch_matches_single_lattice_bitwise(mods, shape):
+    """Same device update as lks_step: FP32 batch instances equal single-lattice runs bit for bit,
+    with groups inside a CTA and with thread-block clusters spanning 2 or 8 SMs."""
     lks, batch = mods
-    b = batch.Batch("f32", max_instances=16, pool_bytes=64 << 20, threads_per_group=64, groups_per_cta=4)
+    b = batch.Batch("f32", max_instances=16, pool_bytes=64 << 20, threads_per_group=shape[0],
+                    groups_per_cta=shape[1], cluster_ctas=shape[2])
     descs = _descs(batch)
     slots = [b.add(d) for d in descs]
     b.run(250)
@@ -87,16 +92,20 @@ def test_batch_matches_single_lattice_bitwise(mods):
     b.close()
 
 
-def test_alone_equals_in_the_mix(mods):
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_alone_equals_in_the_mix(mods, cluster):
     """Each instance's result is the same alone and in a mixed batch (bitwise, same group size)."""
     lks, batch = mods
     descs = _descs(batch, n=8, tol=1e-9, check_every=100, max_steps=3000)
-    mix = batch.Batch("f32", max_instances=16, pool_bytes=64 << 20, threads_per_group=128, groups_per_cta=2)
+    g = 2 if cluster == 1 else 1
+    mix = batch.Batch("f32", max_instances=16, pool_bytes=64 << 20, threads_per_group=128, groups_per_cta=g,
+                      cluster_ctas=cluster)
     slots = [mix.add(d) for d in descs]
     while mix.run(700):
         pass
     for d, s in zip(descs, slots):
-        alone = batch.Batch("f32", max_instances=1, pool_bytes=8 << 20, threads_per_group=128, groups_per_cta=1)
+        alone = batch.Batch("f32", max_instances=1, pool_bytes=8 << 20, threads_per_group=128, groups_per_cta=1,
+                            cluster_ctas=cluster)
         a = alone.add(d)
         while alone.run(300):
             pass
@@ -169,8 +178,9 @@ def test_autotune_leaves_states_untouched(mods):
     ts = [tun.add(d) for d in descs]
     ref.run(100)
     tun.run(100)
-    best, secs = tun.autotune([(64, 2), (128, 1), (256, 1), (32, 8)], probe_steps=50)
-    assert len(secs) == 4 and all(s > 0 for s in secs)
+    best, secs = tun.autotune([(64, 2, 1), (128, 1, 1), (256, 1, 1), (32, 8, 1), (128, 1, 4), (64, 1, 8)],
+                              probe_steps=50)
+    assert len(secs) == 6 and all(s > 0 for s in secs)
     tun.set_shape(128, 1)
     ref.run(100)
     tun.run(100)

@@ -244,3 +244,39 @@ def test_full_size_perturbed_fp64_sampled_rows(lks):
     for m in (1, 2, 3):
         assert _relmax(mg[m][rows], mo[m][rows]) <= REL64
     g.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("closure", ["link", "moment"])
+def test_pair_kernel_bitwise_equals_single_node_kernel(lks, storage, closure):
+    """16-bit storage with even nx runs the two-nodes-per-thread kernel, odd nx the one-node kernel.
+    On an x-independent flow (rest start, body force and moving wall) every column of both must be
+    bit-identical: the per-node arithmetic is the same."""
+    out = []
+    for nx in (37, 38, 64):
+        g = lks.Lattice(nx, 21, 0.7, 0.9, 0.02, 2e-5, closure, storage)
+        g.set_walls(0.4, math.inf, 0.0, 0.04)
+        g.step(150)
+        f, gg = g.get_state()
+        for a in range(9):
+            assert np.all(f[a] == f[a][:, :1])
+        out.append((f[:, :, 0].copy(), gg[:, :, :, 0].copy()))
+        g.close()
+    for f, gg in out[1:]:
+        assert np.array_equal(f, out[0][0]) and np.array_equal(gg, out[0][1])
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_pair_kernel_perturbed_matches_oracle_one_step(lks, storage):
+    """Perturbed lattice with even nx spanning several warps and rows that do not fill a warp:
+    one step against the oracle within the one-step bound of the storage type."""
+    for nx, ny in ((38, 7), (130, 5), (2, 9)):
+        o, g = _pair(lks, nx, ny, "moment", storage, B0=0.02, Fx=1e-5, c=(0.4, 3.0), u=(0.0, 0.04), seed=3,
+                     amp=1e-2)
+        o0 = oracle.Oracle(nx, ny, 0.8, 0.8, 0.02, 1e-5, oracle.MOMENT)
+        o.step(1)
+        g.step(1)
+        fg, gg = g.get_state()
+        assert np.max(np.abs(fg - o.f)) <= 8 * ONE_STEP[storage] * np.max(np.abs(o.f - o0.f))
+        assert np.max(np.abs(gg - o.g)) <= 8 * ONE_STEP[storage] * np.max(np.abs(o.g - o0.g))
+        g.close()
