@@ -168,6 +168,29 @@ lks_status lks_destroy(lks_handle* h);
  * handle-less error).  Never NULL. */
 const char* lks_last_error(const lks_handle* h);
 
+/* Steady-state residual of a state held in caller memory, computed with no allocation of any
+ * kind.  (The paper has no counterpart: this is a variant of the lks_residual reduction for
+ * callers that cannot allocate device memory -- applications that reserve the whole device for
+ * their own pools, latency-critical loops where cudaMalloc/cudaFree may synchronise the device,
+ * plugin hosts that forbid allocation calls.)
+ *   f, g      device pointers to one lattice's populations in the layout above (deviation form,
+ *             storage type `storage`), nx x ny nodes; read only.
+ *   snap      device pointer to 2*nx*ny doubles: u_x then B_x per node of the previous call; the
+ *             residual compares against it and overwrites it with the current values.
+ *   out       host pointer to 2 doubles: r_u, r_b as defined for lks_residual.
+ *   B0, Fx    the lattice's applied field and body force (needed for B_y and u_x).
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream); synchronised on return.
+ * The partial sums live in a file-scope device array of 4*1216 + 8 doubles (38.9 KB) that every
+ * GPU which loads the library keeps until the process exits.  Lattices above 2^30 nodes are
+ * rejected with LKS_EINVAL and a message naming the limit.  The first call on each device looks
+ * up the array's device address (with that device current); make that first call before any
+ * stream capture.  All calls share the one array: calls that overlap on the GPU (other streams,
+ * other threads) race on it and must be serialised by the caller.  Nothing from a previous call
+ * needs clearing: each call writes every slot it reads.  Errors: LKS_EINVAL, LKS_ECUDA,
+ * LKS_EUNSTABLE (non-finite moments); lks_last_error(NULL) gives the message. */
+lks_status lks_residual_noalloc(const void* f, const void* g, int32_t storage, int32_t nx, int32_t ny, double B0,
+                                double Fx, double* snap, double* out, void* cuda_stream);
+
 /* Static name of a status code. */
 const char* lks_status_string(lks_status s);
 

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -486,3 +487,73 @@ const char* lks_status_string(lks_status s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// lks_residual_noalloc: the steady-state residual of caller-held state with no allocation at all.
+//
+// Some callers cannot allocate device memory: applications that reserve the whole device for their
+// own pools up front, latency-critical loops in which cudaMalloc/cudaFree (which may synchronise
+// the whole device) are not acceptable, and plugin hosts that forbid allocation calls.  This entry
+// point runs the same two-pass residual reduction as lks_residual, but its partial sums live in
+// the file-scope device array below instead of memory it would have to allocate.  The array holds
+// 4 * kNoallocMaxBlocks partial sums plus 4 totals (38.9 KB) and stays allocated on every device
+// that loads the library until the process exits.  The reduction never uses more than
+// kNoallocMaxBlocks blocks, so any lattice up to the 2^30-node limit fits; larger ones are rejected.
+namespace {
+
+constexpr int kNoallocMaxBlocks = 1216;                // the largest value residual_blocks() returns
+constexpr int kNoallocScratch = 4 * kNoallocMaxBlocks + 8;
+constexpr int kNoallocMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratch];
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device: looked up once per device (host code
+// only sees a host-side stand-in for the array's name).
+cudaError_t noalloc_scratch(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        double* p = nullptr;
+        e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" lks_status lks_residual_noalloc(const void* f, const void* g, int32_t storage, int32_t nx, int32_t ny,
+                                           double B0, double Fx, double* snap, double* out, void* cuda_stream) {
+    if (!f || !g || !snap || !out) return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: NULL pointer argument");
+    if (storage < LKS_F64 || storage > LKS_F16_DEV) return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: bad storage");
+    if (nx < 1 || ny < 1) return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: nx and ny must be >= 1");
+    const int64_t N = (int64_t)nx * (int64_t)ny;
+    if (N > ((int64_t)1 << 30))
+        return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: nx*ny exceeds the maximum of 2^30 nodes");
+    if (lks::residual_blocks(N) > kNoallocMaxBlocks)
+        return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: reduction exceeds the static scratch");
+    double* scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lks_residual_noalloc: cudaGetSymbolAddress");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // Every partial and total slot the reduction reads is written earlier in the same call, so
+    // nothing left over from a previous call needs clearing.
+    double* partial = scratch;
+    double* totals = scratch + 4 * kNoallocMaxBlocks;
+    e = lks::launch_residual(storage, f, g, nx, ny, B0, Fx, snap, partial, totals, st);
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s, totals, sizeof(s), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lks_residual_noalloc");
+    for (int k = 0; k < 4; ++k)
+        if (!isfinite(s[k])) return fail(nullptr, LKS_EUNSTABLE, "lks_residual_noalloc: the state is non-finite");
+    out[0] = s[1] > 1e-60 ? sqrt(s[0] / s[1]) : 0.0;
+    out[1] = s[3] > 1e-60 ? sqrt(s[2] / s[3]) : 0.0;
+    return LKS_OK;
+}

@@ -67,6 +67,9 @@ SIGNATURES = {
     "lks_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "lks_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "lks_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lks_residual_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                                            _dp, ctypes.c_void_p]),
 }
 
 _lib = None
