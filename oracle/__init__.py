@@ -32,7 +32,7 @@ class OracleParams(ctypes.Structure):
         ("closure", ctypes.c_int32),
         ("pi20_literal", ctypes.c_int32),
         ("freeze_u", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("coupling", ctypes.c_int32),
         ("tau_f", ctypes.c_double),
         ("tau_m", ctypes.c_double),
         ("B0", ctypes.c_double),
@@ -96,9 +96,9 @@ class Oracle:
     """
 
     def __init__(self, nx, ny, tau_f, tau_m, B0, Fx=0.0, closure=LINK, c_bot=0.0, c_top=0.0,
-                 u_bot=0.0, u_top=0.0, pi20_literal=False, freeze_u=False, seed=0, perturb_amp=0.0):
+                 u_bot=0.0, u_top=0.0, pi20_literal=False, freeze_u=False, seed=0, perturb_amp=0.0, coupling=0):
         self.p = OracleParams(nx=nx, ny=ny, closure=closure, pi20_literal=int(pi20_literal),
-                              freeze_u=int(freeze_u), pad=0, tau_f=tau_f, tau_m=tau_m, B0=B0, Fx=Fx,
+                              freeze_u=int(freeze_u), coupling=int(coupling), tau_f=tau_f, tau_m=tau_m, B0=B0, Fx=Fx,
                               c_bot=c_bot, c_top=c_top, u_bot=u_bot, u_top=u_top)
         self.nx, self.ny = nx, ny
         self.f = np.zeros((9, ny, nx))

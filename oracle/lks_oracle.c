@@ -40,7 +40,13 @@
  *   - the moving-wall constraint of App. B.2 is applied as x-momentum
  *     Pi_10 = rho U_w, y-momentum Pi_01 = 0, which is what the printed closures
  *     satisfy;
- *   - c = +inf is the limit of each closure (no division by c).
+ *   - c = +inf is the limit of each closure (no division by c);
+ *   - coupling = 1 is the paper's own coupling (Sec. V): no magnetic term in
+ *     f^eq, Lorentz force F_L = J x B in the source and in rho u = sum f e + F/2,
+ *     with J_z = (Lambda^(1)_yx - Lambda^(1)_xy)/(tau_m c_sm^2) from the
+ *     non-equilibrium first moment of g (Sec. IV).  Because Lambda^(0) depends on
+ *     u and u on F_L, the two are iterated to a fixed point; the moment-based
+ *     Pi_20 target is then rho (c_s^2 + U^2) as printed.
  *
  * Arrays are structure-of-arrays: f[a*N + j*nx + i], g[(k*5 + a)*N + j*nx + i]
  * with N = nx*ny, k = 0 for the x component and 1 for the y component.
@@ -61,7 +67,7 @@ typedef struct {
     int32_t closure;      /* 0 = link-based (Sec. VI), 1 = moment-based (Sec. VII) */
     int32_t pi20_literal; /* 1 = Pi_20 target rho (c_s^2 + U^2) exactly as printed */
     int32_t freeze_u;     /* 1 = u forced to 0 in g^eq (pure induction-diffusion) */
-    int32_t pad;
+    int32_t coupling;     /* 0 = Maxwell stress in f^eq; 1 = Lorentz-force source (Sec. IV-V) */
     double tau_f, tau_m;  /* relaxation times of f and g */
     double B0;            /* applied field along y */
     double Fx;            /* external body force along x */
@@ -154,7 +160,7 @@ int orc_init(const orc_params* p, uint64_t seed, double amp, double* f, double* 
             uy = amp * (2.0 * splitmix_unit(seed, 2ULL * (uint64_t)n + 1ULL) - 1.0);
         }
         for (int a = 0; a < 9; ++a)
-            f[a * N + n] = feq_hyd(a, 1.0, ux, uy) + feq_mag(a, 0.0, p->B0);
+            f[a * N + n] = feq_hyd(a, 1.0, ux, uy) + (p->coupling == 1 ? 0.0 : feq_mag(a, 0.0, p->B0));
         for (int i = 0; i < 2; ++i)
             for (int a = 0; a < 5; ++a)
                 g[(i * 5 + a) * N + n] = geq(a, i, ux, uy, 0.0, p->B0);
@@ -183,6 +189,9 @@ int orc_step(const orc_params* p, const double* fs, const double* gs, double* fo
     if (nx < 1 || ny < (p->closure == 0 ? 2 : 3)) return 1;
     if (!(p->tau_f > 0.5) || !(p->tau_m > 0.5)) return 1;
     if (!(p->c_bot >= 0.0) || !(p->c_top >= 0.0)) return 1;
+    /* the Lorentz-force coupling reads J back from the stored (post-collision) g, which carries
+     * (1 - 1/tau_m) of the non-equilibrium moment: tau_m must stay away from 1 */
+    if (p->coupling == 1 && fabs(p->tau_m - 1.0) < 0.05) return 1;
     const double a_half = orc_half_width(p);
     double rb, sb, rt, st;
     link_coeffs(p->c_bot, a_half, p->tau_m, &rb, &sb);
@@ -267,21 +276,33 @@ int orc_step(const orc_params* p, const double* fs, const double* gs, double* fo
                     }
                     double bx = 0.0, by = 0.0;
                     for (int a = 0; a < 5; ++a) { bx += g[0][a]; by += g[1][a]; }
+                    /* Momentum targets.  Maxwell-stress coupling: Pi_10 = rho U, Pi_01 = 0 as printed.
+                     * Lorentz-force coupling: the wall node's velocity (Pi + F/2)/rho is set to
+                     * (U, 0), i.e. Pi_10 = rho U - F_x/2, Pi_01 = -F_y/2, with F = F_ext + J x B and
+                     * J_z from the closed g at u = (U, 0). */
+                    double hfx = 0.0, hfy = 0.0;
+                    if (p->coupling == 1) {
+                        const double lyx = g[0][2] - g[0][4], lxy = g[1][1] - g[1][3];
+                        const double l0yx = -by * uw, l0xy = uw * by;
+                        const double jz = ((lyx - l0yx) - (lxy - l0xy)) / (p->tau_m * CS2);
+                        hfx = 0.5 * (p->Fx - jz * by);
+                        hfy = 0.5 * (jz * bx);
+                    }
                     if (bottom) {
-                        /* App. A: rho_b from Pi_00 and Pi_01 = 0 */
-                        double rho = f[0] + f[1] + f[3] + 2.0 * (f[4] + f[7] + f[8]);
+                        /* App. A: rho_b from Pi_00 and Pi_01 */
+                        double rho = f[0] + f[1] + f[3] + 2.0 * (f[4] + f[7] + f[8]) - hfy;
                         double P = rho * (CS2 + uw * uw);
-                        if (!p->pi20_literal) P += 0.5 * (by * by - bx * bx);
-                        f[2] = -P + f[1] + f[3] + f[4] + 2.0 * (f[7] + f[8]);
-                        f[5] = 0.5 * (P + rho * uw) - (f[1] + f[8]);
-                        f[6] = 0.5 * (P - rho * uw) - (f[3] + f[7]);
+                        if (!p->pi20_literal && p->coupling == 0) P += 0.5 * (by * by - bx * bx);
+                        f[2] = -P + f[1] + f[3] + f[4] + 2.0 * (f[7] + f[8]) - hfy;
+                        f[5] = 0.5 * (P + rho * uw - hfx) - (f[1] + f[8]);
+                        f[6] = 0.5 * (P - rho * uw + hfx) - (f[3] + f[7]);
                     } else {
-                        double rho = f[0] + f[1] + f[3] + 2.0 * (f[2] + f[5] + f[6]);
+                        double rho = f[0] + f[1] + f[3] + 2.0 * (f[2] + f[5] + f[6]) + hfy;
                         double P = rho * (CS2 + uw * uw);
-                        if (!p->pi20_literal) P += 0.5 * (by * by - bx * bx);
-                        f[4] = -P + f[1] + f[2] + f[3] + 2.0 * (f[5] + f[6]);
-                        f[7] = 0.5 * (P - rho * uw) - (f[3] + f[6]);
-                        f[8] = 0.5 * (P + rho * uw) - (f[1] + f[5]);
+                        if (!p->pi20_literal && p->coupling == 0) P += 0.5 * (by * by - bx * bx);
+                        f[4] = -P + f[1] + f[2] + f[3] + 2.0 * (f[5] + f[6]) + hfy;
+                        f[7] = 0.5 * (P - rho * uw + hfx) - (f[3] + f[6]);
+                        f[8] = 0.5 * (P + rho * uw - hfx) - (f[1] + f[5]);
                     }
                 }
                 if (fpre) for (int a = 0; a < 9; ++a) fpre[a * N + n] = f[a];
@@ -296,8 +317,26 @@ int orc_step(const orc_params* p, const double* fs, const double* gs, double* fo
                     my += f[a] * EY9[a];
                 }
                 for (int a = 0; a < 5; ++a) { bx += g[0][a]; by += g[1][a]; }
-                const double Fx = p->Fx, Fy = 0.0;
+                double Fx = p->Fx, Fy = 0.0;
                 double ux = (mx + 0.5 * Fx) / rho, uy = (my + 0.5 * Fy) / rho;
+                if (p->coupling == 1) {
+                    /* Lambda_ji = sum_a e_aj g_ai (Sec. IV): Lambda_yx and Lambda_xy */
+                    const double lyx = g[0][2] - g[0][4], lxy = g[1][1] - g[1][3];
+                    for (int it = 0; it < 100; ++it) {
+                        /* Lambda^(0)_ji = u_j B_i - B_j u_i (Eq. rank2antisymmtensoreq) */
+                        const double l0yx = uy * bx - by * ux, l0xy = ux * by - bx * uy;
+                        /* J_z = -(1/(tau_m c_sm^2)) eps_zjk Lambda^(1)_jk */
+                        const double jz = ((lyx - l0yx) - (lxy - l0xy)) / (p->tau_m * CS2);
+                        /* F = J x B + F_ext with J = (0, 0, J_z), B = (B_x, B_y, 0) */
+                        Fx = p->Fx - jz * by;
+                        Fy = jz * bx;
+                        const double nux = (mx + 0.5 * Fx) / rho, nuy = (my + 0.5 * Fy) / rho;
+                        const double d = fabs(nux - ux) + fabs(nuy - uy);
+                        ux = nux;
+                        uy = nuy;
+                        if (d <= 1e-17 * (fabs(ux) + fabs(uy)) || d == 0.0) break;
+                    }
+                }
                 if (mom) {
                     mom[0 * N + n] = rho; mom[1 * N + n] = ux; mom[2 * N + n] = uy;
                     mom[3 * N + n] = bx; mom[4 * N + n] = by;
@@ -305,7 +344,7 @@ int orc_step(const orc_params* p, const double* fs, const double* gs, double* fo
                 /* 4./5. Equilibria, source and BGK collision (Eqs. LBMforflowfield,
                  *       LKSformagneticfield). */
                 for (int a = 0; a < 9; ++a) {
-                    double feq = feq_hyd(a, rho, ux, uy) + feq_mag(a, bx, by);
+                    double feq = feq_hyd(a, rho, ux, uy) + (p->coupling == 1 ? 0.0 : feq_mag(a, bx, by));
                     double S = source(a, rho, ux, uy, Fx, Fy);
                     fo[a * N + n] = f[a] - (f[a] - feq) / p->tau_f + (1.0 - 0.5 / p->tau_f) * S;
                 }
@@ -354,9 +393,26 @@ void orc_moments(const orc_params* p, const double* f, const double* g, double* 
             my += f[a * N + n] * EY9[a];
         }
         for (int a = 0; a < 5; ++a) { bx += g[a * N + n]; by += g[(5 + a) * N + n]; }
+        double ux = (mx - 0.5 * p->Fx) / rho, uy = my / rho;
+        if (p->coupling == 1) {
+            /* The collision relaxes Lambda - Lambda^(0) by the factor (1 - 1/tau_m), so the
+             * stored state carries (1 - 1/tau_m) Lambda^(1) of the last step: J_z (and with it
+             * F_L and the F/2 shift of u) is recovered from it, iterated with u as in the step. */
+            const double lyx = g[2 * N + n] - g[4 * N + n], lxy = g[(5 + 1) * N + n] - g[(5 + 3) * N + n];
+            for (int it = 0; it < 100; ++it) {
+                const double l0yx = uy * bx - by * ux, l0xy = ux * by - bx * uy;
+                const double jz = ((lyx - l0yx) - (lxy - l0xy)) / ((1.0 - 1.0 / p->tau_m) * p->tau_m * CS2);
+                const double fx = p->Fx - jz * by, fy = jz * bx;
+                const double nux = (mx - 0.5 * fx) / rho, nuy = (my - 0.5 * fy) / rho;
+                const double d = fabs(nux - ux) + fabs(nuy - uy);
+                ux = nux;
+                uy = nuy;
+                if (d <= 1e-17 * (fabs(ux) + fabs(uy)) || d == 0.0) break;
+            }
+        }
         mom[0 * N + n] = rho;
-        mom[1 * N + n] = (mx - 0.5 * p->Fx) / rho;
-        mom[2 * N + n] = my / rho;
+        mom[1 * N + n] = ux;
+        mom[2 * N + n] = uy;
         mom[3 * N + n] = bx;
         mom[4 * N + n] = by;
     }

@@ -281,3 +281,69 @@ def test_grid_convergence_second_order(closure):
     pb = _order(eb, ns)
     assert 1.7 < pu < 2.3, pu
     assert 1.7 < pb < 2.3, pb
+
+
+# ---- the paper's own coupling: Lorentz-force source with J from the non-equilibrium moment of g ----
+
+@pytest.mark.parametrize("closure", [oracle.LINK, oracle.MOMENT])
+@pytest.mark.parametrize("ha,c", [(5.0, 0.0), (5.0, 0.5), (10.0, 0.1), (5.0, 1e4)])
+def test_lorentz_coupling_hartmann_profiles(closure, ha, c):
+    """Sec. IV-V coupling (F_L = J x B in the source, J_z from Lambda^(1)): steady Hartmann profiles
+    agree with the closed form like the Maxwell-stress coupling does."""
+    o, a, b0, fx = hartmann(65, closure, ha, c, 0.8, 0.8, 0.01, coupling=1)
+    r = o.run_to_steady(1e-9, 200, 400_000)
+    assert r < 1e-9
+    u, b = o.profiles()
+    ua, ba = an.hartmann_profiles(o.y(), a, ha, c, fx, 0.8, 0.8)
+    assert an.rel_l2(u, ua) < _tol(ha)
+    assert an.rel_l2(b, ba) < _tol(ha)
+
+
+@pytest.mark.parametrize("closure", [oracle.LINK, oracle.MOMENT])
+@pytest.mark.parametrize("ha,cl,cu", [(5.0, 0.0, 0.0), (5.0, 0.5, 0.5), (20.0, 0.5, 0.0)])
+def test_lorentz_coupling_couette_profiles(closure, ha, cl, cu):
+    a = 65 / 2 if closure == oracle.LINK else 32.0
+    b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+    o = oracle.Oracle(3, 65, 0.8, 0.8, b0, 0.0, closure, cl, cu, 0.0, 0.05, coupling=1)
+    r = o.run_to_steady(1e-9, 200, 400_000)
+    assert r < 1e-9
+    u, b = o.profiles()
+    ua, ba = an.couette_profiles(o.y(), a, ha, cl, cu, 0.05, 0.8, 0.8)
+    assert an.rel_l2(u, ua) < 2 * _tol(ha)
+    assert an.rel_l2(b, ba) < 2 * _tol(ha)
+
+
+def test_lorentz_coupling_moments_solve_the_implicit_system():
+    """The step's u and the Lorentz force are mutually consistent: rho u = sum f e + (F_ext + J x B)/2
+    with J_z = (Lambda^(1)_yx - Lambda^(1)_xy)/(tau_m c_sm^2) evaluated with that same u (Sec. IV-V);
+    at moment-based wall nodes u = (U, 0)."""
+    for closure in (oracle.LINK, oracle.MOMENT):
+        o = oracle.Oracle(7, 11, 0.7, 0.85, 0.05, 3e-5, closure, 0.4, 2.0, 0.0, 0.03, seed=3, perturb_amp=1e-2,
+                          coupling=1)
+        o.step(4)
+        fpre, gpre, mom = o.step_detail()
+        rho, ux, uy, bx, by = mom
+        lyx = gpre[0, 2] - gpre[0, 4]
+        lxy = gpre[1, 1] - gpre[1, 3]
+        e = ux * by - uy * bx                         # Lambda^(0)_xy = E, Lambda^(0)_yx = -E
+        jz = ((lyx + e) - (lxy - e)) / (0.85 / 3.0)
+        mx = (fpre * EX9[:, None, None]).sum(axis=0)
+        my = (fpre * EY9[:, None, None]).sum(axis=0)
+        np.testing.assert_allclose(rho * ux, mx + 0.5 * (3e-5 - jz * by), rtol=0, atol=1e-16)
+        np.testing.assert_allclose(rho * uy, my + 0.5 * (jz * bx), rtol=0, atol=1e-16)
+        if closure == oracle.MOMENT:
+            np.testing.assert_allclose(ux[0], 0.0, atol=1e-16)
+            np.testing.assert_allclose(ux[-1], 0.03, atol=1e-16)
+            np.testing.assert_allclose(uy[[0, -1]], 0.0, atol=1e-16)
+
+
+@pytest.mark.parametrize("closure", [oracle.LINK, oracle.MOMENT])
+def test_lorentz_coupling_rest_state_and_stored_moments(closure):
+    o = oracle.Oracle(4, 9, 0.7, 0.9, 0.02, 0.0, closure, 0.3, 0.3, coupling=1)
+    f0 = o.f.copy()
+    o.step(50)
+    np.testing.assert_allclose(o.f, f0, rtol=0, atol=1e-15)
+    o = oracle.Oracle(5, 9, 0.7, 0.85, 0.03, 2e-5, closure, 0.3, 1.5, 0.0, 0.02, seed=7, perturb_amp=1e-2, coupling=1)
+    o.step(5)
+    _, _, mom = o.step_detail()
+    np.testing.assert_allclose(o.moments(), mom, rtol=1e-12, atol=1e-16)
