@@ -326,6 +326,21 @@ def bench_ours(args):
                                           "peak_source": "nominal GB300 FP64 rate"}}
         l64.close()
         del l64
+        # the paper's own coupling (Lorentz force in the source), FP32, same workload
+        ll = lks.Lattice(n, n, phys["tau_f"], phys["tau_m"], phys["B0"], phys["Fx"], "moment", "f32",
+                         coupling="lorentz")
+        ll.set_walls(phys["c"], phys["c"], 0.0, phys["u_w"])
+        ll.step(3)
+        barrier()
+        kl = max(10, min(args.steps, 2000))
+        tl = max_over_ranks(_time_steps(ll, kl, stream))
+        vl = nodes * kl * ws / tl / 1e6
+        al = 152 * nodes / (tl / kl) / 1e9
+        extra["lorentz_f32"] = {"value": round(vl, 1), "unit": UNIT, "steps": kl,
+                                "roofline": {"bound": "hbm", "achieved": round(al, 1), "peak": peak, "unit": "GB/s",
+                                             "frac": round(al / peak, 4)}}
+        ll.close()
+        del ll
         for st in ("bf16", "f16"):
             lr = make(st)
             lr.step(3)
@@ -486,6 +501,12 @@ def bench_sweep(args):
         states[r["state"]] = states.get(r["state"], 0) + 1
     resolved = [r for r in recs if r["state"] in ("converged", "stalled") and r["ny"] / 2 / r["ha"] >= 3.0]
     gate = [max(r["l2_u"], r["l2_b"]) for r in resolved]
+    # FP64 through the batched engine on the first instances: the same answers as one-at-a-time FP64
+    # (identical per-node arithmetic), so its speedup over the baseline is like for like.
+    nb64 = max(args.sweep_baseline, args.sweep_fp64_sample)
+    res64 = sweep.run_batched(sample[:nb64], "f64", tol=1e-10, check_every=100, quantum=args.sweep_quantum,
+                              max_steps=args.sweep_max_steps, tune_candidates=cands,
+                              time_budget=args.sweep_time)
     base = sweep.run_one_at_a_time(sample[: args.sweep_baseline], "f64", tol=1e-10, check_every=100,
                                    max_steps=args.sweep_max_steps)
     brecs = base["records"]
@@ -499,13 +520,30 @@ def bench_sweep(args):
         eu = float(np.sqrt(np.mean((r32["u"] - r64["u"]) ** 2)) / max(1e-300, np.max(np.abs(r64["u"]))))
         eb = float(np.sqrt(np.mean((r32["b"] - r64["b"]) ** 2)) / max(1e-300, np.max(np.abs(r64["b"]))))
         vs64.append(max(eu, eb))
+    r64 = res64["records"]
+    same64 = []
+    for a, c in zip(r64, brecs):
+        if a["state"] == "unstable":
+            continue
+        same64.append(max(float(np.max(np.abs(a["u"] - c["u"])) / max(1e-300, np.max(np.abs(c["u"])))),
+                          float(np.max(np.abs(a["b"] - c["b"])) / max(1e-300, np.max(np.abs(c["b"]))))))
+    t64 = np.array([r["t_done"] for r in r64 if r["t_done"] is not None])
+    fp64_batched = {"instances": len(r64), "wall_s": round(res64["wall"], 3),
+                    "solves_per_s": round(len(t64) / res64["wall"], 4),
+                    "time_to_steady_p50_s": float(np.percentile(t64, 50)) if len(t64) else None,
+                    "time_to_steady_p99_s": float(np.percentile(t64, 99)) if len(t64) else None,
+                    "states": {k: sum(1 for r in r64 if r["state"] == k) for k in {r["state"] for r in r64}},
+                    "autotune_best": res64["tune"]["best"] if res64["tune"] else None,
+                    "max_rel_diff_vs_one_at_a_time_fp64": same64,
+                    "baseline_instances_time_s": round(max([r["t_done"] or 0 for r in r64[: len(brecs)]]), 3)}
     out = {"workload": "sweep", "metric": "sweep solves/s", "unit": "solves/s", "higher_is_better": True,
            "sample": len(sample), "of": len(specs), "dtype": "f32",
            "value": round(len(done) / res["wall"], 3), "wall_s": round(res["wall"], 3),
            "time_to_steady_p50_s": float(np.percentile(t_done, 50)),
            "time_to_steady_p99_s": float(np.percentile(t_done, 99)),
            "states": states, "glups": round(node_updates / res["wall"] / 1e9, 2), "launches": res["launches"],
-           "autotune": res["tune"],
+           "autotune": res["tune"], "tail_shape_at_s": res["tail_shape_at"],
+           "fp64_batched": fp64_batched,
            "gate_l2_le_1e-4": {"resolved_instances": len(resolved), "pass": int(sum(g <= 1e-4 for g in gate)),
                                "median_l2": float(np.median(gate)) if gate else None},
            "baseline_fp64_one_at_a_time": {
@@ -556,6 +594,33 @@ def bench_serve(args):
     return 0
 
 
+def bench_validation(args):
+    """The paper's E1-E6 experiments on the GPU (FP64 batch, residual 1e-10); CSV profiles in
+    --validation-out; prints a JSON summary of the errors and convergence orders."""
+    import numpy as np
+    import torch
+    from paper_2112_13930_gb300 import build, lks, validation
+    torch.cuda.set_device(0)
+    build.build()
+    lks.load()
+    t0 = time.perf_counter()
+    rows, orders = validation.run(args.validation_out)
+    wall = time.perf_counter() - t0
+    per_exp = {}
+    for r in rows:
+        e = per_exp.setdefault(r["exp"], {"cases": 0, "max_l2_u": 0.0, "max_l2_b": 0.0, "states": {}})
+        e["cases"] += 1
+        e["max_l2_u"] = max(e["max_l2_u"], r["l2_u"])
+        e["max_l2_b"] = max(e["max_l2_b"], r["l2_b"])
+        e["states"][r["state"]] = e["states"].get(r["state"], 0) + 1
+    out = {"workload": "validation", "wall_s": round(wall, 2), "experiments": per_exp,
+           "convergence_orders": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in o.items()}
+                                  for o in orders],
+           "csv_dir": args.validation_out}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # FP64 arithmetic per bulk node per step in collide_node, counted from the source with an FMA as
 # 2 flops: moments and 1/rho (Newton) 40, equilibrium set-up 23, nine directions 116, g 33.
 FP64_FLOPS_PER_NODE = 212
@@ -575,11 +640,13 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["main", "precision", "sweep", "serve"], default="main")
+    ap.add_argument("--workload", choices=["main", "precision", "sweep", "serve", "validation"], default="main")
+    ap.add_argument("--validation-out", default="validation_out")
     ap.add_argument("--precision-steps", type=int, default=1000)
     ap.add_argument("--precision-max-steps", type=int, default=3_000_000)
     ap.add_argument("--sweep-sample", type=int, default=512)
     ap.add_argument("--sweep-baseline", type=int, default=8)
+    ap.add_argument("--sweep-fp64-sample", type=int, default=64)
     ap.add_argument("--sweep-quantum", type=int, default=20000)
     ap.add_argument("--sweep-max-steps", type=int, default=2_000_000)
     ap.add_argument("--sweep-time", type=float, default=600.0)
@@ -600,6 +667,8 @@ def main():
         return bench_sweep(args)
     if args.workload == "serve":
         return bench_serve(args)
+    if args.workload == "validation":
+        return bench_validation(args)
     return bench_ours(args)
 
 

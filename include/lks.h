@@ -29,8 +29,9 @@
  * Memory layout in HBM (structure of arrays, x fastest):
  *   f[a][y][x] for a = 0..8 and g[k][a][y][x] for k = x,y component, a = 0..4,
  *   stored as deviations from the rest equilibrium (rho = 1, u = 0,
- *   B = (0, B0)) in the storage type of lks_params.storage; two such buffers
- *   (ping-pong).  The state held between steps is the post-collision field.
+ *   B = (0, B0), with the Maxwell stress under LKS_MAXWELL) in the storage type
+ *   of lks_params.storage; two such buffers (ping-pong).  The state held between
+ *   steps is the post-collision field.
  *
  * Ownership: a handle owns its device buffers, or borrows caller memory
  * (lks_params.dev_buffer), which must outlive the handle.  Host pointers
@@ -69,6 +70,19 @@ typedef enum {
 
 typedef enum { LKS_LINK = 0, LKS_MOMENT = 1 } lks_closure;
 
+/* How the magnetic field acts on the flow.
+ *   LKS_MAXWELL -- Dellar's Maxwell stress (|B|^2 I/2 - BB) in f^eq; the default.
+ *   LKS_LORENTZ -- the paper's own form (Sec. IV-V): f^eq without magnetic terms and the Lorentz
+ *                  force F_L = J x B in the source term and in rho u = sum f e + F/2, with
+ *                  J_z = (Lambda^(1)_yx - Lambda^(1)_xy)/(tau_m c_sm^2) from the non-equilibrium first
+ *                  moment of g (Eq. rank2antisymmtensornoneq).  u and J depend on each other linearly
+ *                  and are solved together exactly.  At moment-based wall nodes the closure sets the
+ *                  node's velocity (sum f e + F/2)/rho to (U, 0), i.e. Pi_10 = rho U - F_x/2 and
+ *                  Pi_01 = -F_y/2, and Pi_20 = rho (c_s^2 + U^2).  Requires |tau_m - 1| >= 0.05 (the
+ *                  moments of a stored state read J back from the (1 - 1/tau_m)-scaled
+ *                  non-equilibrium part of the post-collision g). */
+typedef enum { LKS_MAXWELL = 0, LKS_LORENTZ = 1 } lks_coupling;
+
 /* Storage type of the populations; arithmetic is FP64 for LKS_F64 and FP32 otherwise. */
 typedef enum { LKS_F64 = 0, LKS_F32 = 1, LKS_BF16_DEV = 2, LKS_F16_DEV = 3 } lks_storage;
 
@@ -86,6 +100,8 @@ typedef struct lks_params {
     void* cuda_stream;     /* cudaStream_t; NULL = legacy default stream */
     void* dev_buffer;      /* optional caller-owned device memory (NULL = library allocates) */
     size_t dev_buffer_bytes; /* size of dev_buffer; must be >= lks_footprint_bytes() */
+    int32_t coupling;      /* lks_coupling (0 = LKS_MAXWELL) */
+    int32_t pad;
 } lks_params;
 
 typedef struct lks_handle lks_handle;

@@ -27,9 +27,9 @@
  * Residual (steady-state criterion; the paper gives none): every check_every steps,
  * r = max(|u_x - u_x'|_2 / |u_x|_2, |B_x - B_x'|_2 / |B_x|_2) over the instance's nodes, FP64,
  * against the snapshot of the previous check (a term with a denominator below 1e-30 counts 0).
- * An instance is CONVERGED when r < tol, STALLED when r is below 1e-4 and has not reached a new
- * minimum for 1000 checks in a row (the storage precision's rounding floor), UNSTABLE when r is
- * not finite, MAX_STEPS at max_steps.
+ * An instance is CONVERGED when r < tol, STALLED when r is below the storage type's rounding floor
+ * (1e-12 FP64, 1e-4 FP32, 1e-2 16-bit) and has not reached a new minimum for 1000 checks in a row,
+ * UNSTABLE when r is not finite, MAX_STEPS at max_steps.
  *
  * Threading: a batch handle is not thread-safe.
  */

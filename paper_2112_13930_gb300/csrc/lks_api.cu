@@ -58,6 +58,9 @@ const char* validate(const lks_params* p) {
     if (!(p->tau_m > 0.5) || !isfinite(p->tau_m)) return "tau_m must be finite and > 1/2";
     if (!isfinite(p->B0) || !isfinite(p->Fx)) return "B0 and Fx must be finite";
     if (!isfinite(p->perturb_amp) || fabs(p->perturb_amp) >= 0.3) return "|perturb_amp| must be < 0.3";
+    if (p->coupling != LKS_MAXWELL && p->coupling != LKS_LORENTZ) return "coupling must be LKS_MAXWELL or LKS_LORENTZ";
+    if (p->coupling == LKS_LORENTZ && fabs(p->tau_m - 1.0) < 0.05)
+        return "the Lorentz-force coupling needs |tau_m - 1| >= 0.05 (J is read back from the stored g)";
     return nullptr;
 }
 
@@ -108,7 +111,7 @@ static WallCoef<double> wall_coef(int closure, double a, double tau_m, double B0
 }
 
 StepParams<double> make_step_params(int nx, int ny, int closure, double tau_f, double tau_m, double B0, double Fx,
-                                    double c_bot, double c_top, double u_bot, double u_top) {
+                                    double c_bot, double c_top, double u_bot, double u_top, int coupling) {
     StepParams<double> s;
     const double a = closure == LKS_LINK ? 0.5 * ny : 0.5 * (ny - 1);
     s.nx = nx;
@@ -129,6 +132,8 @@ StepParams<double> make_step_params(int nx, int ny, int closure, double tau_f, d
     s.sw0 = s.src_coef * 3.0 * Fx * (4.0 / 9.0);
     s.sw1 = s.src_coef * 3.0 * Fx * (1.0 / 9.0);
     s.sw5 = s.src_coef * 3.0 * Fx * (1.0 / 36.0);
+    s.src3 = 3.0 * s.src_coef;
+    s.coupling = coupling;
     s.bot = wall_coef(closure, a, tau_m, B0, c_bot, u_bot, +1.0);
     s.top = wall_coef(closure, a, tau_m, B0, c_top, u_top, -1.0);
     return s;
@@ -180,7 +185,7 @@ lks_status cuda_fail(lks_handle* h, cudaError_t e, const char* where) {
 void refresh_params(lks_handle* h) {
     const lks_params& p = h->p;
     h->sp = lks::make_step_params(p.nx, p.ny, p.closure, p.tau_f, p.tau_m, p.B0, p.Fx, h->c_bot, h->c_top, h->u_bot,
-                                  h->u_top);
+                                  h->u_top, p.coupling);
 }
 
 void drop_graphs(lks_handle* h) {
@@ -273,7 +278,8 @@ lks_status lks_create(const lks_params* p, lks_handle** out) {
     refresh_params(h);
     e = lks::launch_init(p->storage, h->f[0], h->g[0], p->nx, p->ny, p->B0, p->seed, p->perturb_amp, h->stream);
     if (e == cudaSuccess)
-        e = lks::launch_snapshot(p->storage, h->f[0], h->g[0], p->nx, p->ny, p->B0, p->Fx, h->snap, h->stream);
+        e = lks::launch_snapshot(p->storage, h->f[0], h->g[0], p->nx, p->ny, p->B0, p->Fx, h->snap, h->stream,
+                                 p->coupling, p->tau_m);
     if (e != cudaSuccess) {
         lks_destroy(h);
         return cuda_fail(nullptr, e, "lks_create: init kernel");
@@ -328,7 +334,7 @@ lks_status lks_moments_device(lks_handle* h, int what, double* dev_out) {
     if (!dev_out) return fail(h, LKS_EINVAL, "dev_out is NULL");
     if (what != LKS_MOMENTS_NODES && what != LKS_MOMENTS_PROFILES) return fail(h, LKS_EINVAL, "bad 'what'");
     cudaError_t e = lks::launch_moments(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0,
-                                        h->p.Fx, what, dev_out, h->stream);
+                                        h->p.Fx, what, dev_out, h->stream, h->p.coupling, h->p.tau_m);
     if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
     return LKS_OK;
 }
@@ -363,7 +369,8 @@ lks_status lks_moments(lks_handle* h, int what, double* host_out) {
 lks_status lks_residual(lks_handle* h, double* r_u, double* r_b) {
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     cudaError_t e = lks::launch_residual(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0,
-                                         h->p.Fx, h->snap, h->partial, h->dout, h->stream);
+                                         h->p.Fx, h->snap, h->partial, h->dout, h->stream, h->p.coupling,
+                                         h->p.tau_m);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->host_small, h->dout, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -414,7 +421,7 @@ lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g) {
         return fail(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
     }
     e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], (int64_t)N, h->p.B0, tmp, tmp + 9 * N,
-                           h->stream);
+                           h->stream, h->p.coupling);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_g, tmp + 9 * N, 10 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -439,10 +446,10 @@ lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host
         e = cudaMemcpyAsync(tmp + 9 * N, host_g, 10 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = lks::launch_from_abs(h->p.storage, tmp, tmp + 9 * N, (int64_t)N, h->p.B0, h->f[h->cur], h->g[h->cur],
-                                 h->stream);
+                                 h->stream, h->p.coupling);
     if (e == cudaSuccess)
         e = lks::launch_snapshot(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0, h->p.Fx,
-                                 h->snap, h->stream);
+                                 h->snap, h->stream, h->p.coupling, h->p.tau_m);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_set_state");

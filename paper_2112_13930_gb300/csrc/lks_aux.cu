@@ -19,11 +19,19 @@ __device__ __forceinline__ int ey9(int a) {
     const int t[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     return t[a];
 }
-// Rest equilibrium f^eq(rho = 1, u = 0, B = (0, B0)) including the Maxwell stress.
-__device__ __forceinline__ double f_rest(int a, double B0) {
+// Rest equilibrium f^eq(rho = 1, u = 0, B = (0, B0)): with the Maxwell stress (coupling 0) or
+// without magnetic terms (coupling 1, Lorentz force in the source).
+__device__ __forceinline__ double f_rest(int a, double B0, int coupling) {
+    if (coupling == 1) return w9(a);
     const double m = (a == 1 || a == 3) ? 0.5 * B0 * B0 : ((a == 2 || a == 4) ? -0.5 * B0 * B0 : 0.0);
     return w9(a) * (1.0 + 4.5 * m);
 }
+
+// What the moments of a stored state depend on.
+struct MomentModel {
+    double B0, Fx, tau_m;
+    int coupling;
+};
 
 // SplitMix64 (Steele, Lea & Flood 2014) of seed XOR counter -> [0, 1) with 53 bits.
 __device__ __forceinline__ double splitmix_unit(uint64_t seed, uint64_t counter) {
@@ -57,10 +65,14 @@ __global__ void init_kernel(S* f, S* g, int64_t N, double B0, uint64_t seed, dou
 }
 
 // FP64 moments of node n of a stored state: rho, u_x, u_y, B_x, B_y.
+// Coupling 0: rho u = sum f~ e - F/2.  Coupling 1: the force includes J x B; the stored g carries
+// (1 - 1/tau_m) Lambda^(1) of the last collision, so with k' = 3/(tau_m - 1) and
+// D~ = Lambda~_yx - Lambda~_xy:  J_z = k' [D~ + 2 (B_y (j_x - F_ext/2) - B_x j_y)/rho] / (1 - k' |B|^2/rho).
 template <typename S, typename C>
-__device__ __forceinline__ void node_moments(const S* f, const S* g, int64_t N, int64_t n, double B0, double Fx,
+__device__ __forceinline__ void node_moments(const S* f, const S* g, int64_t N, int64_t n, const MomentModel& mm,
                                              double m[5]) {
     double drho = 0.0, jx = 0.0, jy = 0.0, bx = 0.0, dby = 0.0;
+    double gv[10];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         const double v = (double)load_s<S, C>(f + a * N + n);
@@ -70,23 +82,35 @@ __device__ __forceinline__ void node_moments(const S* f, const S* g, int64_t N, 
     }
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
-        bx += (double)load_s<S, C>(g + a * N + n);
-        dby += (double)load_s<S, C>(g + (5 + a) * N + n);
+        gv[a] = (double)load_s<S, C>(g + a * N + n);
+        gv[5 + a] = (double)load_s<S, C>(g + (5 + a) * N + n);
+        bx += gv[a];
+        dby += gv[5 + a];
     }
     const double rho = 1.0 + drho;
+    const double by = mm.B0 + dby;
+    double ux = (jx - 0.5 * mm.Fx) / rho, uy = jy / rho;
+    if (mm.coupling == 1) {
+        const double kp = 3.0 / (mm.tau_m - 1.0);
+        const double D = (gv[2] - gv[4]) - (gv[5 + 1] - gv[5 + 3]);
+        const double jxp = jx - 0.5 * mm.Fx;
+        const double jz = kp * (D + 2.0 * (by * jxp - bx * jy) / rho) / (1.0 - kp * (bx * bx + by * by) / rho);
+        ux = (jxp + 0.5 * jz * by) / rho;
+        uy = (jy - 0.5 * jz * bx) / rho;
+    }
     m[0] = rho;
-    m[1] = (jx - 0.5 * Fx) / rho;
-    m[2] = jy / rho;
+    m[1] = ux;
+    m[2] = uy;
     m[3] = bx;
-    m[4] = B0 + dby;
+    m[4] = by;
 }
 
 template <typename S, typename C>
-__global__ void moments_kernel(const S* f, const S* g, int64_t N, double B0, double Fx, double* out) {
+__global__ void moments_kernel(const S* f, const S* g, int64_t N, MomentModel mm, double* out) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     double m[5];
-    node_moments<S, C>(f, g, N, n, B0, Fx, m);
+    node_moments<S, C>(f, g, N, n, mm, m);
 #pragma unroll
     for (int k = 0; k < 5; ++k) out[k * N + n] = m[k];
 }
@@ -110,15 +134,15 @@ __device__ __forceinline__ void block_sum(double v[K], double* sh) {
 }
 
 template <typename S, typename C>
-__global__ void __launch_bounds__(kThreads) profiles_kernel(const S* f, const S* g, int nx, int ny, double B0,
-                                                           double Fx, double* out) {
+__global__ void __launch_bounds__(kThreads) profiles_kernel(const S* f, const S* g, int nx, int ny, MomentModel mm,
+                                                           double* out) {
     __shared__ double sh[5 * kThreads];
     const int j = blockIdx.x;
     const int64_t N = (int64_t)nx * ny;
     double acc[5] = {0, 0, 0, 0, 0};
     for (int i = threadIdx.x; i < nx; i += kThreads) {
         double m[5];
-        node_moments<S, C>(f, g, N, (int64_t)j * nx + i, B0, Fx, m);
+        node_moments<S, C>(f, g, N, (int64_t)j * nx + i, mm, m);
 #pragma unroll
         for (int k = 0; k < 5; ++k) acc[k] += m[k];
     }
@@ -128,13 +152,13 @@ __global__ void __launch_bounds__(kThreads) profiles_kernel(const S* f, const S*
 }
 
 template <typename S, typename C>
-__global__ void __launch_bounds__(kThreads) residual_partial_kernel(const S* f, const S* g, int64_t N, double B0,
-                                                                   double Fx, double* snap, double* partial) {
+__global__ void __launch_bounds__(kThreads) residual_partial_kernel(const S* f, const S* g, int64_t N,
+                                                                   MomentModel mm, double* snap, double* partial) {
     __shared__ double sh[4 * kThreads];
     double acc[4] = {0, 0, 0, 0};
     for (int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x; n < N; n += (int64_t)gridDim.x * kThreads) {
         double m[5];
-        node_moments<S, C>(f, g, N, n, B0, Fx, m);
+        node_moments<S, C>(f, g, N, n, mm, m);
         const double du = m[1] - snap[n];
         const double db = m[3] - snap[N + n];
         acc[0] += du * du;
@@ -160,20 +184,20 @@ __global__ void __launch_bounds__(kThreads) residual_final_kernel(const double* 
 }
 
 template <typename S, typename C>
-__global__ void snapshot_kernel(const S* f, const S* g, int64_t N, double B0, double Fx, double* snap) {
+__global__ void snapshot_kernel(const S* f, const S* g, int64_t N, MomentModel mm, double* snap) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     double m[5];
-    node_moments<S, C>(f, g, N, n, B0, Fx, m);
+    node_moments<S, C>(f, g, N, n, mm, m);
     snap[n] = m[1];
     snap[N + n] = m[3];
 }
 
 template <typename S, typename C>
-__global__ void to_abs_kernel(const S* f, const S* g, int64_t N, double B0, double* fa, double* ga) {
+__global__ void to_abs_kernel(const S* f, const S* g, int64_t N, double B0, int coupling, double* fa, double* ga) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    for (int a = 0; a < 9; ++a) fa[a * N + n] = (double)load_s<S, C>(f + a * N + n) + f_rest(a, B0);
+    for (int a = 0; a < 9; ++a) fa[a * N + n] = (double)load_s<S, C>(f + a * N + n) + f_rest(a, B0, coupling);
     for (int a = 0; a < 5; ++a) {
         ga[a * N + n] = (double)load_s<S, C>(g + a * N + n);
         ga[(5 + a) * N + n] = (double)load_s<S, C>(g + (5 + a) * N + n) + w5(a) * B0;
@@ -181,10 +205,10 @@ __global__ void to_abs_kernel(const S* f, const S* g, int64_t N, double B0, doub
 }
 
 template <typename S, typename C>
-__global__ void from_abs_kernel(const double* fa, const double* ga, int64_t N, double B0, S* f, S* g) {
+__global__ void from_abs_kernel(const double* fa, const double* ga, int64_t N, double B0, int coupling, S* f, S* g) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    for (int a = 0; a < 9; ++a) store_s<S, C>(f + a * N + n, (C)(fa[a * N + n] - f_rest(a, B0)));
+    for (int a = 0; a < 9; ++a) store_s<S, C>(f + a * N + n, (C)(fa[a * N + n] - f_rest(a, B0, coupling)));
     for (int a = 0; a < 5; ++a) {
         store_s<S, C>(g + a * N + n, (C)ga[a * N + n]);
         store_s<S, C>(g + (5 + a) * N + n, (C)(ga[(5 + a) * N + n] - w5(a) * B0));
@@ -224,14 +248,15 @@ cudaError_t launch_init(int storage, void* f, void* g, int nx, int ny, double B0
 }
 
 cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                           int what, double* out, cudaStream_t st) {
+                           int what, double* out, cudaStream_t st, int coupling, double tau_m) {
     const int64_t N = (int64_t)nx * ny;
+    const MomentModel mm{B0, Fx, tau_m, coupling};
     if (what == 0) {
         LKS_DISPATCH(storage, (moments_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N,
-                                                                                      B0, Fx, out)));
+                                                                                      mm, out)));
     } else {
-        LKS_DISPATCH(storage, (profiles_kernel<S, C><<<ny, kThreads, 0, st>>>((const S*)f, (const S*)g, nx, ny, B0,
-                                                                              Fx, out)));
+        LKS_DISPATCH(storage, (profiles_kernel<S, C><<<ny, kThreads, 0, st>>>((const S*)f, (const S*)g, nx, ny, mm,
+                                                                              out)));
     }
     return cudaGetLastError();
 }
@@ -244,34 +269,36 @@ int residual_blocks(int64_t N) {
 }
 
 cudaError_t launch_residual(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                            double* snap, double* partial, double* out, cudaStream_t st) {
+                            double* snap, double* partial, double* out, cudaStream_t st, int coupling, double tau_m) {
     const int64_t N = (int64_t)nx * ny;
     const int nblk = residual_blocks(N);
+    const MomentModel mm{B0, Fx, tau_m, coupling};
     LKS_DISPATCH(storage, (residual_partial_kernel<S, C><<<nblk, kThreads, 0, st>>>((const S*)f, (const S*)g, N,
-                                                                                    B0, Fx, snap, partial)));
+                                                                                    mm, snap, partial)));
     residual_final_kernel<<<1, kThreads, 0, st>>>(partial, nblk, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_snapshot(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                            double* snap, cudaStream_t st) {
+                            double* snap, cudaStream_t st, int coupling, double tau_m) {
     const int64_t N = (int64_t)nx * ny;
-    LKS_DISPATCH(storage, (snapshot_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N, B0,
-                                                                                   Fx, snap)));
+    const MomentModel mm{B0, Fx, tau_m, coupling};
+    LKS_DISPATCH(storage, (snapshot_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N, mm,
+                                                                                   snap)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, double B0, double* fabs,
-                          double* gabs, cudaStream_t st) {
+                          double* gabs, cudaStream_t st, int coupling) {
     LKS_DISPATCH(storage, (to_abs_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N, B0,
-                                                                                 fabs, gabs)));
+                                                                                 coupling, fabs, gabs)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, double B0, void* f,
-                            void* g, cudaStream_t st) {
-    LKS_DISPATCH(storage, (from_abs_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>(fabs, gabs, N, B0, (S*)f,
-                                                                                   (S*)g)));
+                            void* g, cudaStream_t st, int coupling) {
+    LKS_DISPATCH(storage, (from_abs_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>(fabs, gabs, N, B0, coupling,
+                                                                                   (S*)f, (S*)g)));
     return cudaGetLastError();
 }
 

@@ -28,11 +28,11 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kMaxGroups = 15;  // named barriers 1..15 (0 is __syncthreads)
 // An instance is declared STALLED when its residual has not reached a new minimum for kStallChecks
-// checks in a row while already below kStallBelow: the rounding floor of the storage type.  A long
-// window keeps slowly converging instances (diffusive times of 1e6+ steps, residual falling by
-// well under 1 % per check and jittering) from being stopped early.
+// checks in a row while already below the rounding floor of the storage type (stall_below: 1e-12
+// FP64, 1e-4 FP32, 1e-2 16-bit).  A long window keeps slowly converging instances (diffusive times
+// of 1e6+ steps, residual falling by well under 1 % per check and jittering) from being stopped early.
 constexpr int kStallChecks = 1000;
-constexpr double kStallBelow = 1e-4;
+inline double stall_floor(int storage) { return storage == 0 ? 1e-12 : (storage == 1 ? 1e-4 : 1e-2); }
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -43,7 +43,7 @@ struct InstDev {
     char* g[2];
     double* snap;
     int64_t steps, check_every, max_steps;
-    double tol, best_r, residual;
+    double tol, best_r, residual, stall_below;
     int32_t closure, cur, state, stall;
 };
 
@@ -79,6 +79,7 @@ __device__ __forceinline__ StepParams<C> to_compute(const StepParams<double>& d)
     o.owf0 = (C)d.owf0; o.owf1 = (C)d.owf1; o.owf5 = (C)d.owf5;
     o.owm0 = (C)d.owm0; o.owm1 = (C)d.owm1;
     o.sw0 = (C)d.sw0; o.sw1 = (C)d.sw1; o.sw5 = (C)d.sw5;
+    o.src3 = (C)d.src3; o.coupling = d.coupling;
     o.bot.r = (C)d.bot.r; o.bot.bc = (C)d.bot.bc; o.bot.kx = (C)d.bot.kx; o.bot.du = (C)d.bot.du; o.bot.U = (C)d.bot.U;
     o.top.r = (C)d.top.r; o.top.bc = (C)d.top.bc; o.top.kx = (C)d.top.kx; o.top.du = (C)d.top.du; o.top.U = (C)d.top.U;
     return o;
@@ -135,9 +136,11 @@ __global__ void __launch_bounds__(512) batch_kernel(InstDev* tab, const int32_t*
             S* fo = (S*)I->f[cur ^ 1];
             S* go = (S*)I->g[cur ^ 1];
             if (closure == 0) {
-                for (int64_t n = lt; n < N; n += T) lks::step_node<S, C, 0, false>(fi, gi, fo, go, p, n);
+                for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
+                    lks::step_node<S, C, 0, false>(fi, gi, fo, go, p, w.n, w.i, w.j);
             } else {
-                for (int64_t n = lt; n < N; n += T) lks::step_node<S, C, 1, false>(fi, gi, fo, go, p, n);
+                for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
+                    lks::step_node<S, C, 1, false>(fi, gi, fo, go, p, w.n, w.i, w.j);
             }
             cur ^= 1;
             ++steps;
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(512) batch_kernel(InstDev* tab, const int32_t*
                         if (r < best) {
                             best = r;
                             stall = 0;
-                        } else if (++stall >= kStallChecks && best < kStallBelow) {
+                        } else if (++stall >= kStallChecks && best < I->stall_below) {
                             st = LKS_INST_STALLED;
                         }
                         if (st == LKS_INST_RUNNING && steps >= max_steps) st = LKS_INST_MAX_STEPS;
@@ -277,9 +280,11 @@ __global__ void __launch_bounds__(512) batch_cluster_kernel(InstDev* tab, const 
             S* fo = (S*)I->f[cur ^ 1];
             S* go = (S*)I->g[cur ^ 1];
             if (closure == 0) {
-                for (int64_t n = first; n < N; n += stride) lks::step_node_with<S, C, 0, CgLoader<S, C>>(fi, gi, fo, go, p, n);
+                for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
+                    lks::step_node_with<S, C, 0, CgLoader<S, C>>(fi, gi, fo, go, p, w.n, w.i, w.j);
             } else {
-                for (int64_t n = first; n < N; n += stride) lks::step_node_with<S, C, 1, CgLoader<S, C>>(fi, gi, fo, go, p, n);
+                for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
+                    lks::step_node_with<S, C, 1, CgLoader<S, C>>(fi, gi, fo, go, p, w.n, w.i, w.j);
             }
             cur ^= 1;
             ++steps;
@@ -335,7 +340,7 @@ __global__ void __launch_bounds__(512) batch_cluster_kernel(InstDev* tab, const 
                         if (r < best) {
                             best = r;
                             stall = 0;
-                        } else if (++stall >= kStallChecks && best < kStallBelow) {
+                        } else if (++stall >= kStallChecks && best < I->stall_below) {
                             st = LKS_INST_STALLED;
                         }
                         if (st == LKS_INST_RUNNING && steps >= max_steps) st = LKS_INST_MAX_STEPS;
@@ -694,6 +699,7 @@ lks_status lks_batch_add(lks_batch* b, const lks_instance_desc* d, int32_t* slot
     I.check_every = d->check_every;
     I.max_steps = d->max_steps;
     I.tol = d->tol;
+    I.stall_below = stall_floor(b->cfg.storage);
     I.best_r = INFINITY;
     I.residual = INFINITY;
     I.closure = d->closure;

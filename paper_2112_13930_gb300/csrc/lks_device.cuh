@@ -39,6 +39,8 @@ struct StepParams {
     C owf0, owf1, owf5;   // omega_f * w_a for |e_a|^2 = 0, 1, 2
     C owm0, owm1;         // omega_m * W_a for a = 0 and a = 1..4
     C sw0, sw1, sw5;      // (1 - 1/(2 tau_f)) * 3 Fx * w_a   (source-term prefactor)
+    C src3;               // 3 (1 - 1/(2 tau_f))   (source prefactor when the force varies per node)
+    int32_t coupling;     // 0: Maxwell stress in f^eq; 1: Lorentz force J x B in the source
     WallCoef<C> bot, top;
 };
 
@@ -158,41 +160,142 @@ __device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const Ste
 }
 
 // Moment-based closures at a wet wall node (Sec. VII, App. A, App. B.2), deviation form.
-// g first (its B_x enters the Pi_20 target of f), then f.  Bottom: unknown f2, f5, f6, g2.
-template <typename C>
-__device__ __forceinline__ void moment_closure_bottom(C f[9], C gx[5], C gy[5], const WallCoef<C>& w, C B0) {
+// g first (its moments enter the f closure), then f.  Bottom: unknown f2, f5, f6, g2.
+//   COUPLING 0 (Maxwell stress in f^eq): Pi_10 = rho U, Pi_01 = 0,
+//              Pi_20 = rho (c^2 + U^2) + (B_y^2 - B_x^2)/2 (the full equilibrium value).
+//   COUPLING 1 (Lorentz force in the source): the node's velocity (Pi + F/2)/rho is (U, 0):
+//              Pi_10 = rho U - F_x/2, Pi_01 = -F_y/2 with F = F_ext + J x B, J_z from the closed g
+//              at u = (U, 0) (J_z = 3 omega_m (Lambda_yx - Lambda_xy + 2 U B_y)); Pi_20 = rho (c^2 + U^2).
+// In both, the rest state satisfies the closure exactly, so the deviations need no constant terms.
+template <typename C, int COUPLING>
+__device__ __forceinline__ void wall_force_halves(const C gx[5], const C gy[5], C bx, C by, C U,
+                                                  const StepParams<C>& p, C& hfx, C& hfy) {
+    if (COUPLING == 1) {
+        const C jz = C(3) * p.omega_m * (((gx[2] - gx[4]) - (gy[1] - gy[3])) + C(2) * U * by);
+        hfx = C(0.5) * (p.Fx - jz * by);
+        hfy = C(0.5) * (jz * bx);
+    } else {
+        hfx = C(0);
+        hfy = C(0);
+    }
+}
+
+template <typename C, int COUPLING>
+__device__ __forceinline__ void moment_closure_bottom(C f[9], C gx[5], C gy[5], const WallCoef<C>& w,
+                                                      const StepParams<C>& p) {
     const C half = C(0.5), cs2 = C(1.0 / 3.0);
+    const C B0 = p.B0;
     gx[2] = w.r * gx[4] - w.bc * ((gx[0] + gx[1]) + gx[3]) + w.kx;
     gy[2] = -(((gy[0] + gy[1]) + gy[3]) + gy[4]);
     const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
     const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
-    const C drho = (f[0] + f[1]) + f[3] + C(2) * ((f[4] + f[7]) + f[8]);
-    const C rho = C(1) + drho;
     const C U = w.U;
-    // P - P_rest with P = rho (c^2 + U^2) + (B_y^2 - B_x^2)/2 and P_rest = c^2 + B0^2/2
-    const C dP = U * U + drho * (cs2 + U * U) + dby * (B0 + half * dby) - half * bx * bx;
-    const C rU = rho * U;
-    f[2] = -dP + (f[1] + f[3]) + f[4] + C(2) * (f[7] + f[8]);
+    C hfx, hfy;
+    wall_force_halves<C, COUPLING>(gx, gy, bx, B0 + dby, U, p, hfx, hfy);
+    const C drho = (f[0] + f[1]) + f[3] + C(2) * ((f[4] + f[7]) + f[8]) - hfy;
+    const C rho = C(1) + drho;
+    // P - P_rest
+    C dP = U * U + drho * (cs2 + U * U);
+    if (COUPLING == 0) dP += dby * (B0 + half * dby) - half * bx * bx;
+    const C rU = rho * U - hfx;
+    f[2] = -dP + (f[1] + f[3]) + f[4] + C(2) * (f[7] + f[8]) - hfy;
     f[5] = half * (dP + rU) - (f[1] + f[8]);
     f[6] = half * (dP - rU) - (f[3] + f[7]);
 }
 
 // Top: unknown f4, f7, f8, g4.
-template <typename C>
-__device__ __forceinline__ void moment_closure_top(C f[9], C gx[5], C gy[5], const WallCoef<C>& w, C B0) {
+template <typename C, int COUPLING>
+__device__ __forceinline__ void moment_closure_top(C f[9], C gx[5], C gy[5], const WallCoef<C>& w,
+                                                   const StepParams<C>& p) {
     const C half = C(0.5), cs2 = C(1.0 / 3.0);
+    const C B0 = p.B0;
     gx[4] = w.r * gx[2] - w.bc * ((gx[0] + gx[1]) + gx[3]) + w.kx;
     gy[4] = -(((gy[0] + gy[1]) + gy[2]) + gy[3]);
     const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
     const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
-    const C drho = (f[0] + f[1]) + f[3] + C(2) * ((f[2] + f[5]) + f[6]);
-    const C rho = C(1) + drho;
     const C U = w.U;
-    const C dP = U * U + drho * (cs2 + U * U) + dby * (B0 + half * dby) - half * bx * bx;
-    const C rU = rho * U;
-    f[4] = -dP + (f[1] + f[2]) + f[3] + C(2) * (f[5] + f[6]);
+    C hfx, hfy;
+    wall_force_halves<C, COUPLING>(gx, gy, bx, B0 + dby, U, p, hfx, hfy);
+    const C drho = (f[0] + f[1]) + f[3] + C(2) * ((f[2] + f[5]) + f[6]) + hfy;
+    const C rho = C(1) + drho;
+    C dP = U * U + drho * (cs2 + U * U);
+    if (COUPLING == 0) dP += dby * (B0 + half * dby) - half * bx * bx;
+    const C rU = rho * U - hfx;
+    f[4] = -dP + (f[1] + f[2]) + f[3] + C(2) * (f[5] + f[6]) + hfy;
     f[7] = half * (dP - rU) - (f[3] + f[6]);
     f[8] = half * (dP + rU) - (f[1] + f[5]);
+}
+
+// Collision with the paper's own coupling (Sec. IV-V): f^eq without magnetic terms; the Lorentz
+// force F_L = J x B, J_z = (Lambda^(1)_yx - Lambda^(1)_xy)/(tau_m c_sm^2), enters the source and the
+// half shift of rho u.  Lambda^(1) = Lambda - Lambda^(0)(u) and u = (j + F/2)/rho depend on each
+// other linearly; with k = 3 omega_m and D = Lambda_yx - Lambda_xy the exact solution is
+//   J_z = k [D + 2 (B_y (j_x + F_ext/2) - B_x j_y)/rho] / (1 + k |B|^2 / rho).
+template <typename C>
+__device__ __forceinline__ void collide_node_lorentz(C f[9], C gx[5], C gy[5], const StepParams<C>& p) {
+    const C half = C(0.5), three = C(3), four5 = C(4.5), one5 = C(1.5);
+    const C drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const C rho = C(1) + drho;
+    const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const C inv_rho = recip(rho);
+    const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
+    const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
+    const C by = p.B0 + dby;
+    const C k = three * p.omega_m;
+    const C D = (gx[2] - gx[4]) - (gy[1] - gy[3]);
+    const C jxp = jx + half * p.Fx;
+    const C jz = k * (D + C(2) * inv_rho * (by * jxp - bx * jy)) / (C(1) + k * inv_rho * (bx * bx + by * by));
+    const C Fx = p.Fx - jz * by, Fy = jz * bx;
+    const C ux = (jx + half * Fx) * inv_rho;
+    const C uy = (jy + half * Fy) * inv_rho;
+    const C usq = one5 * (ux * ux + uy * uy);
+    const C ax = p.src3 * Fx, ay = p.src3 * Fy;
+    // (e_x - u_x) a_x and (e_y - u_y) a_y for e = -1, 0, +1
+    const C px0 = -ux * ax, pxp = (C(1) - ux) * ax, pxm = (C(-1) - ux) * ax;
+    const C py0 = -uy * ay, pyp = (C(1) - uy) * ay, pym = (C(-1) - uy) * ay;
+    const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w5 = C(1.0 / 36.0);
+    const C om1 = p.om1f;
+#define LKS_DIRL(A, EU, OW, W, PX, PY)                                                  \
+    {                                                                                   \
+        const C eu = (EU);                                                              \
+        const C bm1 = (three + four5 * eu) * eu - usq;                                  \
+        const C ofeq = (OW) * (drho + rho * bm1);                                       \
+        const C sa = (W) * ((PX) + (PY));                                               \
+        f[A] = om1 * f[A] + (ofeq + (sa + sa * bm1));                                   \
+    }
+    LKS_DIRL(0, C(0), p.owf0, w0, px0, py0)
+    LKS_DIRL(1, ux, p.owf1, w1, pxp, py0)
+    LKS_DIRL(2, uy, p.owf1, w1, px0, pyp)
+    LKS_DIRL(3, -ux, p.owf1, w1, pxm, py0)
+    LKS_DIRL(4, -uy, p.owf1, w1, px0, pym)
+    LKS_DIRL(5, ux + uy, p.owf5, w5, pxp, pyp)
+    LKS_DIRL(6, uy - ux, p.owf5, w5, pxm, pyp)
+    LKS_DIRL(7, -ux - uy, p.owf5, w5, pxm, pym)
+    LKS_DIRL(8, ux - uy, p.owf5, w5, pxp, pym)
+#undef LKS_DIRL
+    const C om1m = p.om1m;
+    const C ce = p.owm1 * (three * (ux * by - uy * bx));
+    const C cb0 = p.owm0 * bx, cb1 = p.owm1 * bx;
+    const C cd0 = p.owm0 * dby, cd1 = p.owm1 * dby;
+    gx[0] = om1m * gx[0] + cb0;
+    gx[1] = om1m * gx[1] + cb1;
+    gx[2] = om1m * gx[2] + (cb1 - ce);
+    gx[3] = om1m * gx[3] + cb1;
+    gx[4] = om1m * gx[4] + (cb1 + ce);
+    gy[0] = om1m * gy[0] + cd0;
+    gy[1] = om1m * gy[1] + (cd1 + ce);
+    gy[2] = om1m * gy[2] + cd1;
+    gy[3] = om1m * gy[3] + (cd1 - ce);
+    gy[4] = om1m * gy[4] + cd1;
+}
+
+template <typename C, int COUPLING>
+__device__ __forceinline__ void collide(C f[9], C gx[5], C gy[5], const StepParams<C>& p) {
+    if (COUPLING == 1)
+        collide_node_lorentz<C>(f, gx, gy, p);
+    else
+        collide_node<C>(f, gx, gy, p);
 }
 
 // One node of the fused step (hot-path steps a1-a6): pull-stream from (fin, gin), wall closure,
@@ -202,12 +305,10 @@ __device__ __forceinline__ void moment_closure_top(C f[9], C gx[5], C gy[5], con
 // link-based wall rows take the unknown incoming populations from the same node's outgoing ones
 // (Sec. VI, App. B.1), which nobody else reads; moment-based wall rows reconstruct them from the
 // pulled ones (Sec. VII, App. A, App. B.2).
-template <typename S, typename C, int CLOSURE, typename L>
+template <typename S, typename C, int CLOSURE, typename L, int COUPLING = 0>
 __device__ __forceinline__ void step_node_with(const S* fin, const S* gin, S* fout, S* gout, const StepParams<C>& p,
-                                               int64_t n) {
+                                               int64_t n, int i, int j) {
     const int nx = p.nx;
-    const int j = (int)(n / nx);
-    const int i = (int)(n - (int64_t)j * nx);
     const int64_t N = p.N;
     const int64_t rc = n - i;    // start of row j
     const int64_t rs = rc - nx;  // row j-1
@@ -263,11 +364,11 @@ __device__ __forceinline__ void step_node_with(const S* fin, const S* gin, S* fo
             gy[4] = -L::ld(gyin + 2 * N + rc + i);
         }
     } else {
-        if (bottom) moment_closure_bottom<C>(f, gx, gy, p.bot, p.B0);
-        if (top) moment_closure_top<C>(f, gx, gy, p.top, p.B0);
+        if (bottom) moment_closure_bottom<C, COUPLING>(f, gx, gy, p.bot, p);
+        if (top) moment_closure_top<C, COUPLING>(f, gx, gy, p.top, p);
     }
     // a3-a5
-    collide_node<C>(f, gx, gy, p);
+    collide<C, COUPLING>(f, gx, gy, p);
     // a6: store
     S* gxo = gout;
     S* gyo = gout + 5 * N;
@@ -279,11 +380,33 @@ __device__ __forceinline__ void step_node_with(const S* fin, const S* gin, S* fo
     for (int a = 0; a < 5; ++a) store_s<S, C>(gyo + a * N + n, gy[a]);
 }
 
-// step_node with the read-only loads (RO) or plain coherent loads.
-template <typename S, typename C, int CLOSURE, bool RO>
+// step_node with the read-only (RO) or plain coherent loads; (i, j) are n's column and row.
+template <typename S, typename C, int CLOSURE, bool RO, int COUPLING = 0>
 __device__ __forceinline__ void step_node(const S* fin, const S* gin, S* fout, S* gout, const StepParams<C>& p,
-                                          int64_t n) {
-    step_node_with<S, C, CLOSURE, Loader<S, C, RO>>(fin, gin, fout, gout, p, n);
+                                          int64_t n, int i, int j) {
+    step_node_with<S, C, CLOSURE, Loader<S, C, RO>, COUPLING>(fin, gin, fout, gout, p, n, i, j);
 }
+
+// Walks a thread's nodes n = first, first + stride, ... of an nx-wide lattice keeping (i, j) up
+// to date with additions only (no per-node division).
+struct NodeWalker {
+    int64_t n;
+    int i, j, di, dj, nx;
+    __device__ __forceinline__ NodeWalker(int64_t first, int64_t stride, int nx_) : n(first), nx(nx_) {
+        j = (int)(first / nx_);
+        i = (int)(first - (int64_t)j * nx_);
+        dj = (int)(stride / nx_);
+        di = (int)(stride - (int64_t)dj * nx_);
+    }
+    __device__ __forceinline__ void next(int64_t stride) {
+        n += stride;
+        i += di;
+        j += dj;
+        if (i >= nx) {
+            i -= nx;
+            ++j;
+        }
+    }
+};
 
 }  // namespace lks

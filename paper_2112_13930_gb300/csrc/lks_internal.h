@@ -29,6 +29,8 @@ inline StepParams<C> convert_params(const StepParams<double>& d) {
     o.sw0 = (C)d.sw0;
     o.sw1 = (C)d.sw1;
     o.sw5 = (C)d.sw5;
+    o.src3 = (C)d.src3;
+    o.coupling = d.coupling;
     const WallCoef<double>* src[2] = {&d.bot, &d.top};
     WallCoef<C>* dst[2] = {&o.bot, &o.top};
     for (int k = 0; k < 2; ++k) {
@@ -44,7 +46,7 @@ inline StepParams<C> convert_params(const StepParams<double>& d) {
 // Step parameters (relaxation rates, force, field and both walls' closure coefficients) of a
 // channel; c = INFINITY selects each closure's perfectly conducting limit.
 StepParams<double> make_step_params(int nx, int ny, int closure, double tau_f, double tau_m, double B0, double Fx,
-                                    double c_bot, double c_top, double u_bot, double u_top);
+                                    double c_bot, double c_top, double u_bot, double u_top, int coupling = 0);
 
 // Bytes per stored population for each lks_storage value.
 inline size_t storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
@@ -58,22 +60,24 @@ cudaError_t launch_init(int storage, void* f, void* g, int nx, int ny, double B0
                         cudaStream_t st);
 
 // Moments of a stored state: out[m*N + n] (what = 0) or x-averaged profiles out[m*ny + j] (what = 1).
+// coupling / tau_m: the moment model of the state (0: Maxwell stress; 1: Lorentz force, which needs tau_m).
 cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                           int what, double* out, cudaStream_t st);
+                           int what, double* out, cudaStream_t st, int coupling = 0, double tau_m = 1.0);
 
 // Residual partial sums: nblk blocks write partial[4*blk + k] = (sum du^2, sum u^2, sum db^2, sum b^2)
 // and refresh the snapshot snap[0..N) = u_x, snap[N..2N) = B_x; then one block reduces in fixed order
 // into out[0..4).
 int residual_blocks(int64_t N);
 cudaError_t launch_residual(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                            double* snap, double* partial, double* out, cudaStream_t st);
+                            double* snap, double* partial, double* out, cudaStream_t st, int coupling = 0,
+                            double tau_m = 1.0);
 cudaError_t launch_snapshot(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                            double* snap, cudaStream_t st);
+                            double* snap, cudaStream_t st, int coupling = 0, double tau_m = 1.0);
 
 // FP64 absolute populations <-> stored deviations.
 cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, double B0, double* fabs,
-                          double* gabs, cudaStream_t st);
+                          double* gabs, cudaStream_t st, int coupling = 0);
 cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, double B0, void* f,
-                            void* g, cudaStream_t st);
+                            void* g, cudaStream_t st, int coupling = 0);
 
 }  // namespace lks

@@ -14,13 +14,25 @@
 
 namespace lks {
 
-template <typename S, typename C, int CLOSURE>
+// ROWS2D: grid (ceil(nx/256), ny), the column and row come from the block indices; otherwise a
+// 1D grid over n = y*nx + x (narrow lattices), split with one 32-bit division.
+template <typename S, typename C, int CLOSURE, int COUPLING, bool ROWS2D>
 __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
                                                    S* __restrict__ fout, S* __restrict__ gout,
                                                    const StepParams<C> p) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= p.N) return;
-    step_node<S, C, CLOSURE, true>(fin, gin, fout, gout, p, n);
+    int i, j;
+    if (ROWS2D) {
+        i = blockIdx.x * blockDim.x + threadIdx.x;
+        j = blockIdx.y;
+        if (i >= p.nx) return;
+    } else {
+        const unsigned n32 = blockIdx.x * blockDim.x + threadIdx.x;
+        if ((int64_t)n32 >= p.N) return;
+        j = (int)(n32 / (unsigned)p.nx);
+        i = (int)(n32 - (unsigned)j * (unsigned)p.nx);
+    }
+    const int64_t n = (int64_t)j * p.nx + i;
+    step_node<S, C, CLOSURE, true, COUPLING>(fin, gin, fout, gout, p, n, i, j);
 }
 
 // 16-bit storage moves 2 bytes per population, so the one-node kernel issues twice the load/store
@@ -53,20 +65,31 @@ struct Packed<__half> {
     }
 };
 
-template <typename S, int CLOSURE>
-__global__ void __launch_bounds__(256) step_kernel_pair(const S* __restrict__ fin, const S* __restrict__ gin,
+template <typename S, int CLOSURE, int COUPLING, bool ROWS2D>
+__global__ void __launch_bounds__(256, 4) step_kernel_pair(const S* __restrict__ fin, const S* __restrict__ gin,
                                                         S* __restrict__ fout, S* __restrict__ gout,
                                                         const StepParams<float> p) {
     typedef Packed<S> P;
     const unsigned FULL = 0xffffffffu;
     const int nx = p.nx, npr = nx >> 1;
     const int64_t N = p.N, NP = N >> 1;
-    const int64_t q0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = q0 < NP;
-    const int64_t q = active ? q0 : NP - 1;      // inactive lanes still take part in the shuffles
     const int lane = threadIdx.x & 31;
-    const int j = (int)(q / npr);
-    const int ip = (int)(q - (int64_t)j * npr);
+    // inactive lanes (past the end) still take part in the shuffles, on a clamped pair
+    int j, ip;
+    bool active;
+    if (ROWS2D) {
+        const int ip0 = blockIdx.x * blockDim.x + threadIdx.x;
+        active = ip0 < npr;
+        ip = active ? ip0 : npr - 1;
+        j = blockIdx.y;
+    } else {
+        const unsigned q0 = blockIdx.x * blockDim.x + threadIdx.x;
+        active = (int64_t)q0 < NP;
+        const unsigned q1 = active ? q0 : (unsigned)(NP - 1);
+        j = (int)(q1 / (unsigned)npr);
+        ip = (int)(q1 - (unsigned)j * (unsigned)npr);
+    }
+    const int64_t q = (int64_t)j * npr + ip;
     const int x0 = ip << 1;
     const int64_t rc = (int64_t)j * npr;         // row starts, in pairs
     const int64_t rs = rc - npr, rn = rc + npr;
@@ -155,17 +178,17 @@ __global__ void __launch_bounds__(256) step_kernel_pair(const S* __restrict__ fi
         }
     } else {
         if (bottom) {
-            moment_closure_bottom<float>(fA, gxA, gyA, p.bot, p.B0);
-            moment_closure_bottom<float>(fB, gxB, gyB, p.bot, p.B0);
+            moment_closure_bottom<float, COUPLING>(fA, gxA, gyA, p.bot, p);
+            moment_closure_bottom<float, COUPLING>(fB, gxB, gyB, p.bot, p);
         }
         if (top) {
-            moment_closure_top<float>(fA, gxA, gyA, p.top, p.B0);
-            moment_closure_top<float>(fB, gxB, gyB, p.top, p.B0);
+            moment_closure_top<float, COUPLING>(fA, gxA, gyA, p.top, p);
+            moment_closure_top<float, COUPLING>(fB, gxB, gyB, p.top, p);
         }
     }
     // a3-a5
-    collide_node<float>(fA, gxA, gyA, p);
-    collide_node<float>(fB, gxB, gyB, p);
+    collide<float, COUPLING>(fA, gxA, gyA, p);
+    collide<float, COUPLING>(fB, gxB, gyB, p);
     // a6: store both nodes of each plane as one word
     if (!active) return;
     uint32_t* fo = reinterpret_cast<uint32_t*>(fout);
@@ -178,29 +201,55 @@ __global__ void __launch_bounds__(256) step_kernel_pair(const S* __restrict__ fi
     for (int a = 0; a < 5; ++a) go[(5 + a) * NP + q] = P::pack(gyA[a], gyB[a]);
 }
 
+// A row-per-grid-row layout when rows are wide enough to fill blocks and ny fits gridDim.y.
+static bool rows2d(int row_items, int ny) { return row_items >= 64 && ny <= 65535; }
+
+template <typename S, bool R2>
+static void launch_pair_grid(const S* fi, const S* gi, S* fo, S* go, const StepParams<float>& p, int closure,
+                             dim3 grid, cudaStream_t st) {
+    if (p.coupling == 0) {
+        if (closure == 0) step_kernel_pair<S, 0, 0, R2><<<grid, 256, 0, st>>>(fi, gi, fo, go, p);
+        else step_kernel_pair<S, 1, 0, R2><<<grid, 256, 0, st>>>(fi, gi, fo, go, p);
+    } else {
+        if (closure == 0) step_kernel_pair<S, 0, 1, R2><<<grid, 256, 0, st>>>(fi, gi, fo, go, p);
+        else step_kernel_pair<S, 1, 1, R2><<<grid, 256, 0, st>>>(fi, gi, fo, go, p);
+    }
+}
+
 template <typename S>
 static cudaError_t launch_pair(const void* fin, const void* gin, void* fout, void* gout, const StepParams<float>& p,
                                int closure, cudaStream_t st) {
-    const int threads = 256;
-    const int64_t blocks = (p.N / 2 + threads - 1) / threads;
-    if (closure == 0)
-        step_kernel_pair<S, 0><<<(unsigned)blocks, threads, 0, st>>>((const S*)fin, (const S*)gin, (S*)fout, (S*)gout, p);
+    const int npr = p.nx / 2;
+    if (rows2d(npr, p.ny))
+        launch_pair_grid<S, true>((const S*)fin, (const S*)gin, (S*)fout, (S*)gout, p, closure,
+                                  dim3((npr + 255) / 256, p.ny), st);
     else
-        step_kernel_pair<S, 1><<<(unsigned)blocks, threads, 0, st>>>((const S*)fin, (const S*)gin, (S*)fout, (S*)gout, p);
+        launch_pair_grid<S, false>((const S*)fin, (const S*)gin, (S*)fout, (S*)gout, p, closure,
+                                   dim3((unsigned)((p.N / 2 + 255) / 256)), st);
     return cudaGetLastError();
+}
+
+template <typename S, typename C, bool R2>
+static void launch_typed_grid(const S* fi, const S* gi, S* fo, S* go, const StepParams<C>& p, int closure,
+                              dim3 grid, cudaStream_t st) {
+    if (p.coupling == 0) {
+        if (closure == 0) step_kernel<S, C, 0, 0, R2><<<grid, 256, 0, st>>>(fi, gi, fo, go, p);
+        else step_kernel<S, C, 1, 0, R2><<<grid, 256, 0, st>>>(fi, gi, fo, go, p);
+    } else {
+        if (closure == 0) step_kernel<S, C, 0, 1, R2><<<grid, 256, 0, st>>>(fi, gi, fo, go, p);
+        else step_kernel<S, C, 1, 1, R2><<<grid, 256, 0, st>>>(fi, gi, fo, go, p);
+    }
 }
 
 template <typename S, typename C>
 static cudaError_t launch_typed(const void* fin, const void* gin, void* fout, void* gout, const StepParams<C>& p,
                                 int closure, cudaStream_t st) {
-    const int threads = 256;
-    const int64_t blocks = (p.N + threads - 1) / threads;
-    if (closure == 0)
-        step_kernel<S, C, 0><<<(unsigned)blocks, threads, 0, st>>>((const S*)fin, (const S*)gin, (S*)fout,
-                                                                    (S*)gout, p);
+    if (rows2d(p.nx, p.ny))
+        launch_typed_grid<S, C, true>((const S*)fin, (const S*)gin, (S*)fout, (S*)gout, p, closure,
+                                      dim3((p.nx + 255) / 256, p.ny), st);
     else
-        step_kernel<S, C, 1><<<(unsigned)blocks, threads, 0, st>>>((const S*)fin, (const S*)gin, (S*)fout,
-                                                                    (S*)gout, p);
+        launch_typed_grid<S, C, false>((const S*)fin, (const S*)gin, (S*)fout, (S*)gout, p, closure,
+                                       dim3((unsigned)((p.N + 255) / 256)), st);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,8 @@ F64, F32, BF16_DEV, F16_DEV = 0, 1, 2, 3
 MOMENTS_NODES, MOMENTS_PROFILES = 0, 1
 
 CLOSURES = {"link": LINK, "moment": MOMENT, LINK: LINK, MOMENT: MOMENT}
+MAXWELL, LORENTZ = 0, 1
+COUPLINGS = {"maxwell": MAXWELL, "lorentz": LORENTZ, MAXWELL: MAXWELL, LORENTZ: LORENTZ}
 STORAGES = {"f64": F64, "f32": F32, "bf16": BF16_DEV, "f16": F16_DEV,
             F64: F64, F32: F32, BF16_DEV: BF16_DEV, F16_DEV: F16_DEV}
 STORAGE_BYTES = {F64: 8, F32: 4, BF16_DEV: 2, F16_DEV: 2}
@@ -45,6 +47,8 @@ class LksParams(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("dev_buffer", ctypes.c_void_p),
         ("dev_buffer_bytes", ctypes.c_size_t),
+        ("coupling", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 
@@ -116,10 +120,11 @@ def _dptr(a):
 
 
 def make_params(nx, ny, tau_f, tau_m, B0, Fx=0.0, closure="link", storage="f64", seed=0, perturb_amp=0.0,
-                stream=0, dev_buffer=0, dev_buffer_bytes=0):
+                stream=0, dev_buffer=0, dev_buffer_bytes=0, coupling="maxwell"):
     return LksParams(nx=nx, ny=ny, closure=CLOSURES[closure], storage=STORAGES[storage], tau_f=tau_f, tau_m=tau_m,
                      B0=B0, Fx=Fx, seed=seed, perturb_amp=perturb_amp, cuda_stream=stream or None,
-                     dev_buffer=dev_buffer or None, dev_buffer_bytes=dev_buffer_bytes)
+                     dev_buffer=dev_buffer or None, dev_buffer_bytes=dev_buffer_bytes, coupling=COUPLINGS[coupling],
+                     pad=0)
 
 
 def footprint_bytes(nx, ny, closure="link", storage="f64", tau_f=0.8, tau_m=0.8):
@@ -131,7 +136,7 @@ class Lattice:
     """One channel lattice resident on the GPU (a wrapped lks_handle)."""
 
     def __init__(self, nx, ny, tau_f, tau_m, B0, Fx=0.0, closure="link", storage="f64", seed=0, perturb_amp=0.0,
-                 stream=None, torch_memory=True):
+                 stream=None, torch_memory=True, coupling="maxwell"):
         import torch
         L = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -142,7 +147,8 @@ class Lattice:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
-        p = make_params(nx, ny, tau_f, tau_m, B0, Fx, closure, storage, seed, perturb_amp, stream.cuda_stream)
+        p = make_params(nx, ny, tau_f, tau_m, B0, Fx, closure, storage, seed, perturb_amp, stream.cuda_stream,
+                        coupling=coupling)
         self.nbytes = int(L.lks_footprint_bytes(ctypes.byref(p)))
         if self.nbytes == 0:
             raise LksError(LKS_EINVAL, "invalid lattice parameters")
@@ -218,6 +224,19 @@ class Lattice:
         g = np.ascontiguousarray(g, dtype=np.float64)
         assert f.shape == (9, self.ny, self.nx) and g.shape == (2, 5, self.ny, self.nx)
         _check(load().lks_set_state(self._h, _dptr(f), _dptr(g)), self._h)
+
+    def save(self, path, **meta):
+        """Checkpoint: the state (FP64 absolute populations via lks_get_state) and the step count."""
+        f, g = self.get_state()
+        np.savez(path, f=f, g=g, steps=self.steps, nx=self.nx, ny=self.ny, **meta)
+
+    def load(self, path):
+        """Resume from a checkpoint written by save() for a lattice of the same shape."""
+        d = np.load(path)
+        if int(d["nx"]) != self.nx or int(d["ny"]) != self.ny:
+            raise ValueError("checkpoint shape %dx%d does not match %dx%d" % (d["nx"], d["ny"], self.nx, self.ny))
+        self.set_state(d["f"], d["g"])
+        return int(d["steps"])
 
     def sync(self):
         _check(load().lks_sync(self._h), self._h)

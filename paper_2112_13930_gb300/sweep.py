@@ -44,26 +44,37 @@ def analytic_error(spec, u, b, tau=TAU):
 
 
 def run_batched(specs, storage="f32", tol=1e-10, check_every=100, quantum=20000, max_steps=10**9, shape=None,
-                tune_candidates=None, time_budget=None):
+                tune_candidates=None, time_budget=None, tail_shape=(128, 1, 8), tail_below=None):
     """Admit every instance into one batch and run persistent launches of `quantum` steps until
     none is running.  Returns per-instance records and the wall time.  An instance's
-    time-to-steady is the wall time at the end of the launch in which it left RUNNING."""
+    time-to-steady is the wall time at the end of the launch in which it left RUNNING.
+
+    Shape policy: the autotuned (or given) shape while many instances run; once fewer than
+    `tail_below` (default: the number of SMs) remain, `tail_shape` -- clusters of CTAs on several
+    SMs per instance -- so the last, longest instances advance faster per step."""
     import torch
     descs = [make_desc(s, tol, check_every, max_steps) for s in specs]
     pool = sum(_batch.instance_footprint(d, storage) for d in descs) + (1 << 20)
     b = _batch.Batch(storage, max_instances=len(descs), pool_bytes=pool,
-                     threads_per_group=shape[0] if shape else 0, groups_per_cta=shape[1] if shape else 0)
+                     threads_per_group=shape[0] if shape else 0, groups_per_cta=shape[1] if shape else 0,
+                     cluster_ctas=shape[2] if shape and len(shape) > 2 else 0)
     slots = [b.add(d) for d in descs]
     tune = None
     if tune_candidates:
         best, secs = b.autotune(tune_candidates, probe_steps=200)
         tune = {"best": list(best), "seconds": secs, "candidates": [list(c) for c in tune_candidates]}
+    if tail_below is None:
+        tail_below = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     done_at = [None] * len(slots)
     running = len(slots)
     launches = 0
+    tail_at = None
     while running:
+        if tail_shape and tail_at is None and running < tail_below:
+            b.set_shape(*tail_shape)
+            tail_at = time.perf_counter() - t0
         running = b.run(quantum)
         launches += 1
         now = time.perf_counter() - t0
@@ -83,7 +94,7 @@ def run_batched(specs, storage="f32", tol=1e-10, check_every=100, quantum=20000,
                      "t_done": done_at[k], "l2_u": eu, "l2_b": eb, "nodes": spec["nx"] * spec["ny"],
                      "u": u, "b": bx})
     b.close()
-    return {"records": recs, "wall": wall, "launches": launches, "tune": tune}
+    return {"records": recs, "wall": wall, "launches": launches, "tune": tune, "tail_shape_at": tail_at}
 
 
 def run_one_at_a_time(specs, storage="f64", tol=1e-10, check_every=100, max_steps=10**9):

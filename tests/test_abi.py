@@ -83,10 +83,13 @@ def test_footprint_counts_both_buffers(lib):
     (dict(nx=4, ny=8, closure="link", tau_f=0.5), False),
     (dict(nx=4, ny=8, closure="link", tau_m=0.4), False),
     (dict(nx=4, ny=8, closure="link", tau_m=math.nan), False),
+    (dict(nx=4, ny=8, closure="moment", tau_m=0.8, coupling="lorentz"), True),
+    (dict(nx=4, ny=8, closure="moment", tau_m=1.0, coupling="lorentz"), False),
+    (dict(nx=4, ny=8, closure="moment", tau_m=1.0, coupling="maxwell"), True),
 ])
 def test_parameter_validation(lib, kw, ok):
     p = lks.make_params(kw.get("nx"), kw.get("ny"), kw.get("tau_f", 0.8), kw.get("tau_m", 0.8), 0.01,
-                        closure=kw["closure"])
+                        closure=kw["closure"], coupling=kw.get("coupling", "maxwell"))
     assert (lib.lks_footprint_bytes(ctypes.byref(p)) > 0) == ok
 
 

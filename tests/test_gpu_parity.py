@@ -280,3 +280,90 @@ def test_pair_kernel_perturbed_matches_oracle_one_step(lks, storage):
         assert np.max(np.abs(fg - o.f)) <= 8 * ONE_STEP[storage] * np.max(np.abs(o.f - o0.f))
         assert np.max(np.abs(gg - o.g)) <= 8 * ONE_STEP[storage] * np.max(np.abs(o.g - o0.g))
         g.close()
+
+
+# ---- the paper's own coupling (Lorentz force in the source), kernel variant ----
+
+def _pair_lorentz(lks, nx, ny, closure, storage="f64", tau_f=0.7, tau_m=0.9, B0=0.03, Fx=0.0, c=(0.0, 0.0),
+                  u=(0.0, 0.0), seed=0, amp=0.0):
+    cl = oracle.LINK if closure == "link" else oracle.MOMENT
+    o = oracle.Oracle(nx, ny, tau_f, tau_m, B0, Fx, cl, c[0], c[1], u[0], u[1], seed=seed, perturb_amp=amp,
+                      coupling=1)
+    g = lks.Lattice(nx, ny, tau_f, tau_m, B0, Fx, closure, storage, seed=seed, perturb_amp=amp, coupling="lorentz")
+    g.set_walls(c[0], c[1], u[0], u[1])
+    return o, g
+
+
+@pytest.mark.parametrize("case", CASES[:5], ids=lambda c: "%s-%dx%d" % (c["closure"], c["nx"], c["ny"]))
+def test_lorentz_fp64_parity_cases(lks, case):
+    """Lorentz-force coupling (the oracle iterates u and J to a fixed point, the kernel solves the
+    linear system exactly): FP64 parity <= 1e-11 on populations and moments."""
+    o, g = _pair_lorentz(lks, case["nx"], case["ny"], case["closure"], "f64", B0=0.04, Fx=case["Fx"], c=case["c"],
+                         u=case["u"], seed=99, amp=case["amp"])
+    for n in (1, 7, 130):
+        o.step(n)
+        g.step(n)
+        _compare_fields(o, g, REL64, REL64)
+
+
+@pytest.mark.parametrize("closure", ["link", "moment"])
+def test_lorentz_hartmann_channel_fp64_and_analytic(lks, closure):
+    ny, ha, c = 65, 10.0, 0.5
+    a = ny / 2 if closure == "link" else (ny - 1) / 2
+    b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+    fx = an.force_for_centre_speed(0.01, ha, c, a, 0.8)
+    o, g = _pair_lorentz(lks, 4, ny, closure, "f64", tau_f=0.8, tau_m=0.8, B0=b0, Fx=fx, c=(c, c))
+    o.step(20000)
+    g.step(20000)
+    _compare_fields(o, g, REL64, REL64)
+    u, b = g.profiles()
+    ua, ba = an.hartmann_profiles(g.y(), a, ha, c, fx, 0.8, 0.8)
+    assert an.rel_l2(u, ua) < 5e-3 and an.rel_l2(b, ba) < 5e-3
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("closure", ["link", "moment"])
+def test_lorentz_reduced_precision(lks, storage, closure):
+    """Same bounds as the Maxwell-stress coupling: one step within 8 u_s, 2000 steps within the
+    long-run bounds."""
+    o, g = _pair_lorentz(lks, 38, 11, closure, storage, B0=0.02, Fx=1e-5, c=(0.4, 3.0), u=(0.0, 0.04), seed=17,
+                         amp=1e-2)
+    o0 = oracle.Oracle(38, 11, 0.7, 0.9, 0.02, 1e-5, oracle.LINK, coupling=1)
+    o.step(1)
+    g.step(1)
+    fg, gg = g.get_state()
+    assert np.max(np.abs(fg - o.f)) <= 8 * ONE_STEP[storage] * np.max(np.abs(o.f - o0.f))
+    assert np.max(np.abs(gg - o.g)) <= 8 * ONE_STEP[storage] * np.max(np.abs(o.g - o0.g))
+    o.step(1999)
+    g.step(1999)
+    mo, mg = o.moments(), g.moments()
+    tu, tb = LONG_RUN[storage]
+    assert _relmax(mg[1], mo[1]) <= tu and _relmax(mg[3], mo[3]) <= tb
+
+
+def test_lorentz_pair_kernel_bitwise(lks):
+    out = []
+    for nx in (37, 38):
+        g = lks.Lattice(nx, 21, 0.7, 0.9, 0.02, 2e-5, "moment", "f16", coupling="lorentz")
+        g.set_walls(0.4, math.inf, 0.0, 0.04)
+        g.step(150)
+        f, gg = g.get_state()
+        out.append((f[:, :, 0].copy(), gg[:, :, :, 0].copy()))
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_checkpoint_resume(lks, tmp_path):
+    """save() / load() round trip: a run resumed from a checkpoint continues like the original."""
+    o, g = _pair(lks, 40, 12, "moment", "f64", B0=0.02, Fx=1e-5, c=(0.3, 2.0), u=(0.0, 0.03), seed=4, amp=1e-2)
+    g.step(37)
+    path = str(tmp_path / "ckpt.npz")
+    g.save(path)
+    h = lks.Lattice(40, 12, 0.8, 0.8, 0.02, 1e-5, "moment", "f64")
+    h.set_walls(0.3, 2.0, 0.0, 0.03)
+    assert h.load(path) == 37
+    g.step(50)
+    h.step(50)
+    fg, gg = g.get_state()
+    fh, gh = h.get_state()
+    assert np.max(np.abs(fg - fh)) < 1e-15 and np.max(np.abs(gg - gh)) < 1e-15
