@@ -621,6 +621,59 @@ def bench_validation(args):
     return 0
 
 
+def bench_c1(args):
+    """Body-force Hartmann channel, 4 x 65 nodes, walls at y = +-a with the Shercliff condition
+    (link-based closure), B0 from Ha = 10, c = 0.1, tau_f = tau_m = 0.8, FP64, 2e4 steps: GPU wall
+    time for the 2e4 steps, parity with the FP64 oracle, and the profile against the closed form."""
+    import numpy as np
+    import torch
+    from paper_2112_13930_gb300 import build, lks, profiles
+    torch.cuda.set_device(0)
+    build.build()
+    lks.load()
+    nx, ny, ha, c, tau, steps = 4, 65, 10.0, 0.1, 0.8, 20000
+    a, y = profiles.node_y(ny, "link")
+    nu = (tau - 0.5) / 3.0
+    b0 = ha * nu / a
+    fx = profiles.hartmann_force(0.01, ha, c, a, tau)
+    lat = lks.Lattice(nx, ny, tau, tau, b0, fx, "link", "f64")
+    lat.set_walls(c, c)
+    lat.step(64)
+    lat2 = lks.Lattice(nx, ny, tau, tau, b0, fx, "link", "f64")
+    lat2.set_walls(c, c)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat2.step(steps)
+    lat2.sync()
+    t_gpu = time.perf_counter() - t0
+    u, b = lat2.profiles()
+    ua, ba = profiles.hartmann(y, a, ha, c, fx, tau, tau)
+    out = {"workload": "c1", "config": {"nx": nx, "ny": ny, "Ha": ha, "c": c, "tau": tau, "B0": b0, "Fx": fx,
+                                        "closure": "link", "storage": "f64", "steps": steps},
+           "gpu_wall_s": round(t_gpu, 4), "gpu_mlups": round(nx * ny * steps / t_gpu / 1e6, 2),
+           "gpu_us_per_step": round(t_gpu / steps * 1e6, 3),
+           "l2_vs_closed_form": {"u": profiles.rel_l2(u, ua), "B": profiles.rel_l2(b, ba)}}
+    if not args.skip_cpu:
+        import oracle
+        o = oracle.Oracle(nx, ny, tau, tau, b0, fx, oracle.LINK, c, c)
+        t0 = time.perf_counter()
+        o.step(steps)
+        t_cpu = time.perf_counter() - t0
+        fg, gg = lat2.get_state()
+        out["oracle_wall_s"] = round(t_cpu, 3)
+        out["oracle_cores"] = oracle.threads_used()
+        out["fp64_parity_max_rel"] = max(float(np.max(np.abs(fg - o.f)) / np.max(np.abs(o.f))),
+                                         float(np.max(np.abs(gg - o.g)) / np.max(np.abs(o.g))))
+    steps_ss, r, status = lat.run_to_steady(1e-10, 100, 2_000_000, raise_on_fail=False)
+    u2, b2 = lat.profiles()
+    out["to_steady"] = {"steps": steps_ss + 64, "residual": r, "status": int(status),
+                        "l2_u": profiles.rel_l2(u2, ua), "l2_B": profiles.rel_l2(b2, ba)}
+    lat.close()
+    lat2.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # FP64 arithmetic per bulk node per step in collide_node, counted from the source with an FMA as
 # 2 flops: moments and 1/rho (Newton) 40, equilibrium set-up 23, nine directions 116, g 33.
 FP64_FLOPS_PER_NODE = 212
@@ -640,7 +693,10 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["main", "precision", "sweep", "serve", "validation"], default="main")
+    ap.add_argument("--workload", choices=["main", "c1", "precision", "sweep", "serve", "validation"], default="main")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=None,
+                    help="preset of the five benchmark configurations: 1 = c1, 2 = main, 3 = precision, "
+                         "4 = sweep, 5 = serve")
     ap.add_argument("--validation-out", default="validation_out")
     ap.add_argument("--precision-steps", type=int, default=1000)
     ap.add_argument("--precision-max-steps", type=int, default=3_000_000)
@@ -659,8 +715,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.config is not None:
+        args.workload = {1: "c1", 2: "main", 3: "precision", 4: "sweep", 5: "serve"}[args.config]
     if args.impl == "reference":
         return bench_reference(args)
+    if args.workload == "c1":
+        return bench_c1(args)
     if args.workload == "precision":
         return bench_precision(args)
     if args.workload == "sweep":

@@ -9,6 +9,8 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lks.h"
 #include "lks_internal.h"
 
@@ -22,6 +24,12 @@ constexpr int64_t kGraphSteps = 64;  // even, so a graph returns the state to th
 constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// NVTX range around a C-ABI call (visible in Nsight tools; near-free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct Layout {
     size_t f_bytes, g_bytes, off_fa, off_ga, off_fb, off_gb, off_snap, off_partial, off_out, off_prof, total;
@@ -232,6 +240,7 @@ size_t lks_footprint_bytes(const lks_params* p) {
 }
 
 lks_status lks_create(const lks_params* p, lks_handle** out) {
+    NvtxRange nvtx_range("lks_create");
     if (!out) return fail(nullptr, LKS_EINVAL, "out is NULL");
     *out = nullptr;
     if (const char* m = validate(p)) return fail(nullptr, LKS_EINVAL, m);
@@ -302,6 +311,7 @@ lks_status lks_set_walls(lks_handle* h, double c_bottom, double c_top, double u_
 }
 
 lks_status lks_step(lks_handle* h, int64_t n) {
+    NvtxRange nvtx_range("lks_step");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (n < 0) return fail(h, LKS_EINVAL, "n must be >= 0");
     while (n >= kGraphSteps && !h->graphs_disabled) {
@@ -340,6 +350,7 @@ lks_status lks_moments_device(lks_handle* h, int what, double* dev_out) {
 }
 
 lks_status lks_moments(lks_handle* h, int what, double* host_out) {
+    NvtxRange nvtx_range("lks_moments");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_out) return fail(h, LKS_EINVAL, "host_out is NULL");
     if (what != LKS_MOMENTS_NODES && what != LKS_MOMENTS_PROFILES) return fail(h, LKS_EINVAL, "bad 'what'");
@@ -367,6 +378,7 @@ lks_status lks_moments(lks_handle* h, int what, double* host_out) {
 }
 
 lks_status lks_residual(lks_handle* h, double* r_u, double* r_b) {
+    NvtxRange nvtx_range("lks_residual");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     cudaError_t e = lks::launch_residual(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0,
                                          h->p.Fx, h->snap, h->partial, h->dout, h->stream, h->p.coupling,
@@ -387,6 +399,7 @@ lks_status lks_residual(lks_handle* h, double* r_u, double* r_b) {
 
 lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int64_t max_steps, int64_t* steps_out,
                              double* r_out) {
+    NvtxRange nvtx_range("lks_run_to_steady");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (check_every < 1 || max_steps < 0 || !(tol > 0.0)) return fail(h, LKS_EINVAL, "bad run_to_steady arguments");
     int64_t taken = 0;
@@ -411,6 +424,7 @@ lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int
 }
 
 lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g) {
+    NvtxRange nvtx_range("lks_get_state");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
     const size_t N = (size_t)h->p.nx * h->p.ny;
@@ -432,6 +446,7 @@ lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g) {
 }
 
 lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host_g) {
+    NvtxRange nvtx_range("lks_set_state");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
     const size_t N = (size_t)h->p.nx * h->p.ny;

@@ -18,6 +18,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lks_batch.h"
 #include "lks_internal.h"
 
@@ -731,6 +733,10 @@ lks_status lks_batch_add(lks_batch* b, const lks_instance_desc* d, int32_t* slot
 
 lks_status lks_batch_run(lks_batch* b, int64_t quantum, int32_t* n_running) {
     if (!b) return bfail(nullptr, LKS_EINVAL, "batch is NULL");
+    nvtxRangePushA("lks_batch_run");
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop;
     if (quantum < 1) return bfail(b, LKS_EINVAL, "quantum_steps must be >= 1");
     int nwork = 0;
     for (size_t k = 0; k < b->slots.size(); ++k)

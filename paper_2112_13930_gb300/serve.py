@@ -13,6 +13,12 @@ the GPU:
 
 Every result is the same as the request solved alone: the per-node update and the per-instance
 residual reduction do not depend on what else is resident.
+
+Failure handling (all on the host): a request the library rejects (LKS_EINVAL) is recorded as
+"rejected" and the server continues; an exception while solving a large-lane request is recorded
+as "error" and its stream and memory share are released; a request can be cancelled while queued
+or while in the small lane (its pool memory is freed at once) -- a large-lane request that is
+already solving finishes and is then reported as "cancelled".
 """
 import collections
 import concurrent.futures
@@ -29,26 +35,39 @@ from . import sweep as _sweep
 TAU = _sweep.TAU
 
 
+def _default_lattice(req, storage, stream):
+    p = _sweep.lattice_params(req)
+    lat = _lks.Lattice(req["nx"], req["ny"], TAU, TAU, p["B0"], p["Fx"], req["closure"], storage, stream=stream)
+    lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
+    return lat
+
+
 class Server:
     def __init__(self, storage="f32", budget_bytes=120 << 30, small_pool_bytes=8 << 30, small_max_nodes=32768,
                  max_small=8192, large_workers=6, tol=1e-9, check_every=100, quantum=2000, max_steps=10**9,
-                 shape=None):
-        import torch
+                 shape=None, batch=None, lattice_factory=None, streams=None):
         self.storage = storage
         self.tol, self.check_every, self.quantum, self.max_steps = tol, check_every, quantum, max_steps
         self.small_max_nodes = small_max_nodes
         small_pool_bytes = min(small_pool_bytes, budget_bytes // 2)
         self.large_budget = budget_bytes - small_pool_bytes
         self.large_used = 0
-        self.batch = _batch.Batch(storage, max_instances=max_small, pool_bytes=small_pool_bytes,
-                                  threads_per_group=shape[0] if shape else 0, groups_per_cta=shape[1] if shape else 0)
+        if batch is None:
+            batch = _batch.Batch(storage, max_instances=max_small, pool_bytes=small_pool_bytes,
+                                 threads_per_group=shape[0] if shape else 0, groups_per_cta=shape[1] if shape else 0,
+                                 cluster_ctas=shape[2] if shape and len(shape) > 2 else 0)
+        self.batch = batch
+        self.lattice_factory = lattice_factory or (lambda req, stream: _default_lattice(req, storage, stream))
+        if streams is None:
+            import torch
+            streams = [torch.cuda.Stream() for _ in range(large_workers)]
+        self.streams = streams
         self.pool = concurrent.futures.ThreadPoolExecutor(max_workers=large_workers)
         self.large_workers = large_workers
         self.large_active = {}
-        self.streams = [torch.cuda.Stream() for _ in range(large_workers)]
         self.free_streams = list(range(large_workers))
-        self.lock = threading.Lock()
         self.small_slots = {}  # slot -> request record
+        self.cancelled = set()
 
     def is_small(self, req):
         return req["nx"] * req["ny"] <= self.small_max_nodes
@@ -60,21 +79,34 @@ class Server:
         return _lks.footprint_bytes(req["nx"], req["ny"], req["closure"], self.storage)
 
     # -- small lane ------------------------------------------------------------------------
-    def try_admit_small(self, req, now):
+    def try_admit_small(self, req, now, out):
+        """True when the request left the queue (admitted or rejected), False when it must wait."""
         d = _sweep.make_desc(req, self.tol, self.check_every, self.max_steps)
-        slot = self.batch.add(d)
+        try:
+            slot = self.batch.add(d)
+        except _lks.LksError as e:
+            out.append({"req": req, "t_admit": now, "lane": "small", "state": "rejected", "error": str(e),
+                        "steps": 0, "residual": math.inf, "t_done": now, "u": None, "b": None})
+            return True
         if slot is None:
             return False
-        rec = {"req": req, "t_admit": now, "lane": "small"}
-        self.small_slots[slot] = rec
+        self.small_slots[slot] = {"req": req, "t_admit": now, "lane": "small"}
         return True
 
     def collect_small(self, now, out):
         for slot in list(self.small_slots):
+            rec = self.small_slots[slot]
+            if rec["req"]["index"] in self.cancelled:
+                self.batch.remove(slot)
+                del self.small_slots[slot]
+                rec.update({"state": "cancelled", "steps": 0, "residual": math.inf, "t_done": now, "u": None,
+                            "b": None})
+                out.append(rec)
+                continue
             st, steps, r = self.batch.result(slot)
             if st == _batch.INST_RUNNING:
                 continue
-            rec = self.small_slots.pop(slot)
+            del self.small_slots[slot]
             u, b = self.batch.profiles(slot)
             self.batch.remove(slot)
             rec.update({"state": _batch.STATE_NAMES[st], "steps": int(steps), "residual": r, "t_done": now,
@@ -83,19 +115,23 @@ class Server:
 
     # -- large lane ------------------------------------------------------------------------
     def _solve_large(self, req, sidx):
-        p = _sweep.lattice_params(req)
-        lat = _lks.Lattice(req["nx"], req["ny"], TAU, TAU, p["B0"], p["Fx"], req["closure"], self.storage,
-                           stream=self.streams[sidx])
-        lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
-        steps, r, status = lat.run_to_steady(self.tol, self.check_every, self.max_steps, raise_on_fail=False)
-        u, b = lat.profiles()
-        lat.close()
+        lat = self.lattice_factory(req, self.streams[sidx])
+        try:
+            steps, r, status = lat.run_to_steady(self.tol, self.check_every, self.max_steps, raise_on_fail=False)
+            u, b = lat.profiles()
+        finally:
+            lat.close()
         state = {_lks.LKS_OK: "converged", _lks.LKS_ENOTCONVERGED: "max_steps",
                  _lks.LKS_EUNSTABLE: "unstable"}.get(status, "error")
         return {"state": state, "steps": int(steps), "residual": r, "u": u, "b": b}
 
-    def try_admit_large(self, req, now):
+    def try_admit_large(self, req, now, out):
         fp = self.footprint(req)
+        if fp == 0:
+            out.append({"req": req, "t_admit": now, "lane": "large", "state": "rejected",
+                        "error": "invalid parameters", "steps": 0, "residual": math.inf, "t_done": now,
+                        "u": None, "b": None})
+            return True
         if not self.free_streams or self.large_used + fp > self.large_budget:
             return False
         sidx = self.free_streams.pop()
@@ -107,16 +143,27 @@ class Server:
     def collect_large(self, now, out):
         for fut in [f for f in self.large_active if f.done()]:
             rec, sidx, fp = self.large_active.pop(fut)
-            rec.update(fut.result())
+            try:
+                rec.update(fut.result())
+            except Exception as e:  # the lattice could not be created or solved
+                rec.update({"state": "error", "error": "%s: %s" % (type(e).__name__, e), "steps": 0,
+                            "residual": math.inf, "u": None, "b": None})
+            if rec["req"]["index"] in self.cancelled:
+                rec["state"] = "cancelled"
             rec["t_done"] = now
             self.large_used -= fp
             self.free_streams.append(sidx)
             out.append(rec)
 
+    def cancel(self, index):
+        """Cancel request `index` (queued, in the small lane, or -- reported only -- in the large lane)."""
+        self.cancelled.add(index)
+
     # -- the loop ----------------------------------------------------------------------------
     def serve(self, trace, time_limit=None):
-        """Replay a trace (requests with t_arrival in seconds, sorted).  Returns one record per
-        finished request with arrival, admission and completion times (seconds from the start)."""
+        """Replay a trace (requests with t_arrival in seconds, sorted; optional `cancel_after` seconds).
+        Returns one record per request with arrival, admission and completion times (seconds from
+        the start) and its state."""
         t0 = time.perf_counter()
         q_small, q_large = collections.deque(), collections.deque()
         out = []
@@ -127,9 +174,18 @@ class Server:
             while i < n and trace[i]["t_arrival"] <= now:
                 (q_small if self.is_small(trace[i]) else q_large).append(trace[i])
                 i += 1
-            while q_small and self.try_admit_small(q_small[0], now):
+            for req in trace[:i]:
+                ca = req.get("cancel_after")
+                if ca is not None and now >= req["t_arrival"] + ca:
+                    self.cancel(req["index"])
+            for q in (q_small, q_large):
+                for req in [r for r in q if r["index"] in self.cancelled]:
+                    q.remove(req)
+                    out.append({"req": req, "t_admit": None, "lane": "queue", "state": "cancelled", "steps": 0,
+                                "residual": math.inf, "t_done": now, "u": None, "b": None})
+            while q_small and self.try_admit_small(q_small[0], now, out):
                 q_small.popleft()
-            while q_large and self.try_admit_large(q_large[0], now):
+            while q_large and self.try_admit_large(q_large[0], now, out):
                 q_large.popleft()
             if self.small_slots:
                 self.batch.run(self.quantum)
@@ -176,11 +232,12 @@ def serve_one_at_a_time(trace, storage="f64", tol=1e-9, check_every=100, max_ste
 
 
 def summarize(records, n_offered):
-    lat = np.array([r["latency"] for r in records]) if records else np.array([np.nan])
-    t_first = min(r["t_arrival"] for r in records) if records else 0.0
-    t_last = max(r["t_done"] for r in records) if records else 0.0
+    done = [r for r in records if r.get("state") not in ("rejected", "cancelled", "error")]
+    lat = np.array([r["latency"] for r in done]) if done else np.array([np.nan])
+    t_first = min(r["t_arrival"] for r in done) if done else 0.0
+    t_last = max(r["t_done"] for r in done) if done else 0.0
     states = collections.Counter(r.get("state", "done") for r in records)
-    return {"offered": n_offered, "completed": len(records),
-            "solves_per_s": len(records) / max(1e-9, t_last - t_first),
+    return {"offered": n_offered, "completed": len(done),
+            "solves_per_s": len(done) / max(1e-9, t_last - t_first),
             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
             "makespan_s": t_last - t_first, "states": dict(states)}
