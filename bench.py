@@ -34,6 +34,7 @@ def _workload(args):
         "workload": "Hartmann-Couette %dx%d, moment-based closure, U_w=0.05, Ha=20, c=1 both walls, "
                     "tau_f=tau_m=0.8, rest start" % (n, n),
         "nx": n, "ny": n, "closure": "moment", "storage": args.storage,
+        "buffers": "one, in place (pairs of steps)" if getattr(args, "inplace", False) else "two (ping-pong)",
         "l2": "inputs larger than L2 (%.2f GB of populations read per step vs 129 MB L2)"
               % (BYTES_PER_NODE[args.storage] / 2 * n * n / 1e9),
     }
@@ -240,8 +241,9 @@ def bench_ours(args):
     phys = _physics(n)
     stream = torch.cuda.current_stream()
 
-    def make(storage, nn=n):
-        lat = lks.Lattice(nn, nn, phys["tau_f"], phys["tau_m"], phys["B0"], phys["Fx"], "moment", storage)
+    def make(storage, nn=n, inplace=False):
+        lat = lks.Lattice(nn, nn, phys["tau_f"], phys["tau_m"], phys["B0"], phys["Fx"], "moment", storage,
+                          inplace=inplace)
         lat.set_walls(phys["c"], phys["c"], 0.0, phys["u_w"])
         return lat
 
@@ -254,7 +256,10 @@ def bench_ours(args):
         return replica_max(x, ws, "cuda")
 
     # --- main measurement -------------------------------------------------------------------
-    lat = make(args.storage)
+    if args.inplace:  # in-place handles step in pairs
+        args.steps += args.steps & 1
+        args.warmup += args.warmup & 1
+    lat = make(args.storage, inplace=args.inplace)
     lat.step(args.warmup)
     barrier()
     sampler = ClockSampler(local)
@@ -270,12 +275,13 @@ def bench_ours(args):
     peak, peak_kind = _peaks()
     bpn = BYTES_PER_NODE[args.storage]
     achieved = bpn * nodes / per_launch / 1e9
-    traffic = _ncu_traffic(args.storage, n)
+    traffic = None if args.inplace else _ncu_traffic(args.storage, n)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else
                 "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": bpn * nodes, "kernel": "step_kernel<%s,moment>" % args.storage}
+                "algorithmic_bytes_per_launch": bpn * nodes, "kernel": ("step_kernel_aa<%s,moment> (both phases)" if args.inplace else "step_kernel<%s,moment>")
+                % args.storage}
     # sanity: the state must still be finite
     ru, rb = lat.residual()
 
@@ -341,17 +347,22 @@ def bench_ours(args):
                                              "frac": round(al / peak, 4)}}
         ll.close()
         del ll
-        for st in ("bf16", "f16"):
-            lr = make(st)
-            lr.step(3)
+        # 16-bit deviation storage; then the in-place (one-buffer) step in FP32 and BF16
+        for key, st, inplace in (("bf16", "bf16", False), ("f16", "f16", False), ("inplace_f32", "f32", True),
+                                 ("inplace_bf16", "bf16", True)):
+            lr = make(st, inplace=inplace)
+            lr.step(4)
             barrier()
             kr = max(10, min(args.steps, 2000))
+            kr += kr & 1
             tr = max_over_ranks(_time_steps(lr, kr, stream))
             vr = nodes * kr * ws / tr / 1e6
-            ar = 76 * nodes / (tr / kr) / 1e9
-            extra[st] = {"value": round(vr, 1), "unit": UNIT, "steps": kr,
-                         "roofline": {"bound": "hbm", "achieved": round(ar, 1), "peak": peak, "unit": "GB/s",
-                                      "frac": round(ar / peak, 4)}}
+            ar = BYTES_PER_NODE[st] * nodes / (tr / kr) / 1e9
+            extra[key] = {"value": round(vr, 1), "unit": UNIT, "steps": kr,
+                          "roofline": {"bound": "hbm", "achieved": round(ar, 1), "peak": peak, "unit": "GB/s",
+                                       "frac": round(ar / peak, 4)}}
+            if inplace:
+                extra[key]["footprint_bytes"] = lr.nbytes
             lr.close()
             del lr
         torch.cuda.empty_cache()
@@ -571,25 +582,43 @@ def bench_serve(args):
     torch.cuda.set_device(0)
     build.build()
     lks.load()
-    trace = workloads.serve_trace(args.serve_requests, rate=2000.0, seed=5)
-    srv = serve.Server("f32", budget_bytes=120 << 30, small_pool_bytes=16 << 30, small_max_nodes=32768,
-                       large_workers=args.serve_workers, tol=1e-9, check_every=100, quantum=args.serve_quantum,
-                       max_steps=args.serve_max_steps)
-    recs = srv.serve(trace, time_limit=args.serve_time)
-    srv.close()
-    summ = serve.summarize(recs, len(trace))
+    from paper_2112_13930_gb300 import sweep
+
+    def replay(rate):
+        trace = workloads.serve_trace(args.serve_requests, rate=rate, seed=5)
+        srv = serve.Server("f32", budget_bytes=120 << 30, small_pool_bytes=16 << 30, small_max_nodes=32768,
+                           large_workers=args.serve_workers, tol=1e-9, check_every=100, quantum=args.serve_quantum,
+                           max_steps=args.serve_max_steps, inplace=args.serve_inplace)
+        recs = srv.serve(trace, time_limit=args.serve_time)
+        srv.close()
+        summ = serve.summarize(recs, len(trace))
+        errs = [max(sweep.analytic_error(r["req"], r["u"], r["b"])) for r in recs
+                if r.get("state") in serve.STEADY_STATES]
+        if errs:
+            summ["steady_vs_analytic_rel_l2"] = {"median": float(np.median(errs)), "max": float(np.max(errs)),
+                                                 "le_1e-4": int(sum(e <= 1e-4 for e in errs))}
+        lanes = {}
+        for r in recs:
+            lanes[r["lane"]] = lanes.get(r["lane"], 0) + 1
+        summ["lanes"] = lanes
+        summ["offered_rate_per_s"] = rate
+        return trace, summ
+
+    trace, summ = replay(args.serve_rate)
     base = serve.serve_one_at_a_time(trace[: args.serve_baseline], "f64", tol=1e-9, check_every=100,
                                      max_steps=args.serve_max_steps, time_limit=args.serve_time)
     bsum = serve.summarize(base, args.serve_baseline)
-    lanes = {}
-    for r in recs:
-        lanes[r["lane"]] = lanes.get(r["lane"], 0) + 1
     out = {"workload": "serve", "metric": "served solves/s", "unit": "solves/s", "higher_is_better": True,
-           "dtype": "f32", "value": round(summ["solves_per_s"], 3), "summary": summ, "lanes": lanes,
-           "offered_rate_per_s": 2000.0, "baseline_fp64_fifo": bsum,
+           "dtype": "f32", "value": round(summ["solves_per_s"], 3), "summary": summ,
+           "offered_rate_per_s": args.serve_rate, "baseline_fp64_fifo": bsum,
            "settings": {"requests": args.serve_requests, "max_steps": args.serve_max_steps,
+                        "buffers": "one, in place" if args.serve_inplace else "two",
                         "quantum": args.serve_quantum, "large_workers": args.serve_workers,
                         "time_limit_s": args.serve_time}}
+    if args.serve_underload > 0:
+        # the same requests offered below capacity: latency is then solve time, not queueing
+        _, under = replay(args.serve_underload * summ["solves_per_s"])
+        out["underload"] = under
     print(json.dumps(out), flush=True)
     return 0
 
@@ -687,6 +716,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f64", "bf16", "f16"], default="f32")
     ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--inplace", action="store_true",
+                    help="time the in-place (one-buffer) step instead of the two-buffer step")
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
@@ -712,6 +743,11 @@ def main():
     ap.add_argument("--serve-max-steps", type=int, default=200_000)
     ap.add_argument("--serve-workers", type=int, default=6)
     ap.add_argument("--serve-time", type=float, default=600.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-inplace", action="store_true",
+                    help="serve with one population buffer per request (in-place pairs of steps)")
+    ap.add_argument("--serve-underload", type=float, default=0.0,
+                    help="if > 0, replay the trace again at this fraction of the measured solves/s")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

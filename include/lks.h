@@ -101,12 +101,19 @@ typedef struct lks_params {
     void* dev_buffer;      /* optional caller-owned device memory (NULL = library allocates) */
     size_t dev_buffer_bytes; /* size of dev_buffer; must be >= lks_footprint_bytes() */
     int32_t coupling;      /* lks_coupling (0 = LKS_MAXWELL) */
-    int32_t pad;
+    int32_t inplace;       /* 0: two population buffers (each step reads one, writes the
+                              other); 1: one buffer updated in place, steps taken in pairs
+                              (the "AA" access pattern: the first step of a pair pulls from
+                              the neighbours and pushes into their opposite-direction slots,
+                              the second reads and writes only the node's own slots), half
+                              the population memory at the same bytes per step and the
+                              same results bit for bit; lks_step and lks_run_to_steady then
+                              take even step counts (LKS_EINVAL otherwise) */
 } lks_params;
 
 typedef struct lks_handle lks_handle;
 
-/* Device bytes a handle with these parameters needs (both population buffers,
+/* Device bytes a handle with these parameters needs (the population buffer(s),
  * residual snapshot, reduction and profile buffers); 0 if the parameters are
  * invalid.  Used for admission control. */
 size_t lks_footprint_bytes(const lks_params* p);
@@ -128,7 +135,8 @@ lks_status lks_create(const lks_params* p, lks_handle** out);
 lks_status lks_set_walls(lks_handle* h, double c_bottom, double c_top, double u_bottom, double u_top);
 
 /* Enqueue n >= 0 fused collide-stream steps (steps a1-a6 of the hot path).
- * Asynchronous; long runs go through a captured CUDA graph. */
+ * Asynchronous; long runs go through a captured CUDA graph.  n must be even
+ * for an in-place handle (LKS_EINVAL). */
 lks_status lks_step(lks_handle* h, int64_t n);
 
 /* Steps taken since lks_create / lks_set_state. */
@@ -160,7 +168,8 @@ lks_status lks_residual(lks_handle* h, double* r_u, double* r_b);
 /* Repeat { lks_step(h, check_every); lks_residual } until max(r_u, r_b) < tol
  * or max_steps steps have been taken.  *steps_out (nullable) gets the steps
  * taken by this call and *r_out (nullable) the last residual.  Returns
- * LKS_ENOTCONVERGED at max_steps.  Synchronises. */
+ * LKS_ENOTCONVERGED at max_steps.  For an in-place handle check_every and
+ * max_steps must be even (LKS_EINVAL).  Synchronises. */
 lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int64_t max_steps,
                              int64_t* steps_out, double* r_out);
 

@@ -58,13 +58,18 @@ typedef struct lks_batch_config {
     int32_t groups_per_cta;     /* 1..15, threads_per_group * groups_per_cta <= 512; 0 = 1 */
     int32_t cluster_ctas;       /* 1, 2, 4 or 8 CTAs (one per SM) per instance; > 1 needs groups_per_cta = 1;
                                    0 = 1 */
+    int32_t coupling;           /* lks_coupling of every instance of this batch (0 = LKS_MAXWELL) */
+    int32_t inplace;            /* 1: every instance keeps one population buffer, updated in place
+                                   in pairs of steps (as lks_params.inplace; same results bit for
+                                   bit, half the population memory); quantum_steps, check_every
+                                   and max_steps must then be even.  0: two buffers */
     int32_t pad;
 } lks_batch_config;
 
 typedef struct lks_instance_desc {
     int32_t nx, ny;             /* as lks_params */
     int32_t closure;            /* lks_closure */
-    int32_t pad;
+    int32_t coupling;           /* lks_coupling; must equal the batch's; LKS_LORENTZ needs |tau_m - 1| >= 0.05 */
     double tau_f, tau_m, B0, Fx;
     double c_bottom, c_top;     /* wall conductance ratios, >= 0, INFINITY allowed */
     double u_bottom, u_top;     /* tangential wall speeds, |u| < 0.3 */
@@ -91,9 +96,10 @@ typedef struct lks_instance_result {
     double residual;            /* last residual (INFINITY before the first check) */
 } lks_instance_result;
 
-/* Pool bytes one instance needs with this storage type (two population buffers + residual
- * snapshot, 256-byte aligned); 0 if the description is invalid. */
-size_t lks_instance_footprint_bytes(const lks_instance_desc* d, int32_t storage);
+/* Pool bytes one instance needs with this storage type in a batch with this inplace setting
+ * (two population buffers, or one when inplace = 1, + residual snapshot, 256-byte aligned); 0 if
+ * the description is invalid for such a batch. */
+size_t lks_instance_footprint_bytes(const lks_instance_desc* d, int32_t storage, int32_t inplace);
 
 /* Create a batch; allocates the pool unless dev_buffer is given.  *out is NULL on error. */
 lks_status lks_batch_create(const lks_batch_config* cfg, lks_batch** out);
@@ -103,8 +109,8 @@ lks_status lks_batch_create(const lks_batch_config* cfg, lks_batch** out);
  * enough pool memory right now (nothing changed); LKS_EINVAL: invalid description. */
 lks_status lks_batch_add(lks_batch* b, const lks_instance_desc* d, int32_t* slot);
 
-/* One persistent launch: every RUNNING instance advances by up to quantum_steps (>= 1) steps or
- * until it leaves RUNNING.  Synchronises; afterwards lks_batch_result reflects the launch.
+/* One persistent launch: every RUNNING instance advances by up to quantum_steps (>= 1; even for
+ * an in-place batch) steps or until it leaves RUNNING.  Synchronises; afterwards lks_batch_result reflects the launch.
  * *n_running (nullable) gets the number of instances still RUNNING. */
 lks_status lks_batch_run(lks_batch* b, int64_t quantum_steps, int32_t* n_running);
 

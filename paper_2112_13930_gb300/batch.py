@@ -25,6 +25,8 @@ class BatchConfig(ctypes.Structure):
         ("threads_per_group", ctypes.c_int32),
         ("groups_per_cta", ctypes.c_int32),
         ("cluster_ctas", ctypes.c_int32),
+        ("coupling", ctypes.c_int32),
+        ("inplace", ctypes.c_int32),
         ("pad", ctypes.c_int32),
     ]
 
@@ -34,7 +36,7 @@ class InstanceDesc(ctypes.Structure):
         ("nx", ctypes.c_int32),
         ("ny", ctypes.c_int32),
         ("closure", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("coupling", ctypes.c_int32),
         ("tau_f", ctypes.c_double),
         ("tau_m", ctypes.c_double),
         ("B0", ctypes.c_double),
@@ -61,7 +63,8 @@ _I32P = ctypes.POINTER(ctypes.c_int32)
 _DP = ctypes.POINTER(ctypes.c_double)
 _SZP = ctypes.POINTER(ctypes.c_size_t)
 SIGNATURES = {
-    "lks_instance_footprint_bytes": (ctypes.c_size_t, [ctypes.POINTER(InstanceDesc), ctypes.c_int32]),
+    "lks_instance_footprint_bytes": (ctypes.c_size_t, [ctypes.POINTER(InstanceDesc), ctypes.c_int32,
+                                                       ctypes.c_int32]),
     "lks_batch_create": (ctypes.c_int, [ctypes.POINTER(BatchConfig), ctypes.POINTER(_VP)]),
     "lks_batch_add": (ctypes.c_int, [_VP, ctypes.POINTER(InstanceDesc), _I32P]),
     "lks_batch_run": (ctypes.c_int, [_VP, ctypes.c_int64, _I32P]),
@@ -90,21 +93,23 @@ def lib():
 
 
 def make_desc(nx, ny, closure, tau_f, tau_m, B0, Fx=0.0, c_bottom=0.0, c_top=0.0, u_bottom=0.0, u_top=0.0, seed=0,
-              perturb_amp=0.0, tol=1e-10, check_every=100, max_steps=10_000_000):
-    return InstanceDesc(nx=nx, ny=ny, closure=_lks.CLOSURES[closure], pad=0, tau_f=tau_f, tau_m=tau_m, B0=B0, Fx=Fx,
+              perturb_amp=0.0, tol=1e-10, check_every=100, max_steps=10_000_000, coupling="maxwell"):
+    return InstanceDesc(nx=nx, ny=ny, closure=_lks.CLOSURES[closure], coupling=_lks.COUPLINGS[coupling], tau_f=tau_f,
+                        tau_m=tau_m, B0=B0, Fx=Fx,
                         c_bottom=c_bottom, c_top=c_top, u_bottom=u_bottom, u_top=u_top, seed=seed,
                         perturb_amp=perturb_amp, tol=tol, check_every=check_every, max_steps=max_steps)
 
 
-def instance_footprint(desc, storage):
-    return int(lib().lks_instance_footprint_bytes(ctypes.byref(desc), _lks.STORAGES[storage]))
+def instance_footprint(desc, storage, inplace=False):
+    return int(lib().lks_instance_footprint_bytes(ctypes.byref(desc), _lks.STORAGES[storage], int(bool(inplace))))
 
 
 class Batch:
     """A pool of resident channel instances (wrapped lks_batch)."""
 
     def __init__(self, storage="f32", max_instances=4096, pool_bytes=1 << 30, threads_per_group=0,
-                 groups_per_cta=0, cluster_ctas=0, stream=None, torch_memory=True):
+                 groups_per_cta=0, cluster_ctas=0, stream=None, torch_memory=True, coupling="maxwell",
+                 inplace=False):
         import torch
         L = lib()
         if stream is None:
@@ -115,7 +120,9 @@ class Batch:
         cfg = BatchConfig(storage=self.storage, max_instances=max_instances, pool_bytes=pool_bytes,
                           cuda_stream=stream.cuda_stream or None, dev_buffer=None, dev_buffer_bytes=0,
                           threads_per_group=threads_per_group, groups_per_cta=groups_per_cta,
-                          cluster_ctas=cluster_ctas, pad=0)
+                          cluster_ctas=cluster_ctas, coupling=_lks.COUPLINGS[coupling],
+                          inplace=int(bool(inplace)), pad=0)
+        self.inplace = bool(inplace)
         if torch_memory:
             self._pool = torch.empty(pool_bytes, dtype=torch.uint8, device=stream.device)
             cfg.dev_buffer = self._pool.data_ptr()

@@ -44,8 +44,13 @@ Layout make_layout(const lks_params* p) {
     size_t o = 0;
     L.off_fa = o; o += L.f_bytes;
     L.off_ga = o; o += L.g_bytes;
-    L.off_fb = o; o += L.f_bytes;
-    L.off_gb = o; o += L.g_bytes;
+    if (p->inplace) {  // one population buffer (in-place pairs of steps)
+        L.off_fb = L.off_fa;
+        L.off_gb = L.off_ga;
+    } else {
+        L.off_fb = o; o += L.f_bytes;
+        L.off_gb = o; o += L.g_bytes;
+    }
     L.off_snap = o; o += align_up(2 * N * sizeof(double));
     L.off_partial = o; o += align_up(4 * (size_t)lks::residual_blocks((int64_t)N) * sizeof(double));
     L.off_out = o; o += align_up(8 * sizeof(double));
@@ -69,6 +74,7 @@ const char* validate(const lks_params* p) {
     if (p->coupling != LKS_MAXWELL && p->coupling != LKS_LORENTZ) return "coupling must be LKS_MAXWELL or LKS_LORENTZ";
     if (p->coupling == LKS_LORENTZ && fabs(p->tau_m - 1.0) < 0.05)
         return "the Lorentz-force coupling needs |tau_m - 1| >= 0.05 (J is read back from the stored g)";
+    if (p->inplace != 0 && p->inplace != 1) return "inplace must be 0 or 1";
     return nullptr;
 }
 
@@ -204,7 +210,10 @@ void drop_graphs(lks_handle* h) {
         }
 }
 
+// One step.  Two-buffer handles step from buffer `src` into the other; in-place handles take
+// phase `src` of a pair (0: pull and push to the neighbours, 1: own slots) on their one buffer.
 cudaError_t step_once(lks_handle* h, int src, cudaStream_t st) {
+    if (h->p.inplace) return lks::launch_step_aa(h->p.storage, h->p.closure, src, h->f[0], h->g[0], h->sp, st);
     return lks::launch_step(h->p.storage, h->p.closure, h->f[src], h->g[src], h->f[src ^ 1], h->g[src ^ 1], h->sp, st);
 }
 
@@ -314,6 +323,7 @@ lks_status lks_step(lks_handle* h, int64_t n) {
     NvtxRange nvtx_range("lks_step");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (n < 0) return fail(h, LKS_EINVAL, "n must be >= 0");
+    if (h->p.inplace && (n & 1)) return fail(h, LKS_EINVAL, "an in-place handle steps in pairs: n must be even");
     while (n >= kGraphSteps && !h->graphs_disabled) {
         if (!h->graph[h->cur]) {
             cudaError_t e = build_graph(h, h->cur);
@@ -402,6 +412,8 @@ lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int
     NvtxRange nvtx_range("lks_run_to_steady");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (check_every < 1 || max_steps < 0 || !(tol > 0.0)) return fail(h, LKS_EINVAL, "bad run_to_steady arguments");
+    if (h->p.inplace && ((check_every & 1) || (max_steps & 1)))
+        return fail(h, LKS_EINVAL, "an in-place handle steps in pairs: check_every and max_steps must be even");
     int64_t taken = 0;
     double r = INFINITY;
     lks_status s = LKS_OK;

@@ -21,6 +21,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lks_batch.h"
+#include "lks_aa.cuh"
 #include "lks_internal.h"
 
 using lks::StepParams;
@@ -45,7 +46,7 @@ struct InstDev {
     char* g[2];
     double* snap;
     int64_t steps, check_every, max_steps;
-    double tol, best_r, residual, stall_below;
+    double tol, best_r, residual, stall_below, tau_m;
     int32_t closure, cur, state, stall;
 };
 
@@ -87,24 +88,37 @@ __device__ __forceinline__ StepParams<C> to_compute(const StepParams<double>& d)
     return o;
 }
 
-// u_x and B_x (FP64) of node n of a stored post-collision state (coherent loads).
-template <typename S, typename C>
-__device__ __forceinline__ void ux_bx(const S* f, const S* g, int64_t N, int64_t n, double Fx, double& ux,
-                                      double& bx) {
-    typedef lks::Loader<S, C, false> L;
-    double v[9];
+// u_x and B_x (FP64) of node n of a stored post-collision state, loads through L.  Maxwell
+// coupling: rho u_x = sum f~ e_x - F_x/2.  Lorentz coupling: J_z is read back from the
+// (1 - 1/tau_m)-scaled non-equilibrium moment of the stored g, as for lks_moments.
+template <typename S, typename C, typename L, int COUPLING>
+__device__ __forceinline__ void stored_ux_bx(const S* f, const S* g, int64_t N, int64_t n, const InstDev* I,
+                                             double& ux, double& bx) {
+    double v[9], w[10];
 #pragma unroll
     for (int a = 0; a < 9; ++a) v[a] = (double)L::ld(f + a * N + n);
+#pragma unroll
+    for (int a = 0; a < 10; ++a) w[a] = (double)L::ld(g + a * N + n);
     const double drho = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
     const double jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
-    ux = (jx - 0.5 * Fx) / (1.0 + drho);
-    double b = 0.0;
-#pragma unroll
-    for (int a = 0; a < 5; ++a) b += (double)L::ld(g + a * N + n);
-    bx = b;
+    const double rho = 1.0 + drho;
+    const double Fx = (double)I->pd.Fx;
+    bx = ((w[0] + w[1]) + (w[2] + w[3])) + w[4];
+    if (COUPLING == 1) {
+        const double jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+        const double by = (double)I->pd.B0 + (((w[5] + w[6]) + (w[7] + w[8])) + w[9]);
+        const double kp = 3.0 / (I->tau_m - 1.0);
+        const double D = (w[2] - w[4]) - (w[6] - w[8]);
+        const double jxp = lks::ffma(-0.5, Fx, jx);
+        const double jz = lks::fmul(kp, D + lks::fmul(2.0, lks::ffma(by, jxp, -lks::fmul(bx, jy))) / rho) /
+                          (1.0 - lks::fmul(kp, lks::ffma(bx, bx, lks::fmul(by, by))) / rho);
+        ux = lks::ffma(lks::fmul(0.5, jz), by, jxp) / rho;
+    } else {
+        ux = lks::ffma(-0.5, Fx, jx) / rho;
+    }
 }
 
-template <typename S, typename C>
+template <typename S, typename C, int COUPLING, bool INPLACE>
 __global__ void __launch_bounds__(512) batch_kernel(InstDev* tab, const int32_t* work, const Ctl* ctl,
                                                      int32_t* counter, ResultDev* res, int T) {
     extern __shared__ double red[];
@@ -133,18 +147,40 @@ __global__ void __launch_bounds__(512) batch_kernel(InstDev* tab, const int32_t*
         double r = I->residual, best = I->best_r;
         int stall = I->stall;
         for (int64_t s = 0; s < quantum; ++s) {
-            const S* fi = (const S*)I->f[cur];
-            const S* gi = (const S*)I->g[cur];
-            S* fo = (S*)I->f[cur ^ 1];
-            S* go = (S*)I->g[cur ^ 1];
-            if (closure == 0) {
-                for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
-                    lks::step_node<S, C, 0, false>(fi, gi, fo, go, p, w.n, w.i, w.j);
+            if (INPLACE) {  // one buffer: phase (steps & 1) of an in-place pair (lks_aa.cuh)
+                S* fb = (S*)I->f[0];
+                S* gb = (S*)I->g[0];
+                if ((steps & 1) == 0) {
+                    if (closure == 0) {
+                        for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
+                            lks::aa_node_pull_push<S, C, 0, COUPLING>(fb, gb, p, w.n, w.i, w.j);
+                    } else {
+                        for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
+                            lks::aa_node_pull_push<S, C, 1, COUPLING>(fb, gb, p, w.n, w.i, w.j);
+                    }
+                } else {
+                    if (closure == 0) {
+                        for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
+                            lks::aa_node_local<S, C, 0, COUPLING>(fb, gb, p, w.n, w.j);
+                    } else {
+                        for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
+                            lks::aa_node_local<S, C, 1, COUPLING>(fb, gb, p, w.n, w.j);
+                    }
+                }
             } else {
-                for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
-                    lks::step_node<S, C, 1, false>(fi, gi, fo, go, p, w.n, w.i, w.j);
+                const S* fi = (const S*)I->f[cur];
+                const S* gi = (const S*)I->g[cur];
+                S* fo = (S*)I->f[cur ^ 1];
+                S* go = (S*)I->g[cur ^ 1];
+                if (closure == 0) {
+                    for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
+                        lks::step_node<S, C, 0, false, COUPLING>(fi, gi, fo, go, p, w.n, w.i, w.j);
+                } else {
+                    for (lks::NodeWalker w(lt, T, p.nx); w.n < N; w.next(T))
+                        lks::step_node<S, C, 1, false, COUPLING>(fi, gi, fo, go, p, w.n, w.i, w.j);
+                }
+                cur ^= 1;
             }
-            cur ^= 1;
             ++steps;
             group_sync(gid, T);
             if (steps % check_every == 0 || steps >= max_steps) {
@@ -154,12 +190,12 @@ __global__ void __launch_bounds__(512) batch_kernel(InstDev* tab, const int32_t*
                 double* snap = I->snap;
                 for (int64_t n = lt; n < N; n += T) {
                     double ux, bx;
-                    ux_bx<S, C>(fc, gc, N, n, (double)I->pd.Fx, ux, bx);
+                    stored_ux_bx<S, C, lks::Loader<S, C, false>, COUPLING>(fc, gc, N, n, I, ux, bx);
                     const double du = ux - snap[n], db = bx - snap[N + n];
-                    acc[0] += du * du;
-                    acc[1] += ux * ux;
-                    acc[2] += db * db;
-                    acc[3] += bx * bx;
+                    acc[0] = lks::ffma(du, du, acc[0]);
+                    acc[1] = lks::ffma(ux, ux, acc[1]);
+                    acc[2] = lks::ffma(db, db, acc[2]);
+                    acc[3] = lks::ffma(bx, bx, acc[3]);
                     snap[n] = ux;
                     snap[N + n] = bx;
                 }
@@ -238,7 +274,7 @@ template <> struct CgLoader<__half, float> {
 // scope) separates the steps, and the residual partials of the CTAs are summed by CTA 0 in rank
 // order through distributed shared memory.  Large instances then advance CS times faster per step
 // than with one CTA.
-template <typename S, typename C>
+template <typename S, typename C, int COUPLING, bool INPLACE>
 __global__ void __launch_bounds__(512) batch_cluster_kernel(InstDev* tab, const int32_t* work, const Ctl* ctl,
                                                              int32_t* counter, ResultDev* res, int T) {
     namespace cg = cooperative_groups;
@@ -277,18 +313,40 @@ __global__ void __launch_bounds__(512) batch_cluster_kernel(InstDev* tab, const 
         int stall = I->stall;
         const int64_t first = (int64_t)rank * T + lt;
         for (int64_t s = 0; s < quantum; ++s) {
-            const S* fi = (const S*)I->f[cur];
-            const S* gi = (const S*)I->g[cur];
-            S* fo = (S*)I->f[cur ^ 1];
-            S* go = (S*)I->g[cur ^ 1];
-            if (closure == 0) {
-                for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
-                    lks::step_node_with<S, C, 0, CgLoader<S, C>>(fi, gi, fo, go, p, w.n, w.i, w.j);
+            if (INPLACE) {
+                S* fb = (S*)I->f[0];
+                S* gb = (S*)I->g[0];
+                if ((steps & 1) == 0) {
+                    if (closure == 0) {
+                        for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
+                            lks::aa_node_pull_push<S, C, 0, COUPLING, CgLoader<S, C>>(fb, gb, p, w.n, w.i, w.j);
+                    } else {
+                        for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
+                            lks::aa_node_pull_push<S, C, 1, COUPLING, CgLoader<S, C>>(fb, gb, p, w.n, w.i, w.j);
+                    }
+                } else {
+                    if (closure == 0) {
+                        for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
+                            lks::aa_node_local<S, C, 0, COUPLING, CgLoader<S, C>>(fb, gb, p, w.n, w.j);
+                    } else {
+                        for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
+                            lks::aa_node_local<S, C, 1, COUPLING, CgLoader<S, C>>(fb, gb, p, w.n, w.j);
+                    }
+                }
             } else {
-                for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
-                    lks::step_node_with<S, C, 1, CgLoader<S, C>>(fi, gi, fo, go, p, w.n, w.i, w.j);
+                const S* fi = (const S*)I->f[cur];
+                const S* gi = (const S*)I->g[cur];
+                S* fo = (S*)I->f[cur ^ 1];
+                S* go = (S*)I->g[cur ^ 1];
+                if (closure == 0) {
+                    for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
+                        lks::step_node_with<S, C, 0, CgLoader<S, C>, COUPLING>(fi, gi, fo, go, p, w.n, w.i, w.j);
+                } else {
+                    for (lks::NodeWalker w(first, stride, p.nx); w.n < N; w.next(stride))
+                        lks::step_node_with<S, C, 1, CgLoader<S, C>, COUPLING>(fi, gi, fo, go, p, w.n, w.i, w.j);
+                }
+                cur ^= 1;
             }
-            cur ^= 1;
             ++steps;
             cl.sync();
             if (steps % check_every == 0 || steps >= max_steps) {
@@ -297,20 +355,13 @@ __global__ void __launch_bounds__(512) batch_cluster_kernel(InstDev* tab, const 
                 const S* gc = (const S*)I->g[cur];
                 double* snap = I->snap;
                 for (int64_t n = first; n < N; n += stride) {
-                    double v[9];
-#pragma unroll
-                    for (int a = 0; a < 9; ++a) v[a] = (double)CgLoader<S, C>::ld(fc + a * N + n);
-                    const double drho = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-                    const double jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
-                    const double ux = (jx - 0.5 * (double)I->pd.Fx) / (1.0 + drho);
-                    double bx = 0.0;
-#pragma unroll
-                    for (int a = 0; a < 5; ++a) bx += (double)CgLoader<S, C>::ld(gc + a * N + n);
+                    double ux, bx;
+                    stored_ux_bx<S, C, CgLoader<S, C>, COUPLING>(fc, gc, N, n, I, ux, bx);
                     const double du = ux - snap[n], db = bx - snap[N + n];
-                    acc[0] += du * du;
-                    acc[1] += ux * ux;
-                    acc[2] += db * db;
-                    acc[3] += bx * bx;
+                    acc[0] = lks::ffma(du, du, acc[0]);
+                    acc[1] = lks::ffma(ux, ux, acc[1]);
+                    acc[2] = lks::ffma(db, db, acc[2]);
+                    acc[3] = lks::ffma(bx, bx, acc[3]);
                     snap[n] = ux;
                     snap[N + n] = bx;
                 }
@@ -374,24 +425,36 @@ __global__ void __launch_bounds__(512) batch_cluster_kernel(InstDev* tab, const 
 
 typedef void (*BatchClusterFn)(InstDev*, const int32_t*, const Ctl*, int32_t*, ResultDev*, int);
 
-BatchClusterFn cluster_kernel_for(int storage) {
+template <int COUPLING, bool INPLACE>
+BatchClusterFn cluster_kernel_typed(int storage) {
     switch (storage) {
-        case 0: return batch_cluster_kernel<double, double>;
-        case 1: return batch_cluster_kernel<float, float>;
-        case 2: return batch_cluster_kernel<__nv_bfloat16, float>;
-        default: return batch_cluster_kernel<__half, float>;
+        case 0: return batch_cluster_kernel<double, double, COUPLING, INPLACE>;
+        case 1: return batch_cluster_kernel<float, float, COUPLING, INPLACE>;
+        case 2: return batch_cluster_kernel<__nv_bfloat16, float, COUPLING, INPLACE>;
+        default: return batch_cluster_kernel<__half, float, COUPLING, INPLACE>;
     }
+}
+
+BatchClusterFn cluster_kernel_for(const lks_batch_config& c) {
+    if (c.coupling == 1) return c.inplace ? cluster_kernel_typed<1, true>(c.storage) : cluster_kernel_typed<1, false>(c.storage);
+    return c.inplace ? cluster_kernel_typed<0, true>(c.storage) : cluster_kernel_typed<0, false>(c.storage);
 }
 
 typedef void (*BatchKernelFn)(InstDev*, const int32_t*, const Ctl*, int32_t*, ResultDev*, int);
 
-BatchKernelFn kernel_for(int storage) {
+template <int COUPLING, bool INPLACE>
+BatchKernelFn kernel_typed(int storage) {
     switch (storage) {
-        case 0: return batch_kernel<double, double>;
-        case 1: return batch_kernel<float, float>;
-        case 2: return batch_kernel<__nv_bfloat16, float>;
-        default: return batch_kernel<__half, float>;
+        case 0: return batch_kernel<double, double, COUPLING, INPLACE>;
+        case 1: return batch_kernel<float, float, COUPLING, INPLACE>;
+        case 2: return batch_kernel<__nv_bfloat16, float, COUPLING, INPLACE>;
+        default: return batch_kernel<__half, float, COUPLING, INPLACE>;
     }
+}
+
+BatchKernelFn kernel_for(const lks_batch_config& c) {
+    if (c.coupling == 1) return c.inplace ? kernel_typed<1, true>(c.storage) : kernel_typed<1, false>(c.storage);
+    return c.inplace ? kernel_typed<0, true>(c.storage) : kernel_typed<0, false>(c.storage);
 }
 
 const char* validate_desc(const lks_instance_desc* d) {
@@ -408,13 +471,17 @@ const char* validate_desc(const lks_instance_desc* d) {
     if (!(fabs(d->u_bottom) < 0.3) || !(fabs(d->u_top) < 0.3)) return "|wall speed| must be < 0.3";
     if (!isfinite(d->perturb_amp) || fabs(d->perturb_amp) >= 0.3) return "|perturb_amp| must be < 0.3";
     if (!(d->tol > 0.0) || d->check_every < 1 || d->max_steps < 1) return "tol > 0, check_every >= 1, max_steps >= 1";
+    if (d->coupling != LKS_MAXWELL && d->coupling != LKS_LORENTZ) return "coupling must be LKS_MAXWELL or LKS_LORENTZ";
+    if (d->coupling == LKS_LORENTZ && fabs(d->tau_m - 1.0) < 0.05)
+        return "the Lorentz-force coupling needs |tau_m - 1| >= 0.05";
     return nullptr;
 }
 
-size_t inst_bytes(int nx, int ny, int storage) {
+size_t inst_bytes(int nx, int ny, int storage, int inplace) {
     const size_t N = (size_t)nx * ny;
     const size_t sb = lks::storage_bytes(storage);
-    return 2 * align_up(9 * N * sb) + 2 * align_up(10 * N * sb) + align_up(2 * N * sizeof(double));
+    const size_t nbuf = inplace ? 1 : 2;
+    return nbuf * (align_up(9 * N * sb) + align_up(10 * N * sb)) + align_up(2 * N * sizeof(double));
 }
 
 bool valid_shape(int T, int G, int CS) {
@@ -510,7 +577,7 @@ void pool_free(lks_batch* b, size_t off, size_t bytes) {
 int blocks_per_sm(lks_batch* b, int T, int G) {
     int nb = 0;
     const size_t smem = (size_t)G * 4 * T * sizeof(double);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(b->cfg.storage), T * G, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(b->cfg), T * G, smem);
     return nb > 0 ? nb : 1;
 }
 
@@ -521,7 +588,7 @@ cudaError_t enqueue_launch(lks_batch* b, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (CS == 1) {
         const int grid = blocks_per_sm(b, T, G) * b->nsm;
-        kernel_for(b->cfg.storage)<<<grid, T * G, smem, st>>>(b->d_tab, b->d_work, b->d_ctl, b->d_counter, b->d_res,
+        kernel_for(b->cfg)<<<grid, T * G, smem, st>>>(b->d_tab, b->d_work, b->d_ctl, b->d_counter, b->d_res,
                                                               T);
     } else {
         cudaLaunchConfig_t lc = {};
@@ -537,11 +604,11 @@ cudaError_t enqueue_launch(lks_batch* b, cudaStream_t st) {
         lc.numAttrs = 1;
         lc.gridDim = dim3(CS * b->nsm);
         int clusters = 0;
-        e = cudaOccupancyMaxActiveClusters(&clusters, cluster_kernel_for(b->cfg.storage), &lc);
+        e = cudaOccupancyMaxActiveClusters(&clusters, cluster_kernel_for(b->cfg), &lc);
         if (e != cudaSuccess) return e;
         if (clusters < 1) clusters = 1;
         lc.gridDim = dim3(clusters * CS);
-        e = cudaLaunchKernelEx(&lc, cluster_kernel_for(b->cfg.storage), b->d_tab, (const int32_t*)b->d_work,
+        e = cudaLaunchKernelEx(&lc, cluster_kernel_for(b->cfg), b->d_tab, (const int32_t*)b->d_work,
                                (const Ctl*)b->d_ctl, b->d_counter, b->d_res, T);
         if (e != cudaSuccess) return e;
     }
@@ -558,7 +625,7 @@ cudaError_t ensure_graph(lks_batch* b) {
     }
     const size_t smem = (size_t)b->G * 4 * b->T * sizeof(double);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kernel_for(b->cfg.storage), cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(kernel_for(b->cfg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
@@ -586,9 +653,10 @@ cudaError_t ensure_graph(lks_batch* b) {
 
 extern "C" {
 
-size_t lks_instance_footprint_bytes(const lks_instance_desc* d, int32_t storage) {
-    if (validate_desc(d) || storage < LKS_F64 || storage > LKS_F16_DEV) return 0;
-    return inst_bytes(d->nx, d->ny, storage);
+size_t lks_instance_footprint_bytes(const lks_instance_desc* d, int32_t storage, int32_t inplace) {
+    if (validate_desc(d) || storage < LKS_F64 || storage > LKS_F16_DEV || (inplace != 0 && inplace != 1)) return 0;
+    if (inplace && ((d->check_every & 1) || (d->max_steps & 1))) return 0;
+    return inst_bytes(d->nx, d->ny, storage, inplace);
 }
 
 lks_status lks_batch_create(const lks_batch_config* cfg, lks_batch** out) {
@@ -596,6 +664,8 @@ lks_status lks_batch_create(const lks_batch_config* cfg, lks_batch** out) {
     *out = nullptr;
     if (!cfg) return bfail(nullptr, LKS_EINVAL, "config is NULL");
     if (cfg->storage < LKS_F64 || cfg->storage > LKS_F16_DEV) return bfail(nullptr, LKS_EINVAL, "bad storage");
+    if (cfg->coupling != LKS_MAXWELL && cfg->coupling != LKS_LORENTZ) return bfail(nullptr, LKS_EINVAL, "bad coupling");
+    if (cfg->inplace != 0 && cfg->inplace != 1) return bfail(nullptr, LKS_EINVAL, "inplace must be 0 or 1");
     if (cfg->max_instances < 1 || cfg->max_instances > (1 << 24)) return bfail(nullptr, LKS_EINVAL, "bad max_instances");
     if (cfg->pool_bytes < kAlign) return bfail(nullptr, LKS_EINVAL, "pool_bytes too small");
     const int T = cfg->threads_per_group ? cfg->threads_per_group : 256;
@@ -669,6 +739,9 @@ lks_status lks_batch_create(const lks_batch_config* cfg, lks_batch** out) {
 lks_status lks_batch_add(lks_batch* b, const lks_instance_desc* d, int32_t* slot_out) {
     if (!b) return bfail(nullptr, LKS_EINVAL, "batch is NULL");
     if (const char* m = validate_desc(d)) return bfail(b, LKS_EINVAL, m);
+    if (d->coupling != b->cfg.coupling) return bfail(b, LKS_EINVAL, "instance coupling differs from the batch's");
+    if (b->cfg.inplace && ((d->check_every & 1) || (d->max_steps & 1)))
+        return bfail(b, LKS_EINVAL, "an in-place batch steps in pairs: check_every and max_steps must be even");
     int slot = -1;
     for (size_t k = 0; k < b->slots.size(); ++k)
         if (!b->slots[k].used) {
@@ -676,7 +749,7 @@ lks_status lks_batch_add(lks_batch* b, const lks_instance_desc* d, int32_t* slot
             break;
         }
     if (slot < 0) return bfail(b, LKS_EBUSY, "no free slot");
-    const size_t bytes = inst_bytes(d->nx, d->ny, b->cfg.storage);
+    const size_t bytes = inst_bytes(d->nx, d->ny, b->cfg.storage, b->cfg.inplace);
     size_t off = 0;
     if (!pool_alloc(b, bytes, &off)) return bfail(b, LKS_EBUSY, "not enough free pool memory");
     Slot& s = b->slots[slot];
@@ -690,18 +763,25 @@ lks_status lks_batch_add(lks_batch* b, const lks_instance_desc* d, int32_t* slot
     InstDev I;
     memset(&I, 0, sizeof(I));
     I.pd = lks::make_step_params(d->nx, d->ny, d->closure, d->tau_f, d->tau_m, d->B0, d->Fx, d->c_bottom, d->c_top,
-                                 d->u_bottom, d->u_top);
+                                 d->u_bottom, d->u_top, d->coupling);
     char* base = b->pool + off;
     I.f[0] = base;
     I.g[0] = base + align_up(9 * N * sb);
-    I.f[1] = I.g[0] + align_up(10 * N * sb);
-    I.g[1] = I.f[1] + align_up(9 * N * sb);
-    I.snap = (double*)(I.g[1] + align_up(10 * N * sb));
+    if (b->cfg.inplace) {  // one population buffer
+        I.f[1] = I.f[0];
+        I.g[1] = I.g[0];
+        I.snap = (double*)(I.g[0] + align_up(10 * N * sb));
+    } else {
+        I.f[1] = I.g[0] + align_up(10 * N * sb);
+        I.g[1] = I.f[1] + align_up(9 * N * sb);
+        I.snap = (double*)(I.g[1] + align_up(10 * N * sb));
+    }
     I.steps = 0;
     I.check_every = d->check_every;
     I.max_steps = d->max_steps;
     I.tol = d->tol;
     I.stall_below = stall_floor(b->cfg.storage);
+    I.tau_m = d->tau_m;
     I.best_r = INFINITY;
     I.residual = INFINITY;
     I.closure = d->closure;
@@ -718,7 +798,8 @@ lks_status lks_batch_add(lks_batch* b, const lks_instance_desc* d, int32_t* slot
     if (e == cudaSuccess)
         e = lks::launch_init(b->cfg.storage, I.f[0], I.g[0], d->nx, d->ny, d->B0, d->seed, d->perturb_amp, b->stream);
     if (e == cudaSuccess)
-        e = lks::launch_snapshot(b->cfg.storage, I.f[0], I.g[0], d->nx, d->ny, d->B0, d->Fx, I.snap, b->stream);
+        e = lks::launch_snapshot(b->cfg.storage, I.f[0], I.g[0], d->nx, d->ny, d->B0, d->Fx, I.snap, b->stream,
+                                 d->coupling, d->tau_m);
     // the host copy of I is on the stack: make sure the copies have consumed it
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
@@ -738,6 +819,7 @@ lks_status lks_batch_run(lks_batch* b, int64_t quantum, int32_t* n_running) {
         ~Pop() { nvtxRangePop(); }
     } pop;
     if (quantum < 1) return bfail(b, LKS_EINVAL, "quantum_steps must be >= 1");
+    if (b->cfg.inplace && (quantum & 1)) return bfail(b, LKS_EINVAL, "an in-place batch steps in pairs: quantum must be even");
     int nwork = 0;
     for (size_t k = 0; k < b->slots.size(); ++k)
         if (b->slots[k].used && b->h_res[k].state == LKS_INST_RUNNING) b->h_work[nwork++] = (int32_t)k;
@@ -795,7 +877,7 @@ lks_status lks_batch_moments(lks_batch* b, int32_t slot, int what, double* host_
         return bfail(b, LKS_ENOMEM, "cudaMalloc of the moment staging buffer failed");
     }
     e = lks::launch_moments(b->cfg.storage, I.f[I.cur], I.g[I.cur], s.nx, s.ny, I.pd.B0, I.pd.Fx, what, dtmp,
-                            b->stream);
+                            b->stream, I.pd.coupling, I.tau_m);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, dtmp, count * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     cudaFree(dtmp);

@@ -70,17 +70,47 @@ template <> __device__ __forceinline__ void store_s<__nv_bfloat16, float>(__nv_b
 }
 template <> __device__ __forceinline__ void store_s<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
 
+// Pinned floating-point operations.  Every product in the collision and the closures is written
+// as an explicit fused multiply-add (ffma) or a separately rounded multiply (fmul); no plain '*'
+// on floating-point values remains, so the compiler has nothing to contract and every kernel that
+// inlines this code (one- and two-node, in-place, batched, cluster) performs exactly the same
+// operations in the same order -- their results agree bit for bit.
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double ffma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // 1/rho.  FP64: Newton-Raphson iteration for the reciprocal, r <- r + r (1 - rho r), started from
 // the correctly rounded FP32 reciprocal (relative error <= 2^-24); two iterations square the error
 // twice (<= 2^-96 before rounding), far below FP64's resolution.  FP32: the correctly rounded
 // reciprocal.
 __device__ __forceinline__ double recip(double rho) {
     double r = (double)__frcp_rn((float)rho);
-    r = fma(r, fma(-rho, r, 1.0), r);
-    r = fma(r, fma(-rho, r, 1.0), r);
+    r = ffma(r, ffma(-rho, r, 1.0), r);
+    r = ffma(r, ffma(-rho, r, 1.0), r);
     return r;
 }
 __device__ __forceinline__ float recip(float rho) { return __frcp_rn(rho); }
+
+// a4-a5 for g (Eqs. geqmagneticfield, LKSformagneticfield): g' = (1 - w_m) g + w_m g^eq,dev with
+//   g^eq_x = W (Bx - 3 e_y E),  g^eq,dev_y = W (dBy + 3 e_x E),  E = u_x B_y - u_y B_x.
+template <typename C>
+__device__ __forceinline__ void collide_g(C gx[5], C gy[5], C ux, C uy, C bx, C by, C dby, const StepParams<C>& p) {
+    const C om1m = p.om1m;
+    const C ce = fmul(p.owm1, fmul(C(3), ffma(ux, by, -fmul(uy, bx))));
+    const C cb0 = fmul(p.owm0, bx), cb1 = fmul(p.owm1, bx);
+    const C cd0 = fmul(p.owm0, dby), cd1 = fmul(p.owm1, dby);
+    gx[0] = ffma(om1m, gx[0], cb0);
+    gx[1] = ffma(om1m, gx[1], cb1);
+    gx[2] = ffma(om1m, gx[2], cb1 - ce);
+    gx[3] = ffma(om1m, gx[3], cb1);
+    gx[4] = ffma(om1m, gx[4], cb1 + ce);
+    gy[0] = ffma(om1m, gy[0], cd0);
+    gy[1] = ffma(om1m, gy[1], cd1 + ce);
+    gy[2] = ffma(om1m, gy[2], cd1);
+    gy[3] = ffma(om1m, gy[3], cd1 - ce);
+    gy[4] = ffma(om1m, gy[4], cd1);
+}
 
 // Equilibrium deviations and the collision, for one node whose post-stream, post-closure
 // populations are in f[9], gx[5], gy[5] (deviation form).  Overwrites them with the
@@ -102,8 +132,8 @@ __device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const Ste
     const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
     const C inv_rho = recip(rho);
-    const C ux = (jx + half * p.Fx) * inv_rho;
-    const C uy = jy * inv_rho;
+    const C ux = fmul(ffma(half, p.Fx, jx), inv_rho);
+    const C uy = fmul(jy, inv_rho);
     const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
     const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
     const C by = p.B0 + dby;
@@ -114,21 +144,21 @@ __device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const Ste
     //   S_a = 3 (e_ax - u_x) F_x w_a (1 + bm1_a)
     // Maxwell-stress part M_a with q = B_y^2 - B0^2 = dby (2 B0 + dby):
     //   a=1,3: 2.25 w1 (q - Bx^2)   a=2,4: -2.25 w1 (q - Bx^2)   a=5,7: -9 w5 Bx By   a=6,8: +9 w5 Bx By
-    const C q = dby * (p.B0 + by);
-    const C om13 = p.owf1 * (C(2.25) * (q - bx * bx));   // omega * M_1 = omega * M_3 = -omega * M_2
-    const C omxy = p.owf5 * (C(9) * bx * by);            // omega * M_6 = omega * M_8 = -omega * M_5
-    const C usq = one5 * (ux * ux + uy * uy);
-    const C s0 = p.sw0 * (-ux);                            // source prefactors per e_x and weight
-    const C s1p = p.sw1 * (C(1) - ux), s1z = p.sw1 * (-ux), s1m = p.sw1 * (C(-1) - ux);
-    const C s5p = p.sw5 * (C(1) - ux), s5m = p.sw5 * (C(-1) - ux);
+    const C q = fmul(dby, p.B0 + by);
+    const C om13 = fmul(p.owf1, fmul(C(2.25), ffma(-bx, bx, q)));   // omega * M_1 = omega * M_3 = -omega * M_2
+    const C omxy = fmul(p.owf5, fmul(fmul(C(9), bx), by));         // omega * M_6 = omega * M_8 = -omega * M_5
+    const C usq = fmul(one5, ffma(ux, ux, fmul(uy, uy)));
+    const C s0 = fmul(p.sw0, -ux);                                  // source prefactors per e_x and weight
+    const C s1p = fmul(p.sw1, C(1) - ux), s1z = fmul(p.sw1, -ux), s1m = fmul(p.sw1, C(-1) - ux);
+    const C s5p = fmul(p.sw5, C(1) - ux), s5m = fmul(p.sw5, C(-1) - ux);
     const C om1 = p.om1f;
 #define LKS_DIR(A, EU, OW, OMAG, SA)                                                    \
     {                                                                                   \
         const C eu = (EU);                                                              \
-        const C bm1 = (three + four5 * eu) * eu - usq;                                  \
-        const C ofeq = (OW) * (drho + rho * bm1) + (OMAG);                              \
-        const C src = (SA) + (SA) * bm1;                                                \
-        f[A] = om1 * f[A] + (ofeq + src);                                               \
+        const C bm1 = ffma(ffma(four5, eu, three), eu, -usq);                           \
+        const C ofeq = ffma((OW), ffma(rho, bm1, drho), (OMAG));                        \
+        const C src = ffma((SA), bm1, (SA));                                            \
+        f[A] = ffma(om1, f[A], ofeq + src);                                             \
     }
     LKS_DIR(0, C(0), p.owf0, C(0), s0)
     LKS_DIR(1, ux, p.owf1, om13, s1p)
@@ -140,23 +170,7 @@ __device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const Ste
     LKS_DIR(7, -ux - uy, p.owf5, -omxy, s5m)
     LKS_DIR(8, ux - uy, p.owf5, omxy, s5p)
 #undef LKS_DIR
-
-    // a4-a5 for g (Eqs. geqmagneticfield, LKSformagneticfield): g' = (1 - w_m) g + w_m g^eq,dev with
-    //   g^eq_x = W (Bx - 3 e_y E),  g^eq,dev_y = W (dBy + 3 e_x E),  E = u_x B_y - u_y B_x.
-    const C om1m = p.om1m;
-    const C ce = p.owm1 * (three * (ux * by - uy * bx));
-    const C cb0 = p.owm0 * bx, cb1 = p.owm1 * bx;
-    const C cd0 = p.owm0 * dby, cd1 = p.owm1 * dby;
-    gx[0] = om1m * gx[0] + cb0;
-    gx[1] = om1m * gx[1] + cb1;
-    gx[2] = om1m * gx[2] + (cb1 - ce);
-    gx[3] = om1m * gx[3] + cb1;
-    gx[4] = om1m * gx[4] + (cb1 + ce);
-    gy[0] = om1m * gy[0] + cd0;
-    gy[1] = om1m * gy[1] + (cd1 + ce);
-    gy[2] = om1m * gy[2] + cd1;
-    gy[3] = om1m * gy[3] + (cd1 - ce);
-    gy[4] = om1m * gy[4] + cd1;
+    collide_g(gx, gy, ux, uy, bx, by, dby, p);
 }
 
 // Moment-based closures at a wet wall node (Sec. VII, App. A, App. B.2), deviation form.
@@ -171,9 +185,9 @@ template <typename C, int COUPLING>
 __device__ __forceinline__ void wall_force_halves(const C gx[5], const C gy[5], C bx, C by, C U,
                                                   const StepParams<C>& p, C& hfx, C& hfy) {
     if (COUPLING == 1) {
-        const C jz = C(3) * p.omega_m * (((gx[2] - gx[4]) - (gy[1] - gy[3])) + C(2) * U * by);
-        hfx = C(0.5) * (p.Fx - jz * by);
-        hfy = C(0.5) * (jz * bx);
+        const C jz = fmul(fmul(C(3), p.omega_m), ffma(fmul(C(2), U), by, (gx[2] - gx[4]) - (gy[1] - gy[3])));
+        hfx = fmul(C(0.5), ffma(-jz, by, p.Fx));
+        hfy = fmul(C(0.5), fmul(jz, bx));
     } else {
         hfx = C(0);
         hfy = C(0);
@@ -185,22 +199,23 @@ __device__ __forceinline__ void moment_closure_bottom(C f[9], C gx[5], C gy[5], 
                                                       const StepParams<C>& p) {
     const C half = C(0.5), cs2 = C(1.0 / 3.0);
     const C B0 = p.B0;
-    gx[2] = w.r * gx[4] - w.bc * ((gx[0] + gx[1]) + gx[3]) + w.kx;
+    gx[2] = ffma(w.r, gx[4], -fmul(w.bc, (gx[0] + gx[1]) + gx[3])) + w.kx;
     gy[2] = -(((gy[0] + gy[1]) + gy[3]) + gy[4]);
     const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
     const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
     const C U = w.U;
     C hfx, hfy;
     wall_force_halves<C, COUPLING>(gx, gy, bx, B0 + dby, U, p, hfx, hfy);
-    const C drho = (f[0] + f[1]) + f[3] + C(2) * ((f[4] + f[7]) + f[8]) - hfy;
+    const C drho = ffma(C(2), (f[4] + f[7]) + f[8], (f[0] + f[1]) + f[3]) - hfy;
     const C rho = C(1) + drho;
     // P - P_rest
-    C dP = U * U + drho * (cs2 + U * U);
-    if (COUPLING == 0) dP += dby * (B0 + half * dby) - half * bx * bx;
-    const C rU = rho * U - hfx;
-    f[2] = -dP + (f[1] + f[3]) + f[4] + C(2) * (f[7] + f[8]) - hfy;
-    f[5] = half * (dP + rU) - (f[1] + f[8]);
-    f[6] = half * (dP - rU) - (f[3] + f[7]);
+    const C uu = fmul(U, U);
+    C dP = ffma(drho, cs2 + uu, uu);
+    if (COUPLING == 0) dP = dP + ffma(-fmul(half, bx), bx, fmul(dby, ffma(half, dby, B0)));
+    const C rU = ffma(rho, U, -hfx);
+    f[2] = ((-dP + (f[1] + f[3])) + f[4]) + fmul(C(2), f[7] + f[8]) - hfy;
+    f[5] = ffma(half, dP + rU, -(f[1] + f[8]));
+    f[6] = ffma(half, dP - rU, -(f[3] + f[7]));
 }
 
 // Top: unknown f4, f7, f8, g4.
@@ -209,21 +224,22 @@ __device__ __forceinline__ void moment_closure_top(C f[9], C gx[5], C gy[5], con
                                                    const StepParams<C>& p) {
     const C half = C(0.5), cs2 = C(1.0 / 3.0);
     const C B0 = p.B0;
-    gx[4] = w.r * gx[2] - w.bc * ((gx[0] + gx[1]) + gx[3]) + w.kx;
+    gx[4] = ffma(w.r, gx[2], -fmul(w.bc, (gx[0] + gx[1]) + gx[3])) + w.kx;
     gy[4] = -(((gy[0] + gy[1]) + gy[2]) + gy[3]);
     const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
     const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
     const C U = w.U;
     C hfx, hfy;
     wall_force_halves<C, COUPLING>(gx, gy, bx, B0 + dby, U, p, hfx, hfy);
-    const C drho = (f[0] + f[1]) + f[3] + C(2) * ((f[2] + f[5]) + f[6]) + hfy;
+    const C drho = ffma(C(2), (f[2] + f[5]) + f[6], (f[0] + f[1]) + f[3]) + hfy;
     const C rho = C(1) + drho;
-    C dP = U * U + drho * (cs2 + U * U);
-    if (COUPLING == 0) dP += dby * (B0 + half * dby) - half * bx * bx;
-    const C rU = rho * U - hfx;
-    f[4] = -dP + (f[1] + f[2]) + f[3] + C(2) * (f[5] + f[6]) + hfy;
-    f[7] = half * (dP - rU) - (f[3] + f[6]);
-    f[8] = half * (dP + rU) - (f[1] + f[5]);
+    const C uu = fmul(U, U);
+    C dP = ffma(drho, cs2 + uu, uu);
+    if (COUPLING == 0) dP = dP + ffma(-fmul(half, bx), bx, fmul(dby, ffma(half, dby, B0)));
+    const C rU = ffma(rho, U, -hfx);
+    f[4] = ((-dP + (f[1] + f[2])) + f[3]) + fmul(C(2), f[5] + f[6]) + hfy;
+    f[7] = ffma(half, dP - rU, -(f[3] + f[6]));
+    f[8] = ffma(half, dP + rU, -(f[1] + f[5]));
 }
 
 // Collision with the paper's own coupling (Sec. IV-V): f^eq without magnetic terms; the Lorentz
@@ -242,27 +258,29 @@ __device__ __forceinline__ void collide_node_lorentz(C f[9], C gx[5], C gy[5], c
     const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
     const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
     const C by = p.B0 + dby;
-    const C k = three * p.omega_m;
+    const C k = fmul(three, p.omega_m);
     const C D = (gx[2] - gx[4]) - (gy[1] - gy[3]);
-    const C jxp = jx + half * p.Fx;
-    const C jz = k * (D + C(2) * inv_rho * (by * jxp - bx * jy)) / (C(1) + k * inv_rho * (bx * bx + by * by));
-    const C Fx = p.Fx - jz * by, Fy = jz * bx;
-    const C ux = (jx + half * Fx) * inv_rho;
-    const C uy = (jy + half * Fy) * inv_rho;
-    const C usq = one5 * (ux * ux + uy * uy);
-    const C ax = p.src3 * Fx, ay = p.src3 * Fy;
+    const C jxp = ffma(half, p.Fx, jx);
+    const C num = fmul(k, ffma(fmul(C(2), inv_rho), ffma(by, jxp, -fmul(bx, jy)), D));
+    const C den = ffma(fmul(k, inv_rho), ffma(bx, bx, fmul(by, by)), C(1));
+    const C jz = num / den;
+    const C Fx = ffma(-jz, by, p.Fx), Fy = fmul(jz, bx);
+    const C ux = fmul(ffma(half, Fx, jx), inv_rho);
+    const C uy = fmul(ffma(half, Fy, jy), inv_rho);
+    const C usq = fmul(one5, ffma(ux, ux, fmul(uy, uy)));
+    const C ax = fmul(p.src3, Fx), ay = fmul(p.src3, Fy);
     // (e_x - u_x) a_x and (e_y - u_y) a_y for e = -1, 0, +1
-    const C px0 = -ux * ax, pxp = (C(1) - ux) * ax, pxm = (C(-1) - ux) * ax;
-    const C py0 = -uy * ay, pyp = (C(1) - uy) * ay, pym = (C(-1) - uy) * ay;
+    const C px0 = fmul(-ux, ax), pxp = fmul(C(1) - ux, ax), pxm = fmul(C(-1) - ux, ax);
+    const C py0 = fmul(-uy, ay), pyp = fmul(C(1) - uy, ay), pym = fmul(C(-1) - uy, ay);
     const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w5 = C(1.0 / 36.0);
     const C om1 = p.om1f;
 #define LKS_DIRL(A, EU, OW, W, PX, PY)                                                  \
     {                                                                                   \
         const C eu = (EU);                                                              \
-        const C bm1 = (three + four5 * eu) * eu - usq;                                  \
-        const C ofeq = (OW) * (drho + rho * bm1);                                       \
-        const C sa = (W) * ((PX) + (PY));                                               \
-        f[A] = om1 * f[A] + (ofeq + (sa + sa * bm1));                                   \
+        const C bm1 = ffma(ffma(four5, eu, three), eu, -usq);                           \
+        const C ofeq = fmul((OW), ffma(rho, bm1, drho));                                \
+        const C sa = fmul((W), (PX) + (PY));                                            \
+        f[A] = ffma(om1, f[A], ofeq + ffma(sa, bm1, sa));                               \
     }
     LKS_DIRL(0, C(0), p.owf0, w0, px0, py0)
     LKS_DIRL(1, ux, p.owf1, w1, pxp, py0)
@@ -274,20 +292,7 @@ __device__ __forceinline__ void collide_node_lorentz(C f[9], C gx[5], C gy[5], c
     LKS_DIRL(7, -ux - uy, p.owf5, w5, pxm, pym)
     LKS_DIRL(8, ux - uy, p.owf5, w5, pxp, pym)
 #undef LKS_DIRL
-    const C om1m = p.om1m;
-    const C ce = p.owm1 * (three * (ux * by - uy * bx));
-    const C cb0 = p.owm0 * bx, cb1 = p.owm1 * bx;
-    const C cd0 = p.owm0 * dby, cd1 = p.owm1 * dby;
-    gx[0] = om1m * gx[0] + cb0;
-    gx[1] = om1m * gx[1] + cb1;
-    gx[2] = om1m * gx[2] + (cb1 - ce);
-    gx[3] = om1m * gx[3] + cb1;
-    gx[4] = om1m * gx[4] + (cb1 + ce);
-    gy[0] = om1m * gy[0] + cd0;
-    gy[1] = om1m * gy[1] + (cd1 + ce);
-    gy[2] = om1m * gy[2] + cd1;
-    gy[3] = om1m * gy[3] + (cd1 - ce);
-    gy[4] = om1m * gy[4] + cd1;
+    collide_g(gx, gy, ux, uy, bx, by, dby, p);
 }
 
 template <typename C, int COUPLING>
@@ -352,7 +357,7 @@ __device__ __forceinline__ void step_node_with(const S* fin, const S* gin, S* fo
             f[2] = L::ld(fin + 4 * N + rc + i);
             f[5] = L::ld(fin + 7 * N + rc + i) + w.du;
             f[6] = L::ld(fin + 8 * N + rc + i) - w.du;
-            gx[2] = w.r * L::ld(gxin + 4 * N + rc + i) + w.kx;
+            gx[2] = ffma(w.r, L::ld(gxin + 4 * N + rc + i), w.kx);
             gy[2] = -L::ld(gyin + 4 * N + rc + i);
         }
         if (top) {
@@ -360,7 +365,7 @@ __device__ __forceinline__ void step_node_with(const S* fin, const S* gin, S* fo
             f[4] = L::ld(fin + 2 * N + rc + i);
             f[7] = L::ld(fin + 5 * N + rc + i) - w.du;
             f[8] = L::ld(fin + 6 * N + rc + i) + w.du;
-            gx[4] = w.r * L::ld(gxin + 2 * N + rc + i) + w.kx;
+            gx[4] = ffma(w.r, L::ld(gxin + 2 * N + rc + i), w.kx);
             gy[4] = -L::ld(gyin + 2 * N + rc + i);
         }
     } else {

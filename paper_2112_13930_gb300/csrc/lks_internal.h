@@ -54,6 +54,9 @@ inline size_t storage_bytes(int storage) { return storage == 0 ? 8 : (storage ==
 // One fused step: (fin, gin) -> (fout, gout) on stream st.
 cudaError_t launch_step(int storage, int closure, const void* fin, const void* gin, void* fout, void* gout,
                         const StepParams<double>& p, cudaStream_t st);
+// In-place (one-buffer) step, phase 0 or 1 of a pair (lks_aa.cuh); f, g are the single buffers.
+cudaError_t launch_step_aa(int storage, int closure, int phase, void* f, void* g, const StepParams<double>& pd,
+                           cudaStream_t st);
 
 // Initial equilibrium state (deviation form) with the counter-based perturbation.
 cudaError_t launch_init(int storage, void* f, void* g, int nx, int ny, double B0, uint64_t seed, double amp,

@@ -48,7 +48,7 @@ class LksParams(ctypes.Structure):
         ("dev_buffer", ctypes.c_void_p),
         ("dev_buffer_bytes", ctypes.c_size_t),
         ("coupling", ctypes.c_int32),
-        ("pad", ctypes.c_int32),
+        ("inplace", ctypes.c_int32),
     ]
 
 
@@ -120,15 +120,15 @@ def _dptr(a):
 
 
 def make_params(nx, ny, tau_f, tau_m, B0, Fx=0.0, closure="link", storage="f64", seed=0, perturb_amp=0.0,
-                stream=0, dev_buffer=0, dev_buffer_bytes=0, coupling="maxwell"):
+                stream=0, dev_buffer=0, dev_buffer_bytes=0, coupling="maxwell", inplace=False):
     return LksParams(nx=nx, ny=ny, closure=CLOSURES[closure], storage=STORAGES[storage], tau_f=tau_f, tau_m=tau_m,
                      B0=B0, Fx=Fx, seed=seed, perturb_amp=perturb_amp, cuda_stream=stream or None,
                      dev_buffer=dev_buffer or None, dev_buffer_bytes=dev_buffer_bytes, coupling=COUPLINGS[coupling],
-                     pad=0)
+                     inplace=int(bool(inplace)))
 
 
-def footprint_bytes(nx, ny, closure="link", storage="f64", tau_f=0.8, tau_m=0.8):
-    p = make_params(nx, ny, tau_f, tau_m, 0.0, closure=closure, storage=storage)
+def footprint_bytes(nx, ny, closure="link", storage="f64", tau_f=0.8, tau_m=0.8, inplace=False):
+    p = make_params(nx, ny, tau_f, tau_m, 0.0, closure=closure, storage=storage, inplace=inplace)
     return int(load().lks_footprint_bytes(ctypes.byref(p)))
 
 
@@ -136,7 +136,8 @@ class Lattice:
     """One channel lattice resident on the GPU (a wrapped lks_handle)."""
 
     def __init__(self, nx, ny, tau_f, tau_m, B0, Fx=0.0, closure="link", storage="f64", seed=0, perturb_amp=0.0,
-                 stream=None, torch_memory=True, coupling="maxwell"):
+                 stream=None, torch_memory=True, coupling="maxwell", inplace=False):
+        """inplace=True: one population buffer updated in place, steps in pairs (even counts)."""
         import torch
         L = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -148,7 +149,8 @@ class Lattice:
             stream = torch.cuda.current_stream()
         self.stream = stream
         p = make_params(nx, ny, tau_f, tau_m, B0, Fx, closure, storage, seed, perturb_amp, stream.cuda_stream,
-                        coupling=coupling)
+                        coupling=coupling, inplace=inplace)
+        self.inplace = bool(inplace)
         self.nbytes = int(L.lks_footprint_bytes(ctypes.byref(p)))
         if self.nbytes == 0:
             raise LksError(LKS_EINVAL, "invalid lattice parameters")

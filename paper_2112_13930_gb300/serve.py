@@ -35,9 +35,10 @@ from . import sweep as _sweep
 TAU = _sweep.TAU
 
 
-def _default_lattice(req, storage, stream):
+def _default_lattice(req, storage, stream, inplace=False):
     p = _sweep.lattice_params(req)
-    lat = _lks.Lattice(req["nx"], req["ny"], TAU, TAU, p["B0"], p["Fx"], req["closure"], storage, stream=stream)
+    lat = _lks.Lattice(req["nx"], req["ny"], TAU, TAU, p["B0"], p["Fx"], req["closure"], storage, stream=stream,
+                       inplace=inplace)
     lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
     return lat
 
@@ -45,8 +46,12 @@ def _default_lattice(req, storage, stream):
 class Server:
     def __init__(self, storage="f32", budget_bytes=120 << 30, small_pool_bytes=8 << 30, small_max_nodes=32768,
                  max_small=8192, large_workers=6, tol=1e-9, check_every=100, quantum=2000, max_steps=10**9,
-                 shape=None, batch=None, lattice_factory=None, streams=None):
+                 shape=None, batch=None, lattice_factory=None, streams=None, inplace=False):
+        """inplace=True: every request keeps one population buffer (in-place pairs of steps, same
+        results), so the memory budget admits about twice the requests; quantum, check_every and
+        max_steps must then be even."""
         self.storage = storage
+        self.inplace = bool(inplace)
         self.tol, self.check_every, self.quantum, self.max_steps = tol, check_every, quantum, max_steps
         self.small_max_nodes = small_max_nodes
         small_pool_bytes = min(small_pool_bytes, budget_bytes // 2)
@@ -55,9 +60,10 @@ class Server:
         if batch is None:
             batch = _batch.Batch(storage, max_instances=max_small, pool_bytes=small_pool_bytes,
                                  threads_per_group=shape[0] if shape else 0, groups_per_cta=shape[1] if shape else 0,
-                                 cluster_ctas=shape[2] if shape and len(shape) > 2 else 0)
+                                 cluster_ctas=shape[2] if shape and len(shape) > 2 else 0, inplace=inplace)
         self.batch = batch
-        self.lattice_factory = lattice_factory or (lambda req, stream: _default_lattice(req, storage, stream))
+        self.lattice_factory = lattice_factory or (
+            lambda req, stream: _default_lattice(req, storage, stream, inplace))
         if streams is None:
             import torch
             streams = [torch.cuda.Stream() for _ in range(large_workers)]
@@ -75,8 +81,8 @@ class Server:
     def footprint(self, req):
         d = _sweep.make_desc(req, self.tol, self.check_every, self.max_steps)
         if self.is_small(req):
-            return _batch.instance_footprint(d, self.storage)
-        return _lks.footprint_bytes(req["nx"], req["ny"], req["closure"], self.storage)
+            return _batch.instance_footprint(d, self.storage, self.inplace)
+        return _lks.footprint_bytes(req["nx"], req["ny"], req["closure"], self.storage, inplace=self.inplace)
 
     # -- small lane ------------------------------------------------------------------------
     def try_admit_small(self, req, now, out):
@@ -224,20 +230,35 @@ def serve_one_at_a_time(trace, storage="f64", tol=1e-9, check_every=100, max_ste
         lat.close()
         torch.cuda.synchronize()
         t_done = time.perf_counter() - t0
+        state = {_lks.LKS_OK: "converged", _lks.LKS_ENOTCONVERGED: "max_steps",
+                 _lks.LKS_EUNSTABLE: "unstable"}.get(status, "error")
         out.append({"req": req, "t_arrival": req["t_arrival"], "t_done": t_done, "latency": t_done - req["t_arrival"],
-                    "steps": int(steps), "residual": r, "status": int(status), "u": u, "b": b})
+                    "steps": int(steps), "residual": r, "status": int(status), "state": state, "u": u, "b": b})
         if time_limit is not None and t_done > time_limit:
             break
     return out
 
 
+STEADY_STATES = ("converged", "stalled")
+
+
 def summarize(records, n_offered):
+    """Throughput and latency over the requests that finished.  `completed` counts every request
+    the server ran to an end (steady state, its step cap, or instability); `steady` counts those
+    that reached steady state (residual below tol, or stalled at the storage's rounding floor),
+    with their own rate and latency percentiles."""
     done = [r for r in records if r.get("state") not in ("rejected", "cancelled", "error")]
+    steady = [r for r in done if r.get("state") in STEADY_STATES]
     lat = np.array([r["latency"] for r in done]) if done else np.array([np.nan])
+    lat_s = np.array([r["latency"] for r in steady]) if steady else np.array([np.nan])
     t_first = min(r["t_arrival"] for r in done) if done else 0.0
     t_last = max(r["t_done"] for r in done) if done else 0.0
+    span = max(1e-9, t_last - t_first)
     states = collections.Counter(r.get("state", "done") for r in records)
     return {"offered": n_offered, "completed": len(done),
-            "solves_per_s": len(done) / max(1e-9, t_last - t_first),
+            "solves_per_s": len(done) / span,
             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "steady": len(steady), "steady_per_s": len(steady) / span,
+            "steady_latency_p50_s": float(np.percentile(lat_s, 50)),
+            "steady_latency_p99_s": float(np.percentile(lat_s, 99)),
             "makespan_s": t_last - t_first, "states": dict(states)}

@@ -62,6 +62,20 @@ def test_instance_footprint_and_batch_config_validation(lib):
     cfg = batch.BatchConfig(storage=1, max_instances=4, pool_bytes=1 << 20, threads_per_group=128, groups_per_cta=1,
                             cluster_ctas=3)
     assert lib.lks_batch_create(ctypes.byref(cfg), ctypes.byref(h)) == lks.LKS_EINVAL
+    cfg = batch.BatchConfig(storage=1, max_instances=4, pool_bytes=1 << 20, threads_per_group=128, groups_per_cta=1,
+                            coupling=2)
+    assert lib.lks_batch_create(ctypes.byref(cfg), ctypes.byref(h)) == lks.LKS_EINVAL
+    lor = batch.make_desc(4, 20, "link", 0.8, 1.02, 0.01, coupling="lorentz")   # |tau_m - 1| < 0.05
+    assert batch.instance_footprint(lor, "f32") == 0
+    cfg = batch.BatchConfig(storage=1, max_instances=4, pool_bytes=1 << 20, threads_per_group=128, groups_per_cta=1,
+                            inplace=2)
+    assert lib.lks_batch_create(ctypes.byref(cfg), ctypes.byref(h)) == lks.LKS_EINVAL
+    # in place: one population buffer per instance, and even check/step counts
+    d = batch.make_desc(8, 100, "moment", 0.8, 0.8, 0.01, check_every=100, max_steps=1000)
+    two, one = batch.instance_footprint(d, "f32"), batch.instance_footprint(d, "f32", inplace=True)
+    assert two - one == 28928 + 32000    # the f (9 x 800 x 4 B) and g (10 x 800 x 4 B) planes, 256-byte aligned
+    odd = batch.make_desc(8, 100, "moment", 0.8, 0.8, 0.01, check_every=101)
+    assert batch.instance_footprint(odd, "f32") > 0 and batch.instance_footprint(odd, "f32", inplace=True) == 0
     assert lib.lks_batch_destroy(None) == lks.LKS_OK
 
 
@@ -72,6 +86,17 @@ def test_footprint_counts_both_buffers(lib):
         pops = 2 * 19 * nx * ny * sb
         snap = 2 * nx * ny * 8
         assert pops + snap <= fp < pops + snap + 1 << 20
+
+
+def test_inplace_footprint_is_one_population_buffer(lib):
+    nx, ny = 4096, 4096
+    for storage, sb in (("f64", 8), ("f32", 4), ("bf16", 2), ("f16", 2)):
+        two = lks.footprint_bytes(nx, ny, "moment", storage)
+        one = lks.footprint_bytes(nx, ny, "moment", storage, inplace=True)
+        assert two - one == 19 * nx * ny * sb   # 9 f + 10 g planes, 256-byte multiples here
+    p = lks.make_params(8, 8, 0.8, 0.8, 0.01)
+    p.inplace = 2
+    assert lib.lks_footprint_bytes(ctypes.byref(p)) == 0
 
 
 @pytest.mark.parametrize("kw,ok", [

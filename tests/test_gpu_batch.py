@@ -189,3 +189,58 @@ def test_autotune_leaves_states_untouched(mods):
         assert np.array_equal(ref.moments(a), tun.moments(c))
     ref.close()
     tun.close()
+
+
+def _lorentz_descs(batch, **kw):
+    descs = _descs(batch, **kw)
+    for d in descs:
+        d.coupling = 1
+    return descs
+
+
+@pytest.mark.parametrize("shape", [(128, 2, 1), (128, 1, 4)])
+def test_batch_lorentz_fp64_matches_oracle(mods, shape):
+    """The Lorentz-force coupling (Sec. III source term, J from the non-equilibrium moment of g)
+    in the batched engine: FP64 instances equal the oracle with coupling 1 within 1e-11."""
+    lks, batch = mods
+    b = batch.Batch("f64", max_instances=16, pool_bytes=64 << 20, threads_per_group=shape[0], groups_per_cta=shape[1],
+                    cluster_ctas=shape[2], coupling="lorentz")
+    descs = _lorentz_descs(batch)
+    slots = [b.add(d) for d in descs]
+    b.run(60)
+    for d, s in zip(descs, slots):
+        o = oracle.Oracle(d.nx, d.ny, d.tau_f, d.tau_m, d.B0, d.Fx, d.closure, d.c_bottom, d.c_top, d.u_bottom,
+                          d.u_top, seed=d.seed, perturb_amp=d.perturb_amp, coupling=1)
+        o.step(60)
+        mo, mg = o.moments(), b.moments(s)
+        for m in (0, 1, 3):
+            scale = np.max(np.abs(mo[m]))
+            assert np.max(np.abs(mg[m] - mo[m])) <= 1e-11 * scale, (d.closure, m)
+    b.close()
+
+
+@pytest.mark.parametrize("shape", [(64, 4, 1), (64, 1, 8)])
+def test_batch_lorentz_matches_single_lattice_bitwise(mods, shape):
+    lks, batch = mods
+    b = batch.Batch("f32", max_instances=16, pool_bytes=64 << 20, threads_per_group=shape[0],
+                    groups_per_cta=shape[1], cluster_ctas=shape[2], coupling="lorentz")
+    descs = _lorentz_descs(batch)
+    slots = [b.add(d) for d in descs]
+    b.run(250)
+    for d, s in zip(descs, slots):
+        g = lks.Lattice(d.nx, d.ny, d.tau_f, d.tau_m, d.B0, d.Fx, d.closure, "f32", seed=d.seed,
+                        perturb_amp=d.perturb_amp, coupling="lorentz")
+        g.set_walls(d.c_bottom, d.c_top, d.u_bottom, d.u_top)
+        g.step(250)
+        assert np.array_equal(g.moments(), b.moments(s))
+        g.close()
+    b.close()
+
+
+def test_batch_rejects_mixed_coupling(mods):
+    lks, batch = mods
+    b = batch.Batch("f32", max_instances=4, pool_bytes=8 << 20)
+    d = batch.make_desc(4, 20, "link", 0.8, 0.8, 0.01, coupling="lorentz")
+    with pytest.raises(lks.LksError):
+        b.add(d)
+    b.close()

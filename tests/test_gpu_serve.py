@@ -28,11 +28,14 @@ def _trace(workloads):
     return tr
 
 
-def test_served_results_equal_solo_results(mods):
+@pytest.mark.parametrize("inplace", [False, True])
+def test_served_results_equal_solo_results(mods, inplace):
+    """Served (two-buffer or in-place) results equal the two-buffer solo solves bit for bit."""
     lks, batch, serve, sweep, workloads = mods
     tr = _trace(workloads)
     srv = serve.Server("f32", budget_bytes=1 << 30, small_pool_bytes=256 << 20, small_max_nodes=400,
-                       large_workers=2, tol=1e-7, check_every=100, quantum=300, max_steps=4000, shape=(64, 2))
+                       large_workers=2, tol=1e-7, check_every=100, quantum=300, max_steps=4000, shape=(64, 2),
+                       inplace=inplace)
     recs = srv.serve(tr, time_limit=300)
     srv.close()
     assert len(recs) == len(tr)
