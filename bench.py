@@ -329,7 +329,12 @@ def bench_ours(args):
                                           "achieved": round(FP64_FLOPS_PER_NODE * v64 * 1e6 / 1e12, 3),
                                           "peak": 1.25, "unit": "TFLOP/s",
                                           "frac": round(FP64_FLOPS_PER_NODE * v64 * 1e6 / 1.25e12, 4),
-                                          "peak_source": "nominal GB300 FP64 rate"}}
+                                          "peak_source": "nominal GB300 FP64 rate"},
+                         "roofline_fp64_pipe": {"bound": "fp64 pipe", "instr_per_node": FP64_PIPE_INSTR_PER_NODE,
+                                                "achieved": round(FP64_PIPE_INSTR_PER_NODE * v64 * 1e6 / 1e12, 4),
+                                                "peak": FP64_PIPE_PEAK / 1e12, "unit": "T FP64 instr/s",
+                                                "frac": round(FP64_PIPE_INSTR_PER_NODE * v64 * 1e6 / FP64_PIPE_PEAK, 4),
+                                                "source": "profiles/step_kernel_f64_2048sq_fp64_pipe.md"}}
         l64.close()
         del l64
         # the paper's own coupling (Lorentz force in the source), FP32, same workload
@@ -706,6 +711,10 @@ def bench_c1(args):
 # FP64 arithmetic per bulk node per step in collide_node, counted from the source with an FMA as
 # 2 flops: moments and 1/rho (Newton) 40, equilibrium set-up 23, nine directions 116, g 33.
 FP64_FLOPS_PER_NODE = 212
+# FP64 pipe instructions per node of the FP64 step kernel (ncu sm__inst_executed_pipe_fp64.sum x 32
+# / nodes at 2048^2) and the pipe's nominal rate (1.25 TFLOP/s = 0.625e12 DFMA/s on GB300)
+FP64_PIPE_INSTR_PER_NODE = 153
+FP64_PIPE_PEAK = 0.625e12
 
 
 def main():

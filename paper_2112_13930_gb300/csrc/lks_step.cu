@@ -11,6 +11,7 @@
 //   moment-based wall rows reconstruct them from the pulled ones (Sec. VII, App. A, B.2).
 #include "lks_device.cuh"
 #include "lks_internal.h"
+#include "lks_packed.cuh"
 
 namespace lks {
 
@@ -42,29 +43,6 @@ __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ fin, co
 // the left supplies x0-1 through a warp shuffle (a direct 16-bit load at a warp or row edge,
 // wrapping periodically); a pull from x+1 needs (x0+1, x0+2) likewise from the lane to the right.
 // Per node the arithmetic is exactly that of step_node, so results are bit-identical to it.
-template <typename S>
-struct Packed;
-template <>
-struct Packed<__nv_bfloat16> {
-    static __device__ __forceinline__ float lo(uint32_t w) { return __uint_as_float(w << 16); }
-    static __device__ __forceinline__ float hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-    static __device__ __forceinline__ uint32_t pack(float a, float b) {
-        __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<uint32_t*>(&v);
-    }
-};
-template <>
-struct Packed<__half> {
-    static __device__ __forceinline__ float lo(uint32_t w) {
-        return __half2float(__ushort_as_half((unsigned short)(w & 0xffffu)));
-    }
-    static __device__ __forceinline__ float hi(uint32_t w) { return __half2float(__ushort_as_half((unsigned short)(w >> 16))); }
-    static __device__ __forceinline__ uint32_t pack(float a, float b) {
-        __half2 v = __floats2half2_rn(a, b);
-        return *reinterpret_cast<uint32_t*>(&v);
-    }
-};
-
 template <typename S, int CLOSURE, int COUPLING, bool ROWS2D>
 __global__ void __launch_bounds__(256, 4) step_kernel_pair(const S* __restrict__ fin, const S* __restrict__ gin,
                                                         S* __restrict__ fout, S* __restrict__ gout,

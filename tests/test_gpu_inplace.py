@@ -42,8 +42,10 @@ def _make(lks, nx, ny, closure, storage, coupling, inplace, c, u, amp=1e-3, Fx=2
 
 CASES = [
     # nx, ny: 1D grid with odd nx; nx = 1 (the x-neighbours are the node itself); 2D grid with a
-    # ragged last block (300 = 256 + 44); ny = 3, the smallest moment-based channel
-    (37, 9), (1, 12), (300, 7), (64, 3),
+    # ragged last block (300 = 256 + 44); ny = 3, the smallest moment-based channel.  16-bit
+    # storage with even nx takes the two-nodes-per-thread kernels: 24 pairs per row on the 1D grid
+    # (warps spanning two rows), 65 pairs on the 2D grid (one active lane in the last warp)
+    (37, 9), (1, 12), (300, 7), (64, 3), (48, 10), (130, 5),
 ]
 
 
