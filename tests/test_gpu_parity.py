@@ -367,3 +367,20 @@ def test_checkpoint_resume(lks, tmp_path):
     fg, gg = g.get_state()
     fh, gh = h.get_state()
     assert np.max(np.abs(fg - fh)) < 1e-15 and np.max(np.abs(gg - gh)) < 1e-15
+
+
+def test_c1_matches_stored_golden_profiles(lks):
+    """The 4 x 65 Hartmann channel (link-based, Ha = 10, c = 0.1, 2e4 FP64 steps) against the
+    profiles stored in tests/golden/c1_profiles.txt (written by the oracle): within 1e-11."""
+    import os
+    data = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c1_profiles.txt"))
+    a = 32.5
+    b0 = an.b0_from_ha(10.0, a, 0.8, 0.8)
+    fx = an.force_for_centre_speed(0.01, 10.0, 0.1, a, 0.8)
+    g = lks.Lattice(4, 65, 0.8, 0.8, b0, fx, "link", "f64")
+    g.set_walls(0.1, 0.1)
+    g.step(20000)
+    u, bx = g.profiles()
+    assert np.max(np.abs(u - data[:, 1])) <= REL64 * np.max(np.abs(data[:, 1]))
+    assert np.max(np.abs(bx - data[:, 2])) <= REL64 * np.max(np.abs(data[:, 2]))
+    g.close()
