@@ -3,6 +3,8 @@
 - Hartmann flow between plates with equal wall conductance ratio c (Sec. VIII.A,
   the Chang & Lundgren profiles u*(xi), B_x*(xi) with U_ref = a^2 F/(rho nu),
   B_ref = a^2 F mu_m (sigma/(rho nu))^(1/2), Ha = B0 a (sigma/(rho nu))^(1/2)).
+- the same body-force flow with lower/upper ratios c_l, c_u (derived in hartmann_walls_constants
+  the way App. C treats the shear-driven case).
 - Hartmann-Couette flow with lower/upper ratios c_l, c_u, top wall moving at U_w
   (App. C, Eqs. 1DMHDmovingwallfinalsolution and 1DMHDmovingwallintconstants;
   u* = u/U_w, B* = B_x/(U_w (rho nu sigma)^(1/2) mu_m)).
@@ -62,6 +64,46 @@ def hartmann_b_star(xi, ha, c):
     return -xi / ha + (1.0 / ha) * _hartmann_factor(ha, c) * _sinh_over_cosh(ha, xi)
 
 
+def hartmann_walls_constants(ha, c_l, c_u):
+    """P, D of body-force Hartmann flow with lower/upper wall conductance ratios c_l, c_u.
+
+    Derived here the way App. C treats the shear-driven case: integrating B*'' + Ha u*' = 0 once
+    gives B*' + Ha u* = K, so u*'' - Ha^2 u* = -(1 + Ha K) and, with u*(+-1) = 0,
+        u* = P (1 - cosh(Ha xi)/cosh Ha),   B* = -xi/Ha + P sinh(Ha xi)/cosh Ha + D,
+    P = (1 + Ha K)/Ha^2.  The Shercliff conditions -B*' + B*/c_l = 0 at xi = -1 and
+    B*' + B*/c_u = 0 at xi = +1, multiplied by c, read
+        P (Ha c_u + t) + D = (1 + c_u)/Ha,   -P (Ha c_l + t) + D = -(1 + c_l)/Ha,   t = tanh Ha,
+    whence P = (2 + c_l + c_u)/(Ha (Ha (c_l + c_u) + 2 t)) and D = (1 + c_u)/Ha - P (Ha c_u + t),
+    which expands to D = (c_l - c_u)(Ha - t)/(Ha (Ha (c_l + c_u) + 2 t)) (no cancellation of large
+    terms when a ratio is large).  c = inf reduces its condition to B*' = 0: P = 1/Ha^2 and
+    D = -+(Ha - t)/Ha^2 for c_u or c_l infinite; with both walls perfectly conducting D is taken as
+    0, the symmetric limit (D is then fixed by the initial state, not by the walls).  c_l = c_u
+    gives D = 0 and P = (c + 1)/(Ha (Ha c + t)), the equal-walls profile."""
+    t = math.tanh(ha)
+    if math.isinf(c_l) and math.isinf(c_u):
+        return 1.0 / (ha * ha), 0.0
+    if math.isinf(c_u):
+        return 1.0 / (ha * ha), -(ha - t) / (ha * ha)
+    if math.isinf(c_l):
+        return 1.0 / (ha * ha), (ha - t) / (ha * ha)
+    den = ha * (ha * (c_l + c_u) + 2.0 * t)
+    return (2.0 + c_l + c_u) / den, (c_l - c_u) * (ha - t) / den
+
+
+def hartmann_walls_u_star(xi, ha, c_l, c_u):
+    """u/U_ref of body-force Hartmann flow with conductance ratios c_l (xi = -1) and c_u (xi = +1)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    p, _ = hartmann_walls_constants(ha, c_l, c_u)
+    return p * (1.0 - _cosh_ratio(ha, xi))
+
+
+def hartmann_walls_b_star(xi, ha, c_l, c_u):
+    """B_x/B_ref of body-force Hartmann flow with conductance ratios c_l (xi = -1) and c_u (xi = +1)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    p, d = hartmann_walls_constants(ha, c_l, c_u)
+    return -xi / ha + p * _sinh_over_cosh(ha, xi) + d
+
+
 def couette_constants(ha, c_l, c_u):
     """K1, K2 of App. C (Eq. 1DMHDmovingwallintconstants), in the s, l form."""
     t = math.tanh(ha)
@@ -118,6 +160,15 @@ def hartmann_profiles(y, a, ha, c, fx, tau_f, tau_m):
     b_ref = a * a * fx / math.sqrt(nu * eta)
     xi = np.asarray(y, dtype=np.float64) / a
     return u_ref * hartmann_u_star(xi, ha, c), b_ref * hartmann_b_star(xi, ha, c)
+
+
+def hartmann_walls_profiles(y, a, ha, c_l, c_u, fx, tau_f, tau_m):
+    """Dimensional u_x(y), B_x(y) of body-force Hartmann flow with conductance ratios c_l, c_u."""
+    nu, eta = lattice_scales(tau_f, tau_m)
+    u_ref = a * a * fx / nu
+    b_ref = a * a * fx / math.sqrt(nu * eta)
+    xi = np.asarray(y, dtype=np.float64) / a
+    return u_ref * hartmann_walls_u_star(xi, ha, c_l, c_u), b_ref * hartmann_walls_b_star(xi, ha, c_l, c_u)
 
 
 def couette_profiles(y, a, ha, c_l, c_u, u_w, tau_f, tau_m):

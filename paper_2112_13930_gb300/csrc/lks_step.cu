@@ -43,8 +43,12 @@ __global__ void __launch_bounds__(256) step_kernel(const S* __restrict__ fin, co
 // the left supplies x0-1 through a warp shuffle (a direct 16-bit load at a warp or row edge,
 // wrapping periodically); a pull from x+1 needs (x0+1, x0+2) likewise from the lane to the right.
 // Per node the arithmetic is exactly that of step_node, so results are bit-identical to it.
+// Register budget: the moment-based variants fit 64 registers (4 blocks of 256 per SM); the
+// link-based ones, which also load the wall node's own outgoing words, spill at 64 and run faster
+// with 80 (3 blocks per SM): 69.5 against 61.3 GLUPS for BF16 at 8192^2, while 3 blocks cost the
+// moment-based variants 7 % (69.6 against 74.8 GLUPS at 4096^2).
 template <typename S, int CLOSURE, int COUPLING, bool ROWS2D>
-__global__ void __launch_bounds__(256, 4) step_kernel_pair(const S* __restrict__ fin, const S* __restrict__ gin,
+__global__ void __launch_bounds__(256, CLOSURE == 0 ? 3 : 4) step_kernel_pair(const S* __restrict__ fin, const S* __restrict__ gin,
                                                         S* __restrict__ fout, S* __restrict__ gout,
                                                         const StepParams<float> p) {
     typedef Packed<S> P;

@@ -1,7 +1,8 @@
 """Closed-form steady profiles for the accuracy gate of solved channels (product side).
 
 Body-force Hartmann flow between plates of equal wall conductance ratio c (Chang & Lundgren, as
-quoted in Sec. VIII.A) and Hartmann-Couette flow with lower/upper ratios c_l, c_u and the top plate
+quoted in Sec. VIII.A), the same flow with a different ratio on each plate (solved like App. C's
+shear-driven case), and Hartmann-Couette flow with lower/upper ratios c_l, c_u and the top plate
 at U_w (App. C, Eqs. 1DMHDmovingwallfinalsolution / 1DMHDmovingwallintconstants).  Written with
 exponentials of Ha (|xi| - 1), which stay finite for any Ha, and with the App. C constants in the
 form that is finite at c_u = 0 (numerator and denominator multiplied by c_u).
@@ -53,6 +54,38 @@ def hartmann_force(u_c, ha, c, a, tau_f):
     nu = (tau_f - 0.5) / 3.0
     k = 1.0 / ha if math.isinf(c) else (c + 1.0) / (ha * c + math.tanh(ha))
     return u_c * nu / (a * a * (k / ha) * (1.0 - 1.0 / math.cosh(ha)))
+
+
+def _walls_pd(ha, c_l, c_u):
+    """Amplitude P of u/U_ref and offset D of B_x/B_ref for body-force Hartmann flow with the
+    lower/upper conductance ratios c_l, c_u: the Shercliff conditions at both plates fix
+    P = (2 + c_l + c_u)/(Ha (Ha (c_l + c_u) + 2 tanh Ha)), D = (c_l - c_u)(Ha - tanh Ha)/(same)."""
+    t = math.tanh(ha)
+    if math.isinf(c_l) or math.isinf(c_u):
+        if math.isinf(c_l) and math.isinf(c_u):
+            return 1.0 / ha ** 2, 0.0
+        sign = 1.0 if math.isinf(c_l) else -1.0
+        return 1.0 / ha ** 2, sign * (ha - t) / ha ** 2
+    den = ha * (ha * (c_l + c_u) + 2.0 * t)
+    return (2.0 + c_l + c_u) / den, (c_l - c_u) * (ha - t) / den
+
+
+def hartmann_walls(y, a, ha, c_l, c_u, fx, tau_f, tau_m):
+    """u_x(y), B_x(y) of body-force Hartmann flow with conductance ratio c_l on the lower plate and
+    c_u on the upper one (either may be math.inf)."""
+    nu, eta = (tau_f - 0.5) / 3.0, (tau_m - 0.5) / 3.0
+    xi = np.asarray(y, dtype=np.float64) / a
+    pa, d = _walls_pd(ha, c_l, c_u)
+    u = (a * a * fx / nu) * pa * (1.0 - _ch(ha, xi))
+    b = (a * a * fx / math.sqrt(nu * eta)) * (-xi / ha + pa * _sh(ha, xi) + d)
+    return u, b
+
+
+def hartmann_walls_force(u_c, ha, c_l, c_u, a, tau_f):
+    """Body force that gives centreline speed u_c with conductance ratios c_l, c_u."""
+    nu = (tau_f - 0.5) / 3.0
+    pa, _ = _walls_pd(ha, c_l, c_u)
+    return u_c * nu / (a * a * pa * (1.0 - 1.0 / math.cosh(ha)))
 
 
 def couette(y, a, ha, c_l, c_u, u_w, tau_f, tau_m):

@@ -8,6 +8,9 @@ E3     grid convergence, Ha = 20, tau = 0.9, tau_m = 0.95, N in {50, 100, 200}, 
 E4/E5  Hartmann-Couette flow, top plate at U_w = 0.05, 3 x 101 nodes, tau = 0.6, tau_m = 0.65,
        Ha in {5, 20}, (c_u, c_l) in {(0, 0), (0.5, 0.5), (0, 0.5)}, link- / moment-based (Sec. VIII.B);
 E6     Hartmann-Couette, Ha = 5, c_l = 0, c_u in {0, 0.1, 0.5, 1, 1e4}, both closures (Sec. VIII.B).
+E7     body-force Hartmann flow with a different conductance ratio on each plate (not in the paper:
+       the closed form is solved here like App. C's shear-driven case), 3 x 101, tau = 0.57,
+       tau_m = 0.75, Ha in {5, 20}, (c_l, c_u) in {(0, 0.5), (0.1, 2), (0, 1e4)}, both closures.
 
 Every case runs to a residual of 1e-10 (FP64).  Profiles are written as CSV (y, u_x, u_x closed
 form, B_x, B_x closed form) with a summary CSV of the relative L2 errors and the measured
@@ -47,6 +50,11 @@ def cases():
         for cu in C_E1:
             out.append(dict(exp="E6", kind="shear", closure=closure, ny=101, nx=3, ha=5.0, c_l=0.0, c_u=cu,
                             tau_f=0.6, tau_m=0.65, u_w=0.05))
+    for closure in ("link", "moment"):
+        for ha in HA_E1:
+            for cl, cu in ((0.0, 0.5), (0.1, 2.0), (0.0, 1e4)):
+                out.append(dict(exp="E7", kind="body", closure=closure, ny=101, nx=3, ha=ha, c_l=cl, c_u=cu,
+                                tau_f=0.57, tau_m=0.75, u_c=0.01))
     return out
 
 
@@ -56,7 +64,7 @@ def _desc(case, tol, max_steps):
     eta = (case["tau_m"] - 0.5) / 3.0
     b0 = case["ha"] * math.sqrt(nu * eta) / a
     if case["kind"] == "body":
-        fx = profiles.hartmann_force(case["u_c"], case["ha"], case["c_u"], a, case["tau_f"])
+        fx = profiles.hartmann_walls_force(case["u_c"], case["ha"], case["c_l"], case["c_u"], a, case["tau_f"])
         d = _batch.make_desc(case["nx"], case["ny"], case["closure"], case["tau_f"], case["tau_m"], b0, fx,
                              case["c_l"], case["c_u"], tol=tol, check_every=100, max_steps=max_steps)
     else:
@@ -83,7 +91,8 @@ def run(out_dir, tol=1e-10, max_steps=20_000_000, quantum=50_000, storage="f64")
         u, bx = b.profiles(s)
         _, y = profiles.node_y(case["ny"], case["closure"])
         if case["kind"] == "body":
-            ua, ba = profiles.hartmann(y, a, case["ha"], case["c_u"], fx, case["tau_f"], case["tau_m"])
+            ua, ba = profiles.hartmann_walls(y, a, case["ha"], case["c_l"], case["c_u"], fx, case["tau_f"],
+                                             case["tau_m"])
         else:
             ua, ba = profiles.couette(y, a, case["ha"], case["c_l"], case["c_u"], case["u_w"], case["tau_f"],
                                       case["tau_m"])

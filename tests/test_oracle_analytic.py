@@ -49,6 +49,52 @@ def test_hartmann_solves_bvp(ha, c):
         assert abs(c * db_hi + b(1.0)) < tol * max(1.0, c)
 
 
+WALLS_CASES = [(ha, cl, cu) for ha in (1.0, 5.0, 20.0)
+               for cl, cu in ((0.0, 0.5), (0.1, 2.0), (1e4, 0.0), (math.inf, 0.3), (0.5, math.inf))]
+
+
+@pytest.mark.parametrize("ha,cl,cu", WALLS_CASES)
+def test_hartmann_walls_solves_bvp(ha, cl, cu):
+    """Body force with different conductance ratios on the two plates: the same ODEs, u* = 0 at
+    the plates, and the Shercliff condition with c_l at xi = -1 and c_u at xi = +1."""
+    u = lambda x: an.hartmann_walls_u_star(x, ha, cl, cu)
+    b = lambda x: an.hartmann_walls_b_star(x, ha, cl, cu)
+    h = 1e-4 if ha < 10 else 2e-5
+    xi = np.linspace(-0.98, 0.98, 41)
+    scale = max(1.0, ha * ha * float(np.max(np.abs(u(np.linspace(-1, 1, 201))))))
+    assert np.max(np.abs(_d2(u, xi, h) + ha * _d1(b, xi, h) + 1.0)) < 1e-3 * scale
+    assert np.max(np.abs(_d2(b, xi, h) + ha * _d1(u, xi, h))) < 1e-3 * scale
+    assert abs(u(-1.0)) < 1e-12 and abs(u(1.0)) < 1e-12
+    hh = 1e-6
+    db_lo = (b(-1.0 + hh) - b(-1.0)) / hh
+    db_hi = (b(1.0) - b(1.0 - hh)) / hh
+    tol = 1e-4 * max(1.0, ha)
+    if math.isinf(cl):
+        assert abs(db_lo) < tol
+    else:
+        assert abs(-cl * db_lo + b(-1.0)) < tol * max(1.0, cl)
+    if math.isinf(cu):
+        assert abs(db_hi) < tol
+    else:
+        assert abs(cu * db_hi + b(1.0)) < tol * max(1.0, cu)
+
+
+@pytest.mark.parametrize("ha,c", HARTMANN_CASES)
+def test_hartmann_walls_equal_ratios_is_equal_walls_profile(ha, c):
+    xi = np.linspace(-1, 1, 41)
+    assert np.allclose(an.hartmann_walls_u_star(xi, ha, c, c), an.hartmann_u_star(xi, ha, c), rtol=1e-12, atol=1e-15)
+    assert np.allclose(an.hartmann_walls_b_star(xi, ha, c, c), an.hartmann_b_star(xi, ha, c), rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("ha,cl,cu", WALLS_CASES)
+def test_hartmann_walls_mirror(ha, cl, cu):
+    """Swapping the plates mirrors the flow: u*(xi) unchanged, B* odd under xi -> -xi."""
+    xi = np.linspace(-1, 1, 41)
+    assert np.allclose(an.hartmann_walls_u_star(xi, ha, cu, cl), an.hartmann_walls_u_star(-xi, ha, cl, cu), atol=1e-14)
+    assert np.allclose(an.hartmann_walls_b_star(xi, ha, cu, cl), -an.hartmann_walls_b_star(-xi, ha, cl, cu),
+                       atol=1e-13)
+
+
 @pytest.mark.parametrize("ha", [0.5, 3.0, 10.0, 40.0])
 def test_hartmann_insulating_is_textbook(ha):
     """c = 0: the classical Hartmann (1937) profiles u* = (cosh Ha - cosh Ha xi)/(Ha sinh Ha),

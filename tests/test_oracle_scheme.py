@@ -232,6 +232,23 @@ def test_hartmann_steady_profiles(closure, ha, c):
 
 
 @pytest.mark.parametrize("closure", [oracle.LINK, oracle.MOMENT])
+@pytest.mark.parametrize("ha,cl,cu", [(5.0, 0.0, 0.5), (10.0, 0.1, 2.0), (5.0, 1e4, 0.3)])
+def test_hartmann_different_walls_steady_profiles(closure, ha, cl, cu):
+    """Body-force Hartmann flow with a different conductance ratio on each plate, compared with
+    the two-wall closed form."""
+    a = 32.5 if closure == oracle.LINK else 32.0
+    b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+    fx = an.force_for_centre_speed(0.01, ha, 0.5 * (cl + cu) if cl < 1e3 else cu, a, 0.8)
+    o = oracle.Oracle(3, 65, 0.8, 0.8, b0, fx, closure, cl, cu)
+    r = o.run_to_steady(1e-9, 200, 400_000)
+    assert r < 1e-9
+    u, b = o.profiles()
+    ua, ba = an.hartmann_walls_profiles(o.y(), a, ha, cl, cu, fx, 0.8, 0.8)
+    assert an.rel_l2(u, ua) < _tol(ha)
+    assert an.rel_l2(b, ba) < _tol(ha)
+
+
+@pytest.mark.parametrize("closure", [oracle.LINK, oracle.MOMENT])
 @pytest.mark.parametrize("ha,cl,cu", [(5.0, 0.0, 0.0), (5.0, 0.5, 0.5), (5.0, 0.5, 0.0), (20.0, 0.5, 0.0),
                                       (5.0, 0.0, 1e4)])
 def test_couette_steady_profiles(closure, ha, cl, cu):

@@ -30,6 +30,19 @@ def test_couette_agrees(ha, cl, cu):
     np.testing.assert_allclose(b1, b2, rtol=1e-11, atol=1e-15)
 
 
+@pytest.mark.parametrize("ha,cl,cu", [(5.0, 0.0, 0.5), (20.0, 0.1, 2.0), (3.0, math.inf, 0.3), (7.0, 0.5, math.inf),
+                                      (10.0, 0.4, 0.4), (2.0, math.inf, math.inf)])
+def test_hartmann_walls_agrees(ha, cl, cu):
+    y = np.linspace(-32.5, 32.5, 66)
+    u1, b1 = profiles.hartmann_walls(y, 32.5, ha, cl, cu, 1e-5, 0.8, 0.8)
+    u2, b2 = an.hartmann_walls_profiles(y, 32.5, ha, cl, cu, 1e-5, 0.8, 0.8)
+    np.testing.assert_allclose(u1, u2, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(b1, b2, rtol=1e-12, atol=1e-15)
+    fx = profiles.hartmann_walls_force(0.01, ha, cl, cu, 32.5, 0.8)
+    u0, _ = an.hartmann_walls_profiles([0.0], 32.5, ha, cl, cu, fx, 0.8, 0.8)
+    assert u0[0] == pytest.approx(0.01, rel=1e-12)
+
+
 def test_node_coordinates():
     a, y = profiles.node_y(65, "link")
     assert a == 32.5 and y[0] == -32.0 and y[-1] == 32.0
