@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lks_oracle.c")
+_SRC3 = os.path.join(_HERE, "lks3d_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 _lib = None
@@ -44,14 +45,32 @@ class OracleParams(ctypes.Structure):
     ]
 
 
+class Oracle3DParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32),
+        ("ny", ctypes.c_int32),
+        ("nz", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("tau_f", ctypes.c_double),
+        ("tau_m", ctypes.c_double),
+        ("B0", ctypes.c_double),
+        ("Fx", ctypes.c_double),
+        ("c_bot", ctypes.c_double),
+        ("c_top", ctypes.c_double),
+        ("u_bot", ctypes.c_double),
+        ("u_top", ctypes.c_double),
+    ]
+
+
 def build(force=False):
     """Compile the oracle shared library (gcc -O2 -ffp-contract=off -fopenmp)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+    if not force and os.path.exists(_LIB_PATH) and all(
+            os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src) for src in (_SRC, _SRC3)):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
-           "-std=c11", "-o", tmp, _SRC, "-lm"]
+           "-std=c11", "-o", tmp, _SRC, _SRC3, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -78,6 +97,15 @@ def lib():
         L.orc_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = None
+        p3 = ctypes.POINTER(Oracle3DParams)
+        L.o3_init.argtypes = [p3, dp, dp]
+        L.o3_init.restype = ctypes.c_int
+        L.o3_step.argtypes = [p3, dp, dp, dp, dp]
+        L.o3_step.restype = ctypes.c_int
+        L.o3_run.argtypes = [p3, dp, dp, ctypes.c_int64]
+        L.o3_run.restype = ctypes.c_int
+        L.o3_moments.argtypes = [p3, dp, dp, dp]
+        L.o3_moments.restype = None
         _lib = L
     return _lib
 
@@ -185,3 +213,63 @@ def set_threads(n):
 
 def threads_used():
     return lib().orc_threads()
+
+
+class Oracle3D:
+    """Three-dimensional channel (D3Q19 f + D3Q7 g per component of B, link-based walls at the
+    y planes, periodic in x and z) advanced by the FP64 reference scheme of lks3d_oracle.c.
+
+    State arrays: f (19, nz, ny, nx) and g (3, 7, nz, ny, nx), post-collision populations; they
+    may be set directly (e.g. to a perturbed state) before stepping.
+    """
+
+    def __init__(self, nx, ny, nz, tau_f, tau_m, B0, Fx=0.0, c_bot=0.0, c_top=0.0, u_bot=0.0, u_top=0.0):
+        self.p = Oracle3DParams(nx=nx, ny=ny, nz=nz, pad=0, tau_f=tau_f, tau_m=tau_m, B0=B0, Fx=Fx, c_bot=c_bot,
+                                c_top=c_top, u_bot=u_bot, u_top=u_top)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.f = np.zeros((19, nz, ny, nx))
+        self.g = np.zeros((3, 7, nz, ny, nx))
+        if lib().o3_init(ctypes.byref(self.p), _ptr(self.f), _ptr(self.g)) != 0:
+            raise ValueError("oracle init rejected the parameters")
+        self.steps = 0
+
+    @property
+    def a(self):
+        return 0.5 * self.ny
+
+    def y(self):
+        """Wall-normal node coordinates y_j = -a + j + 1/2."""
+        return -self.a + np.arange(self.ny, dtype=np.float64) + 0.5
+
+    def step(self, n=1):
+        if lib().o3_run(ctypes.byref(self.p), _ptr(self.f), _ptr(self.g), int(n)) != 0:
+            raise RuntimeError("oracle step failed")
+        self.steps += n
+
+    def moments(self):
+        """(7, nz, ny, nx): rho, u_x, u_y, u_z, B_x, B_y, B_z of the stored state."""
+        mom = np.empty((7, self.nz, self.ny, self.nx))
+        lib().o3_moments(ctypes.byref(self.p), _ptr(self.f), _ptr(self.g), _ptr(mom))
+        return mom
+
+    def profiles(self):
+        """u_x(y), B_x(y) averaged over x and z."""
+        m = self.moments()
+        return m[1].mean(axis=(0, 2)), m[4].mean(axis=(0, 2))
+
+    def run_to_steady(self, tol=1e-10, check_every=100, max_steps=10_000_000):
+        """Step until the relative change of u_x and B_x over check_every steps is below tol."""
+        prev = self.moments()
+        r = float("inf")
+        while self.steps < max_steps:
+            self.step(check_every)
+            cur = self.moments()
+            r = 0.0
+            for m in (1, 4):
+                den = float(np.sqrt(np.sum(cur[m] ** 2)))
+                if den > 1e-30:
+                    r = max(r, float(np.sqrt(np.sum((cur[m] - prev[m]) ** 2))) / den)
+            prev = cur
+            if r < tol:
+                return r
+        return r
