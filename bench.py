@@ -370,6 +370,24 @@ def bench_ours(args):
                 extra[key]["footprint_bytes"] = lr.nbytes
             lr.close()
             del lr
+        # three-dimensional channel (D3Q19 + 3 x D3Q7, link-based walls), FP32, 256^3
+        from paper_2112_13930_gb300 import lks3d
+        n3 = 256
+        l3 = lks3d.Lattice3D(n3, n3, n3, phys["tau_f"], phys["tau_m"], 20.0 * 0.1 / (n3 / 2), 0.0, "f32")
+        l3.set_walls(phys["c"], phys["c"], 0.0, phys["u_w"])
+        l3.step(3)
+        barrier()
+        k3 = max(10, min(args.steps, 200))
+        t3 = max_over_ranks(_time_steps(l3, k3, stream))
+        nodes3 = n3 ** 3
+        v3 = nodes3 * k3 * ws / t3 / 1e6
+        a3 = 320 * nodes3 / (t3 / k3) / 1e9
+        extra["d3q19_f32"] = {"value": round(v3, 1), "unit": UNIT, "steps": k3,
+                              "config": "256^3, Hartmann-Couette, link-based walls c = 1, U_w = 0.05",
+                              "roofline": {"bound": "hbm", "achieved": round(a3, 1), "peak": peak, "unit": "GB/s",
+                                           "frac": round(a3 / peak, 4), "bytes_per_node": 320}}
+        l3.close()
+        del l3
         torch.cuda.empty_cache()
 
     cpu = None

@@ -1,0 +1,745 @@
+// lks3d.cu -- the three-dimensional channel (include/lks3d.h): fused D3Q19 + 3 x D3Q7 collide-
+// stream kernel with the link-based Shercliff walls, moments, residual, state conversion and the
+// lks3_* C ABI.
+//
+// One thread per node, x fastest (grid: x blocks, y, z), pull scheme: every population of the
+// source buffer is read by exactly one node per step, so a step moves 40 values in and 40 out per
+// node (320 B in FP32).  Stored values are deviations from the rest equilibrium; the arithmetic
+// below is the oracle's (absolute populations) rewritten for deviations:
+//   d_a = f_a - f_rest_a,  f_rest_a = w_a + M_a(0, B0, 0),
+//   rho = 1 + sum d,  rho u = sum d e + F/2,  B = (sum dg_x, B0 + sum dg_y, sum dg_z),
+//   f'_a - f_rest_a = (1 - w) d_a + w [w_a (drho + rho bm1_a) + M_a(B) - M_a(B_rest)]
+//                     + (1 - w/2) 3 (e_ax - u_x) F_x w_a (1 + bm1_a),
+//   bm1_a = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2,
+//   M_a(B) - M_a(B_rest) = 4.5 w_a [ |e|^2 q / 2 - (e.B - e_y B0)(e.B + e_y B0) - q / 6 ],
+//   q = |B|^2 - B0^2 = B_x^2 + B_z^2 + dB_y (2 B0 + dB_y),
+//   g'_ai - g_rest_ai = (1 - w_m) dg_ai + w_m W_a (B_i - B_rest_i + 4 e_a.(u B_i - B u_i)).
+// Rest populations of opposite directions are equal, so the bounce-back closures carry over to
+// deviations unchanged, and the normal-component anti-bounce-back becomes dg_in = -dg_out.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "../../include/lks3d.h"
+#include "lks_device.cuh"
+
+using lks::load_s;
+using lks::store_s;
+
+namespace {
+
+thread_local std::string g3_last_error = "";
+constexpr size_t kAlign3 = 256;
+constexpr int kRedBlocks = 1024;  // residual partial sums (fixed, so the reduction order is fixed)
+
+inline size_t align3(size_t x) { return (x + kAlign3 - 1) & ~(kAlign3 - 1); }
+
+// D3Q19 velocity components (order of lks3d.h) as constant expressions, so that unrolled loops
+// over the directions fold them; D3Q7 is the first seven directions.
+__host__ __device__ constexpr int EXa(int a) {
+    return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1 : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int EYa(int a) {
+    return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1 : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int EZa(int a) {
+    return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1 : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0;
+}
+__host__ __device__ inline double w19(int a) { return a == 0 ? 1.0 / 3.0 : (a <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+__host__ __device__ inline double w7(int a) { return a == 0 ? 0.25 : 0.125; }
+__host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+
+// Rest deviation offsets in FP64 (host side; passed to the conversion kernels).
+double f_rest(int a, double B0) {
+    const double e2 = EXa(a) * EXa(a) + EYa(a) * EYa(a) + EZa(a) * EZa(a);
+    const double eB = EYa(a) * B0;
+    return w19(a) + 4.5 * w19(a) * (0.5 * B0 * B0 * e2 - eB * eB - B0 * B0 / 6.0);
+}
+
+template <typename C>
+struct Wall3 {
+    C r, kx, du;  // tangential-component ratio, B_x moving-wall term, Ladd term for the diagonals
+};
+
+template <typename C>
+struct Params3 {
+    int32_t nx, ny, nz;
+    int64_t N;
+    C om_f, om1f, om_m, om1m, src;  // 1/tau_f, 1 - 1/tau_f, 1/tau_m, 1 - 1/tau_m, 1 - 1/(2 tau_f)
+    C B0, Fx;
+    Wall3<C> bot, top;
+};
+
+template <typename C>
+Params3<C> make_params3(const lks3_params& p, double c_bot, double c_top, double u_bot, double u_top) {
+    Params3<C> q;
+    q.nx = p.nx;
+    q.ny = p.ny;
+    q.nz = p.nz;
+    q.N = (int64_t)p.nx * p.ny * p.nz;
+    q.om_f = (C)(1.0 / p.tau_f);
+    q.om1f = (C)(1.0 - 1.0 / p.tau_f);
+    q.om_m = (C)(1.0 / p.tau_m);
+    q.om1m = (C)(1.0 - 1.0 / p.tau_m);
+    q.src = (C)(1.0 - 0.5 / p.tau_f);
+    q.B0 = (C)p.B0;
+    q.Fx = (C)p.Fx;
+    const double a = 0.5 * p.ny;
+    auto wall = [&](double c, double U, double ey) {
+        Wall3<C> w;
+        double r, k;
+        if (isinf(c)) {
+            r = 1.0;
+            k = 1.0;
+        } else {
+            const double th = c * a / (p.tau_m - 0.5);  // Eq. weightingfactor
+            r = (th - 1.0) / (th + 1.0);
+            k = th / (th + 1.0);
+        }
+        w.r = (C)r;
+        // -(2 theta/(theta+1)) W e_y B0 U / c_sm^2 with W = 1/8, c_sm^2 = 1/4 (App. B.1)
+        w.kx = (C)(-k * ey * p.B0 * U);
+        w.du = (C)(6.0 * (1.0 / 36.0) * U);
+        return w;
+    };
+    q.bot = wall(c_bot, u_bot, +1.0);
+    q.top = wall(c_top, u_top, -1.0);
+    return q;
+}
+
+// The fused step of one node.  S: storage type, C: compute type.
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
+                                                    S* __restrict__ fout, S* __restrict__ gout, const Params3<C> p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.nx) return;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int64_t N = p.N;
+    const int64_t n = ((int64_t)z * ny + y) * nx + x;
+    const bool bottom = (y == 0), top = (y == ny - 1);
+    const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};  // source x for e_x = +1, 0, -1
+    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+    // source index of a pull along e: (x - e_x, y - e_y, z - e_z)
+    auto src = [&](int ex, int ey, int ez) -> int64_t {
+        return ((int64_t)zs[1 - ez] * ny + (y - ey)) * nx + xs[1 - ex];
+    };
+    auto ld = [](const S* ptr) -> C { return load_s<S, C>(ptr); };
+
+    C f[19], gx[7], gy[7], gz[7];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        const int ey = EYa(a);
+        if ((ey == 1 && bottom) || (ey == -1 && top)) continue;  // closed below
+        f[a] = ld(fin + a * N + src(EXa(a), ey, EZa(a)));
+    }
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+        const int ey = EYa(a);
+        if ((ey == 1 && bottom) || (ey == -1 && top)) continue;
+        const int64_t s = src(EXa(a), ey, EZa(a));
+        gx[a] = ld(gin + a * N + s);
+        gy[a] = ld(gin + (7 + a) * N + s);
+        gz[a] = ld(gin + (14 + a) * N + s);
+    }
+    // link-based walls: the node's own outgoing populations, bounced back
+    if (bottom) {  // incoming e_y = +1: 3, 7, 10, 15, 17 (D3Q19); 3 (D3Q7)
+        const Wall3<C>& w = p.bot;
+        f[3] = ld(fin + 4 * N + n);
+        f[7] = ld(fin + 8 * N + n) + w.du;
+        f[10] = ld(fin + 9 * N + n) - w.du;
+        f[15] = ld(fin + 16 * N + n);
+        f[17] = ld(fin + 18 * N + n);
+        gx[3] = w.r * ld(gin + 4 * N + n) + w.kx;
+        gy[3] = -ld(gin + (7 + 4) * N + n);
+        gz[3] = w.r * ld(gin + (14 + 4) * N + n);
+    }
+    if (top) {  // incoming e_y = -1: 4, 8, 9, 16, 18; 4
+        const Wall3<C>& w = p.top;
+        f[4] = ld(fin + 3 * N + n);
+        f[8] = ld(fin + 7 * N + n) - w.du;
+        f[9] = ld(fin + 10 * N + n) + w.du;
+        f[16] = ld(fin + 15 * N + n);
+        f[18] = ld(fin + 17 * N + n);
+        gx[4] = w.r * ld(gin + 3 * N + n) + w.kx;
+        gy[4] = -ld(gin + (7 + 3) * N + n);
+        gz[4] = w.r * ld(gin + (14 + 3) * N + n);
+    }
+    // moments (a3)
+    C drho = C(0), jx = C(0), jy = C(0), jz = C(0);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        drho += f[a];
+        if (EXa(a) == 1) jx += f[a];
+        if (EXa(a) == -1) jx -= f[a];
+        if (EYa(a) == 1) jy += f[a];
+        if (EYa(a) == -1) jy -= f[a];
+        if (EZa(a) == 1) jz += f[a];
+        if (EZa(a) == -1) jz -= f[a];
+    }
+    const C rho = C(1) + drho;
+    const C inv = lks::recip(rho);
+    const C ux = (jx + C(0.5) * p.Fx) * inv, uy = jy * inv, uz = jz * inv;
+    C bx = C(0), dby = C(0), bz = C(0);
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+        bx += gx[a];
+        dby += gy[a];
+        bz += gz[a];
+    }
+    const C B0 = p.B0, by = B0 + dby;
+    // equilibria, source and collision of f (a4-a5)
+    const C q = bx * bx + bz * bz + dby * (C(2) * B0 + dby);  // |B|^2 - B0^2
+    const C usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        const int ex = EXa(a), ey = EYa(a), ez = EZa(a);
+        const C w = (C)w19(a);
+        const C e2 = (C)(ex * ex + ey * ey + ez * ez);
+        const C eu = (C)ex * ux + (C)ey * uy + (C)ez * uz;
+        const C eBm = (C)ex * bx + (C)ey * dby + (C)ez * bz;  // e.B - e_y B0
+        const C eBp = eBm + (C)(2 * ey) * B0;                 // e.B + e_y B0
+        const C bm1 = (C(3) + C(4.5) * eu) * eu - C(1.5) * usq;
+        const C mag = C(4.5) * w * (C(0.5) * e2 * q - eBm * eBp - q * C(1.0 / 6.0));
+        const C feq = w * (drho + rho * bm1) + mag;
+        const C sa = p.src * C(3) * ((C)ex - ux) * p.Fx * w * (C(1) + bm1);
+        store_s<S, C>(fout + a * N + n, p.om1f * f[a] + p.om_f * feq + sa);
+    }
+    // g, per component i: g' = (1 - w_m) dg + w_m W (dB_i +- 4 E_di), E_di = u_d B_i - B_d u_i
+    const C W0 = C(0.25), W1 = C(0.125), om = p.om_m, o1 = p.om1m;
+    auto comp = [&](C* g, C dBi, C Bi, C ui, S* out) {
+        const C Ex = ux * Bi - bx * ui, Ey = uy * Bi - by * ui, Ez = uz * Bi - bz * ui;
+        store_s<S, C>(out + 0 * N + n, o1 * g[0] + om * W0 * dBi);
+        store_s<S, C>(out + 1 * N + n, o1 * g[1] + om * W1 * (dBi + C(4) * Ex));
+        store_s<S, C>(out + 2 * N + n, o1 * g[2] + om * W1 * (dBi - C(4) * Ex));
+        store_s<S, C>(out + 3 * N + n, o1 * g[3] + om * W1 * (dBi + C(4) * Ey));
+        store_s<S, C>(out + 4 * N + n, o1 * g[4] + om * W1 * (dBi - C(4) * Ey));
+        store_s<S, C>(out + 5 * N + n, o1 * g[5] + om * W1 * (dBi + C(4) * Ez));
+        store_s<S, C>(out + 6 * N + n, o1 * g[6] + om * W1 * (dBi - C(4) * Ez));
+    };
+    comp(gx, bx, bx, ux, gout);
+    comp(gy, dby, by, uy, gout + 7 * N);
+    comp(gz, bz, bz, uz, gout + 14 * N);
+}
+
+
+// FP64 moments of the stored state of node n: rho = 1 + sum d, rho u = sum d e - F/2, B.
+template <typename S>
+__device__ void node_moments3(const S* f, const S* g, int64_t N, int64_t n, double B0, double Fx, double m[7]) {
+    double drho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        const double v = (double)load_s<S, float>(f + a * N + n);
+        drho += v;
+        jx += EXa(a) * v;
+        jy += EYa(a) * v;
+        jz += EZa(a) * v;
+    }
+    const double rho = 1.0 + drho;
+    m[0] = rho;
+    m[1] = (jx - 0.5 * Fx) / rho;
+    m[2] = jy / rho;
+    m[3] = jz / rho;
+    double b[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < 7; ++a) b[i] += (double)load_s<S, float>(g + (7 * i + a) * N + n);
+    m[4] = b[0];
+    m[5] = B0 + b[1];
+    m[6] = b[2];
+}
+template <>
+__device__ void node_moments3<double>(const double* f, const double* g, int64_t N, int64_t n, double B0, double Fx,
+                                      double m[7]) {
+    double drho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        const double v = f[a * N + n];
+        drho += v;
+        jx += EXa(a) * v;
+        jy += EYa(a) * v;
+        jz += EZa(a) * v;
+    }
+    const double rho = 1.0 + drho;
+    m[0] = rho;
+    m[1] = (jx - 0.5 * Fx) / rho;
+    m[2] = jy / rho;
+    m[3] = jz / rho;
+    double b[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < 7; ++a) b[i] += g[(7 * i + a) * N + n];
+    m[4] = b[0];
+    m[5] = B0 + b[1];
+    m[6] = b[2];
+}
+
+template <typename S>
+__global__ void moments3_kernel(const S* f, const S* g, int64_t N, double B0, double Fx, double* out) {
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        double m[7];
+        node_moments3<S>(f, g, N, n, B0, Fx, m);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) out[k * N + n] = m[k];
+    }
+}
+
+// x-z averages per row y: one block per row, fixed-order block reduction.
+template <typename S>
+__global__ void profiles3_kernel(const S* f, const S* g, int nx, int ny, int nz, double B0, double Fx, double* out) {
+    __shared__ double red[7][256];
+    const int y = blockIdx.x;
+    const int64_t N = (int64_t)nx * ny * nz;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t k = threadIdx.x; k < (int64_t)nx * nz; k += blockDim.x) {
+        const int z = (int)(k / nx), x = (int)(k - (int64_t)z * nx);
+        double m[7];
+        node_moments3<S>(f, g, N, ((int64_t)z * ny + y) * nx + x, B0, Fx, m);
+#pragma unroll
+        for (int c = 0; c < 7; ++c) acc[c] += m[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 7; ++c) red[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+#pragma unroll
+            for (int c = 0; c < 7; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 7; ++c) out[c * ny + y] = red[c][0] / ((double)nx * nz);
+}
+
+// Residual partial sums (du^2, u^2, db^2, b^2 of u_x, B_x against the snapshot), one per block;
+// the snapshot is replaced.  kRedBlocks blocks of 256 threads, fixed order.
+template <typename S>
+__global__ void residual3_partial(const S* f, const S* g, int64_t N, double B0, double Fx, double* snap,
+                                  double* partial) {
+    __shared__ double red[4][256];
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        double m[7];
+        node_moments3<S>(f, g, N, n, B0, Fx, m);
+        const double du = m[1] - snap[n], db = m[4] - snap[N + n];
+        acc[0] += du * du;
+        acc[1] += m[1] * m[1];
+        acc[2] += db * db;
+        acc[3] += m[4] * m[4];
+        snap[n] = m[1];
+        snap[N + n] = m[4];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; ++c) partial[c * gridDim.x + blockIdx.x] = red[c][0];
+}
+
+__global__ void residual3_final(const double* partial, int nb, double* out) {
+    __shared__ double red[4][1024];
+    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = (int)threadIdx.x < nb ? partial[c * nb + threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; ++c) out[c] = red[c][0];
+}
+
+// Absolute FP64 populations <-> stored deviations.  rest_f: 19 FP64 rest values; g rest is
+// W_a B0 for the y component and 0 otherwise.
+template <typename S, typename C>
+__global__ void to_abs3_kernel(const S* f, const S* g, int64_t N, const double* rest_f, double B0, double* of,
+                               double* og) {
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 19; ++a) of[a * N + n] = (double)load_s<S, C>(f + a * N + n) + rest_f[a];
+        for (int k = 0; k < 21; ++k)
+            og[k * N + n] = (double)load_s<S, C>(g + k * N + n) + (k / 7 == 1 ? w7(k % 7) * B0 : 0.0);
+    }
+}
+
+template <typename S, typename C>
+__global__ void from_abs3_kernel(const double* inf, const double* ing, int64_t N, const double* rest_f, double B0,
+                                 S* f, S* g) {
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 19; ++a) store_s<S, C>(f + a * N + n, (C)(inf[a * N + n] - rest_f[a]));
+        for (int k = 0; k < 21; ++k)
+            store_s<S, C>(g + k * N + n, (C)(ing[k * N + n] - (k / 7 == 1 ? w7(k % 7) * B0 : 0.0)));
+    }
+}
+
+}  // namespace
+
+namespace {
+
+const char* validate3(const lks3_params* p) {
+    if (!p) return "params is NULL";
+    if (p->nx < 1 || p->nz < 1) return "nx and nz must be >= 1";
+    if (p->ny < 2) return "ny must be >= 2";
+    if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
+    if ((int64_t)p->nx * p->ny * p->nz > ((int64_t)1 << 30)) return "nx*ny*nz exceeds 2^30 nodes";
+    if (p->storage != LKS_F64 && p->storage != LKS_F32) return "storage must be LKS_F64 or LKS_F32";
+    if (!(p->tau_f > 0.5) || !isfinite(p->tau_f)) return "tau_f must be finite and > 1/2";
+    if (!(p->tau_m > 0.5) || !isfinite(p->tau_m)) return "tau_m must be finite and > 1/2";
+    if (!isfinite(p->B0) || !isfinite(p->Fx)) return "B0 and Fx must be finite";
+    return nullptr;
+}
+
+struct Layout3 {
+    size_t f_bytes, g_bytes, off_f[2], off_g[2], off_snap, off_partial, off_out, off_prof, off_rest, total;
+};
+
+Layout3 layout3(const lks3_params* p) {
+    Layout3 L;
+    const size_t N = (size_t)p->nx * p->ny * p->nz;
+    const size_t sb = p->storage == LKS_F64 ? 8 : 4;
+    L.f_bytes = align3(19 * N * sb);
+    L.g_bytes = align3(21 * N * sb);
+    size_t o = 0;
+    for (int k = 0; k < 2; ++k) {
+        L.off_f[k] = o;
+        o += L.f_bytes;
+        L.off_g[k] = o;
+        o += L.g_bytes;
+    }
+    L.off_snap = o;
+    o += align3(2 * N * sizeof(double));
+    L.off_partial = o;
+    o += align3(4 * kRedBlocks * sizeof(double));
+    L.off_out = o;
+    o += align3(4 * sizeof(double));
+    L.off_prof = o;
+    o += align3(7 * (size_t)p->ny * sizeof(double));
+    L.off_rest = o;
+    o += align3(19 * sizeof(double));
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+struct lks3_handle {
+    lks3_params p;
+    Layout3 L;
+    cudaStream_t stream = nullptr;
+    char* base = nullptr;
+    bool owns = false;
+    void* f[2] = {nullptr, nullptr};
+    void* g[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *snap = nullptr, *partial = nullptr, *dout = nullptr, *prof = nullptr, *rest = nullptr;
+    double* host4 = nullptr;  // pinned
+    double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
+    int64_t steps = 0;
+    std::string err;
+};
+
+namespace {
+
+lks_status fail3(lks3_handle* h, lks_status s, const std::string& m) {
+    if (h)
+        h->err = m;
+    else
+        g3_last_error = m;
+    return s;
+}
+
+lks_status cuda3(lks3_handle* h, cudaError_t e, const char* where) {
+    return fail3(h, LKS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+unsigned grid_for(int64_t N) { return (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 16); }
+
+cudaError_t launch_step3(lks3_handle* h) {
+    const lks3_params& p = h->p;
+    const dim3 grid((p.nx + 255) / 256, p.ny, p.nz);
+    const int src = h->cur;
+    if (p.storage == LKS_F64) {
+        const Params3<double> q = make_params3<double>(p, h->c_bot, h->c_top, h->u_bot, h->u_top);
+        step3_kernel<double, double><<<grid, 256, 0, h->stream>>>((const double*)h->f[src], (const double*)h->g[src],
+                                                                  (double*)h->f[src ^ 1], (double*)h->g[src ^ 1], q);
+    } else {
+        const Params3<float> q = make_params3<float>(p, h->c_bot, h->c_top, h->u_bot, h->u_top);
+        step3_kernel<float, float><<<grid, 256, 0, h->stream>>>((const float*)h->f[src], (const float*)h->g[src],
+                                                                (float*)h->f[src ^ 1], (float*)h->g[src ^ 1], q);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot3(lks3_handle* h) {
+    const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
+    if (h->p.storage == LKS_F64)
+        residual3_partial<double><<<kRedBlocks, 256, 0, h->stream>>>((const double*)h->f[h->cur],
+                                                                     (const double*)h->g[h->cur], N, h->p.B0, h->p.Fx,
+                                                                     h->snap, h->partial);
+    else
+        residual3_partial<float><<<kRedBlocks, 256, 0, h->stream>>>((const float*)h->f[h->cur],
+                                                                    (const float*)h->g[h->cur], N, h->p.B0, h->p.Fx,
+                                                                    h->snap, h->partial);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lks3_footprint_bytes(const lks3_params* p) {
+    if (validate3(p)) return 0;
+    return layout3(p).total;
+}
+
+lks_status lks3_create(const lks3_params* p, lks3_handle** out) {
+    if (!out) return fail3(nullptr, LKS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (const char* m = validate3(p)) return fail3(nullptr, LKS_EINVAL, m);
+    lks3_handle* h = new (std::nothrow) lks3_handle();
+    if (!h) return fail3(nullptr, LKS_ENOMEM, "host allocation of the handle failed");
+    h->p = *p;
+    h->L = layout3(p);
+    h->stream = (cudaStream_t)p->cuda_stream;
+    cudaError_t e;
+    if (p->dev_buffer) {
+        if (p->dev_buffer_bytes < h->L.total || ((uintptr_t)p->dev_buffer % kAlign3) != 0) {
+            delete h;
+            return fail3(nullptr, LKS_ENOMEM, "dev_buffer is smaller than lks3_footprint_bytes() or not 256-byte aligned");
+        }
+        h->base = (char*)p->dev_buffer;
+    } else {
+        e = cudaMalloc((void**)&h->base, h->L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail3(nullptr, LKS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        h->owns = true;
+    }
+    for (int k = 0; k < 2; ++k) {
+        h->f[k] = h->base + h->L.off_f[k];
+        h->g[k] = h->base + h->L.off_g[k];
+    }
+    h->snap = (double*)(h->base + h->L.off_snap);
+    h->partial = (double*)(h->base + h->L.off_partial);
+    h->dout = (double*)(h->base + h->L.off_out);
+    h->prof = (double*)(h->base + h->L.off_prof);
+    h->rest = (double*)(h->base + h->L.off_rest);
+    double rest[19];
+    for (int a = 0; a < 19; ++a) rest[a] = f_rest(a, p->B0);
+    e = cudaHostAlloc((void**)&h->host4, 4 * sizeof(double), cudaHostAllocDefault);
+    // rest state: all deviations zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, h->L.f_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->g[0], 0, h->L.g_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->rest, rest, sizeof(rest), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_snapshot3(h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // rest[] is on this stack frame
+    if (e != cudaSuccess) {
+        lks3_destroy(h);
+        return cuda3(nullptr, e, "lks3_create");
+    }
+    *out = h;
+    return LKS_OK;
+}
+
+lks_status lks3_set_walls(lks3_handle* h, double c_bottom, double c_top, double u_bottom, double u_top) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!(c_bottom >= 0.0) || !(c_top >= 0.0)) return fail3(h, LKS_EINVAL, "wall conductance ratios must be >= 0");
+    if (!(fabs(u_bottom) < 0.3) || !(fabs(u_top) < 0.3)) return fail3(h, LKS_EINVAL, "|wall speed| must be < 0.3");
+    h->c_bot = c_bottom;
+    h->c_top = c_top;
+    h->u_bot = u_bottom;
+    h->u_top = u_top;
+    return LKS_OK;
+}
+
+lks_status lks3_step(lks3_handle* h, int64_t n) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    if (n < 0) return fail3(h, LKS_EINVAL, "n must be >= 0");
+    for (int64_t k = 0; k < n; ++k) {
+        cudaError_t e = launch_step3(h);
+        if (e != cudaSuccess) return cuda3(h, e, "3D step kernel launch");
+        h->cur ^= 1;
+        h->steps += 1;
+    }
+    return LKS_OK;
+}
+
+int64_t lks3_steps_taken(const lks3_handle* h) { return h ? h->steps : -1; }
+
+lks_status lks3_moments(lks3_handle* h, int what, double* host_out) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!host_out) return fail3(h, LKS_EINVAL, "host_out is NULL");
+    const lks3_params& p = h->p;
+    const int64_t N = (int64_t)p.nx * p.ny * p.nz;
+    cudaError_t e;
+    if (what == LKS_MOMENTS_PROFILES) {
+        if (p.storage == LKS_F64)
+            profiles3_kernel<double><<<p.ny, 256, 0, h->stream>>>((const double*)h->f[h->cur],
+                                                                  (const double*)h->g[h->cur], p.nx, p.ny, p.nz, p.B0,
+                                                                  p.Fx, h->prof);
+        else
+            profiles3_kernel<float><<<p.ny, 256, 0, h->stream>>>((const float*)h->f[h->cur],
+                                                                 (const float*)h->g[h->cur], p.nx, p.ny, p.nz, p.B0,
+                                                                 p.Fx, h->prof);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_out, h->prof, 7 * (size_t)p.ny * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    } else if (what == LKS_MOMENTS_NODES) {
+        double* tmp = nullptr;
+        e = cudaMalloc((void**)&tmp, 7 * (size_t)N * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail3(h, LKS_ENOMEM, "cudaMalloc of the moment staging buffer failed");
+        }
+        if (p.storage == LKS_F64)
+            moments3_kernel<double><<<grid_for(N), 256, 0, h->stream>>>((const double*)h->f[h->cur],
+                                                                        (const double*)h->g[h->cur], N, p.B0, p.Fx, tmp);
+        else
+            moments3_kernel<float><<<grid_for(N), 256, 0, h->stream>>>((const float*)h->f[h->cur],
+                                                                       (const float*)h->g[h->cur], N, p.B0, p.Fx, tmp);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_out, tmp, 7 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(tmp);
+    } else {
+        return fail3(h, LKS_EINVAL, "bad 'what'");
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda3(h, e, "lks3_moments");
+    return LKS_OK;
+}
+
+lks_status lks3_residual(lks3_handle* h, double* r_u, double* r_b) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    cudaError_t e = launch_snapshot3(h);
+    if (e == cudaSuccess) {
+        residual3_final<<<1, 1024, 0, h->stream>>>(h->partial, kRedBlocks, h->dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->host4, h->dout, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda3(h, e, "lks3_residual");
+    const double* s = h->host4;
+    const double ru = s[1] > 1e-30 * 1e-30 ? sqrt(s[0] / s[1]) : 0.0;
+    const double rb = s[3] > 1e-30 * 1e-30 ? sqrt(s[2] / s[3]) : 0.0;
+    if (r_u) *r_u = ru;
+    if (r_b) *r_b = rb;
+    if (!isfinite(s[0]) || !isfinite(s[1]) || !isfinite(s[2]) || !isfinite(s[3]))
+        return fail3(h, LKS_EUNSTABLE, "non-finite state");
+    return LKS_OK;
+}
+
+lks_status lks3_run_to_steady(lks3_handle* h, double tol, int64_t check_every, int64_t max_steps, int64_t* steps_out,
+                              double* r_out) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    if (check_every < 1 || max_steps < 0 || !(tol > 0.0)) return fail3(h, LKS_EINVAL, "bad run_to_steady arguments");
+    int64_t taken = 0;
+    double r = INFINITY;
+    lks_status s = LKS_OK;
+    while (taken < max_steps) {
+        const int64_t n = (max_steps - taken < check_every) ? max_steps - taken : check_every;
+        s = lks3_step(h, n);
+        if (s != LKS_OK) break;
+        taken += n;
+        double ru, rb;
+        s = lks3_residual(h, &ru, &rb);
+        if (s != LKS_OK) break;
+        r = ru > rb ? ru : rb;
+        if (r < tol) break;
+    }
+    if (steps_out) *steps_out = taken;
+    if (r_out) *r_out = r;
+    if (s != LKS_OK) return s;
+    if (!(r < tol)) return fail3(h, LKS_ENOTCONVERGED, "max_steps reached before the residual tolerance");
+    return LKS_OK;
+}
+
+lks_status lks3_get_state(lks3_handle* h, double* host_f, double* host_g) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!host_f || !host_g) return fail3(h, LKS_EINVAL, "host_f/host_g is NULL");
+    const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc((void**)&tmp, 40 * (size_t)N * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail3(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
+    }
+    if (h->p.storage == LKS_F64)
+        to_abs3_kernel<double, double><<<grid_for(N), 256, 0, h->stream>>>(
+            (const double*)h->f[h->cur], (const double*)h->g[h->cur], N, h->rest, h->p.B0, tmp, tmp + 19 * N);
+    else
+        to_abs3_kernel<float, float><<<grid_for(N), 256, 0, h->stream>>>(
+            (const float*)h->f[h->cur], (const float*)h->g[h->cur], N, h->rest, h->p.B0, tmp, tmp + 19 * N);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, 19 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_g, tmp + 19 * N, 21 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda3(h, e, "lks3_get_state");
+    return LKS_OK;
+}
+
+lks_status lks3_set_state(lks3_handle* h, const double* host_f, const double* host_g) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!host_f || !host_g) return fail3(h, LKS_EINVAL, "host_f/host_g is NULL");
+    const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
+    double* tmp = nullptr;
+    cudaError_t e = cudaMalloc((void**)&tmp, 40 * (size_t)N * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail3(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
+    }
+    e = cudaMemcpyAsync(tmp, host_f, 19 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tmp + 19 * N, host_g, 21 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        if (h->p.storage == LKS_F64)
+            from_abs3_kernel<double, double><<<grid_for(N), 256, 0, h->stream>>>(
+                tmp, tmp + 19 * N, N, h->rest, h->p.B0, (double*)h->f[h->cur], (double*)h->g[h->cur]);
+        else
+            from_abs3_kernel<float, float><<<grid_for(N), 256, 0, h->stream>>>(
+                tmp, tmp + 19 * N, N, h->rest, h->p.B0, (float*)h->f[h->cur], (float*)h->g[h->cur]);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_snapshot3(h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda3(h, e, "lks3_set_state");
+    h->steps = 0;
+    return LKS_OK;
+}
+
+lks_status lks3_sync(lks3_handle* h) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda3(h, e, "lks3_sync");
+    return LKS_OK;
+}
+
+lks_status lks3_destroy(lks3_handle* h) {
+    if (!h) return LKS_OK;
+    if (h->stream || h->base) cudaStreamSynchronize(h->stream);
+    if (h->owns && h->base) cudaFree(h->base);
+    if (h->host4) cudaFreeHost(h->host4);
+    delete h;
+    return LKS_OK;
+}
+
+const char* lks3_last_error(const lks3_handle* h) { return h ? h->err.c_str() : g3_last_error.c_str(); }
+
+}  // extern "C"

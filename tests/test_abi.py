@@ -147,3 +147,39 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
             mod.load(str(tmp_path / "missing.so"))
         finally:
             mod._lib = saved
+
+
+def test_every_3d_symbol_is_exported(lib):
+    from paper_2112_13930_gb300 import lks3d
+    text = open(os.path.join(ROOT, "include", "lks3d.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = sorted(set(re.findall(r"\b(lks3_[a-z0-9_]+)\s*\(", text)))
+    assert "lks3_create" in names and "lks3_step" in names and "lks3_run_to_steady" in names
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in lks3d.SIGNATURES, "binding lacks " + n
+
+
+@pytest.mark.parametrize("kw,ok", [
+    (dict(nx=4, ny=2, nz=1), True),
+    (dict(nx=4, ny=1, nz=1), False),
+    (dict(nx=0, ny=8, nz=4), False),
+    (dict(nx=4, ny=8, nz=0), False),
+    (dict(nx=4, ny=8, nz=4, storage="bf16"), False),
+    (dict(nx=4, ny=8, nz=4, tau_m=0.5), False),
+    (dict(nx=1024, ny=1024, nz=1025), False),       # above 2^30 nodes
+])
+def test_3d_parameter_validation(lib, kw, ok):
+    from paper_2112_13930_gb300 import lks3d
+    p = lks3d.make_params(kw["nx"], kw["ny"], kw["nz"], 0.8, kw.get("tau_m", 0.8), 0.01,
+                          storage=kw.get("storage", "f64"))
+    assert (lib.lks3_footprint_bytes(ctypes.byref(p)) > 0) == ok
+
+
+def test_3d_footprint_counts_both_buffers(lib):
+    from paper_2112_13930_gb300 import lks3d
+    n = 256 ** 3
+    for storage, sb in (("f64", 8), ("f32", 4)):
+        fp = lks3d.footprint_bytes(256, 256, 256, storage)
+        pops = 2 * 40 * n * sb
+        assert pops + 2 * n * 8 <= fp < pops + 2 * n * 8 + (1 << 20)

@@ -1,0 +1,121 @@
+"""Three-dimensional channel on the GPU (include/lks3d.h) against the 3D FP64 oracle.
+
+FP64 storage: moments per field within 1e-11 of max|field| and populations within 1e-11 of the
+largest deviation from rest, after 1 and after 40 steps from the same perturbed state, on lattices
+with a ragged x block (300 = 256 + 44), nx = 1, ny = 2 (both rows are wall rows) and every wall
+setting (insulating, finite, perfectly conducting, moving).  FP32 storage: within 1e-4 of the field
+scale after 40 steps (FP32 rounding of deviations ~1e-3 over a few tens of steps).  Steady state:
+closed-form Hartmann profiles with the D3Q7 diffusivity."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analytic as an
+
+pytestmark = pytest.mark.gpu
+
+REL64 = 1e-11
+
+
+@pytest.fixture(scope="module")
+def l3():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_13930_gb300 import build, lks, lks3d
+    build.build()
+    lks.load()
+    return lks3d
+
+
+CASES = [
+    # nx, ny, nz, (c_bot, c_top), (u_bot, u_top)
+    (37, 9, 5, (0.3, math.inf), (0.0, 0.05)),
+    (300, 6, 3, (0.0, 2.0), (-0.02, 0.04)),
+    (1, 12, 1, (1e4, 0.1), (0.03, 0.0)),
+    (4, 2, 7, (0.5, 0.5), (0.0, -0.03)),
+]
+
+
+def _pair(l3, nx, ny, nz, c, u, storage, seed=0):
+    B0, Fx = 0.02, 2e-6
+    o = oracle.Oracle3D(nx, ny, nz, 0.8, 0.7, B0, Fx, c[0], c[1], u[0], u[1])
+    f_rest, g_rest = o.f.copy(), o.g.copy()
+    rng = np.random.default_rng(seed)
+    o.f += 1e-3 * rng.uniform(-1, 1, o.f.shape) * np.abs(o.f)
+    o.g += 1e-5 * rng.uniform(-1, 1, o.g.shape)
+    gpu = l3.Lattice3D(nx, ny, nz, 0.8, 0.7, B0, Fx, storage)
+    gpu.set_walls(c[0], c[1], u[0], u[1])
+    gpu.set_state(o.f, o.g)
+    return o, gpu, f_rest, g_rest
+
+
+def _fields_close(mo, mg, rel):
+    u_scale = float(np.max(np.abs(mo[1:4])))
+    b_scale = max(float(np.max(np.abs(mo[4]))), float(np.max(np.abs(mo[6]))))
+    by_scale = float(np.max(np.abs(mo[5] - np.mean(mo[5]))) + 1e-300)
+    assert np.max(np.abs(mg[0] - mo[0])) <= rel * np.max(np.abs(mo[0]))
+    assert np.max(np.abs(mg[1:4] - mo[1:4])) <= rel * u_scale
+    assert np.max(np.abs(mg[[4, 6]] - mo[[4, 6]])) <= rel * b_scale
+    assert np.max(np.abs(mg[5] - mo[5])) <= rel * max(by_scale, b_scale)
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_fp64_matches_oracle(l3, case):
+    nx, ny, nz, c, u = case
+    o, gpu, f_rest, g_rest = _pair(l3, nx, ny, nz, c, u, "f64")
+    for n in (1, 39):
+        o.step(n)
+        gpu.step(n)
+        fg, gg = gpu.get_state()
+        df = float(np.max(np.abs(o.f - f_rest)))
+        dg = float(np.max(np.abs(o.g - g_rest)))
+        assert np.max(np.abs(fg - o.f)) <= REL64 * df
+        assert np.max(np.abs(gg - o.g)) <= REL64 * dg
+        _fields_close(o.moments(), gpu.moments(), REL64)
+    gpu.close()
+
+
+@pytest.mark.parametrize("case", CASES[:2])
+def test_fp32_close_to_oracle(l3, case):
+    nx, ny, nz, c, u = case
+    o, gpu, _, _ = _pair(l3, nx, ny, nz, c, u, "f32", seed=1)
+    o.step(40)
+    gpu.step(40)
+    _fields_close(o.moments(), gpu.moments(), 1e-4)
+    gpu.close()
+
+
+def test_profiles_and_residual_consistent(l3):
+    o, gpu, _, _ = _pair(l3, 37, 9, 5, (0.3, 0.3), (0.0, 0.05), "f64", seed=2)
+    gpu.residual()
+    m0 = gpu.moments()
+    gpu.step(10)
+    m1 = gpu.moments()
+    u, b = gpu.profiles()
+    assert np.allclose(u, m1[1].mean(axis=(0, 2)), rtol=1e-13, atol=1e-18)
+    assert np.allclose(b, m1[4].mean(axis=(0, 2)), rtol=1e-13, atol=1e-18)
+    ru, rb = gpu.residual()
+    ru_h = np.sqrt(np.sum((m1[1] - m0[1]) ** 2) / np.sum(m1[1] ** 2))
+    rb_h = np.sqrt(np.sum((m1[4] - m0[4]) ** 2) / np.sum(m1[4] ** 2))
+    assert ru == pytest.approx(ru_h, rel=1e-9) and rb == pytest.approx(rb_h, rel=1e-9)
+    gpu.close()
+
+
+@pytest.mark.parametrize("ha,c", [(5.0, 0.5), (10.0, math.inf)])
+def test_steady_hartmann_profiles(l3, ha, c):
+    ny, tau = 48, 0.8
+    a = ny / 2
+    tm2 = 0.5 + 0.75 * (tau - 0.5)     # D2Q5 tau_m with the D3Q7 diffusivity
+    b0 = an.b0_from_ha(ha, a, tau, tm2)
+    fx = an.force_for_centre_speed(0.01, ha, c, a, tau)
+    gpu = l3.Lattice3D(3, ny, 2, tau, tau, b0, fx, "f64")
+    gpu.set_walls(c, c)
+    steps, r, status = gpu.run_to_steady(1e-9, 200, 400_000)
+    assert r < 1e-9
+    u, b = gpu.profiles()
+    ua, ba = an.hartmann_profiles(gpu.y(), a, ha, c, fx, tau, tm2)
+    assert an.rel_l2(u, ua) < 5e-3 and an.rel_l2(b, ba) < 5e-3
+    gpu.close()
