@@ -646,6 +646,34 @@ def bench_serve(args):
     return 0
 
 
+def bench_d3(args):
+    """The three-dimensional channel alone: n^3 nodes (default 256^3), Hartmann-Couette set-up
+    (link-based walls, c = 1, top wall at 0.05, Ha = 20), FP32 or FP64 storage, K timed steps."""
+    import torch
+    from paper_2112_13930_gb300 import build, lks, lks3d
+    torch.cuda.set_device(0)
+    build.build()
+    lks.load()
+    n = args.n if args.n != 4096 else 256
+    storage = args.storage if args.storage in ("f32", "f64") else "f32"
+    lat = lks3d.Lattice3D(n, n, n, 0.8, 0.8, 20.0 * 0.1 / (n / 2), 0.0, storage)
+    lat.set_walls(1.0, 1.0, 0.0, 0.05)
+    lat.step(args.warmup)
+    stream = torch.cuda.current_stream()
+    t = _time_steps(lat, args.steps, stream)
+    nodes = n ** 3
+    bpn = 320 if storage == "f32" else 640
+    peak, _ = _peaks()
+    achieved = bpn * nodes / (t / args.steps) / 1e9
+    out = {"workload": "d3q19", "metric": METRIC, "unit": UNIT, "value": round(nodes * args.steps / t / 1e6, 1),
+           "config": {"n": n, "storage": storage, "steps": args.steps, "bytes_per_node": bpn},
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4)}}
+    lat.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def bench_validation(args):
     """The paper's E1-E6 experiments on the GPU (FP64 batch, residual 1e-10); CSV profiles in
     --validation-out; prints a JSON summary of the errors and convergence orders."""
@@ -751,7 +779,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["main", "c1", "precision", "sweep", "serve", "validation"], default="main")
+    ap.add_argument("--workload", choices=["main", "c1", "precision", "sweep", "serve", "validation", "d3"],
+                    default="main")
     ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=None,
                     help="preset of the five benchmark configurations: 1 = c1, 2 = main, 3 = precision, "
                          "4 = sweep, 5 = serve")
@@ -790,6 +819,8 @@ def main():
         return bench_sweep(args)
     if args.workload == "serve":
         return bench_serve(args)
+    if args.workload == "d3":
+        return bench_d3(args)
     if args.workload == "validation":
         return bench_validation(args)
     return bench_ours(args)

@@ -4,7 +4,8 @@ TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's CPU-baselin
 leg are the only users.  The product library never imports this package, and this
 package imports nothing from the product library.
 
-`lks_oracle.c` holds the scheme (see its header for the paper passages it follows);
+`lks_oracle.c` holds the scheme (see its header for the paper passages it follows),
+`lks3d_oracle.c` the three-dimensional channel (D3Q19 + D3Q7, link-based walls);
 `analytic.py` holds the closed-form profiles.  `build()` compiles the C file with
 gcc (no fast-math, no FP contraction) into `_build/liboracle.so` beside this file.
 """
