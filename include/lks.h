@@ -108,7 +108,13 @@ typedef struct lks_params {
                               the second reads and writes only the node's own slots), half
                               the population memory at the same bytes per step and the
                               same results bit for bit; lks_step and lks_run_to_steady then
-                              take even step counts (LKS_EINVAL otherwise) */
+                              take even step counts (LKS_EINVAL otherwise).  With 16-bit
+                              storage and even nx the in-place buffer keeps each row
+                              interleaved (32-bit word w holds nodes x = w and x = w + nx/2);
+                              lks_moments, lks_get_state and lks_set_state present and take
+                              node order as always, but raw memory seen through dev_buffer
+                              is in that order (and is not a valid input of
+                              lks_residual_noalloc, which expects node order) */
 } lks_params;
 
 typedef struct lks_handle lks_handle;

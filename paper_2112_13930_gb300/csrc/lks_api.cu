@@ -294,10 +294,11 @@ lks_status lks_create(const lks_params* p, lks_handle** out) {
         return cuda_fail(nullptr, e, "lks_create");
     }
     refresh_params(h);
-    e = lks::launch_init(p->storage, h->f[0], h->g[0], p->nx, p->ny, p->B0, p->seed, p->perturb_amp, h->stream);
+    const int ilv = lks::interleave_row(p->storage, p->nx, p->inplace);
+    e = lks::launch_init(p->storage, h->f[0], h->g[0], p->nx, p->ny, p->B0, p->seed, p->perturb_amp, h->stream, ilv);
     if (e == cudaSuccess)
         e = lks::launch_snapshot(p->storage, h->f[0], h->g[0], p->nx, p->ny, p->B0, p->Fx, h->snap, h->stream,
-                                 p->coupling, p->tau_m);
+                                 p->coupling, p->tau_m, ilv);
     if (e != cudaSuccess) {
         lks_destroy(h);
         return cuda_fail(nullptr, e, "lks_create: init kernel");
@@ -354,7 +355,8 @@ lks_status lks_moments_device(lks_handle* h, int what, double* dev_out) {
     if (!dev_out) return fail(h, LKS_EINVAL, "dev_out is NULL");
     if (what != LKS_MOMENTS_NODES && what != LKS_MOMENTS_PROFILES) return fail(h, LKS_EINVAL, "bad 'what'");
     cudaError_t e = lks::launch_moments(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0,
-                                        h->p.Fx, what, dev_out, h->stream, h->p.coupling, h->p.tau_m);
+                                        h->p.Fx, what, dev_out, h->stream, h->p.coupling, h->p.tau_m,
+                                        lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace));
     if (e != cudaSuccess) return cuda_fail(h, e, "moments kernel");
     return LKS_OK;
 }
@@ -392,7 +394,7 @@ lks_status lks_residual(lks_handle* h, double* r_u, double* r_b) {
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     cudaError_t e = lks::launch_residual(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0,
                                          h->p.Fx, h->snap, h->partial, h->dout, h->stream, h->p.coupling,
-                                         h->p.tau_m);
+                                         h->p.tau_m, lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->host_small, h->dout, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -447,7 +449,7 @@ lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g) {
         return fail(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
     }
     e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], (int64_t)N, h->p.B0, tmp, tmp + 9 * N,
-                           h->stream, h->p.coupling);
+                           h->stream, h->p.coupling, lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace));
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_g, tmp + 9 * N, 10 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -473,10 +475,11 @@ lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host
         e = cudaMemcpyAsync(tmp + 9 * N, host_g, 10 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = lks::launch_from_abs(h->p.storage, tmp, tmp + 9 * N, (int64_t)N, h->p.B0, h->f[h->cur], h->g[h->cur],
-                                 h->stream, h->p.coupling);
+                                 h->stream, h->p.coupling, lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace));
     if (e == cudaSuccess)
         e = lks::launch_snapshot(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0, h->p.Fx,
-                                 h->snap, h->stream, h->p.coupling, h->p.tau_m);
+                                 h->snap, h->stream, h->p.coupling, h->p.tau_m,
+                                 lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace));
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_set_state");

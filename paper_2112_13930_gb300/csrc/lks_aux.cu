@@ -33,6 +33,17 @@ struct MomentModel {
     int coupling;
 };
 
+// Storage slot of node n.  ilv = 0: the node order, n = y nx + x.  ilv = nx (16-bit storage, nx
+// even): rows interleaved for the two-nodes-per-thread kernels -- 32-bit word w of a row holds
+// node x = w in its lower half and x = w + nx/2 in its upper half, so slot 2 (x mod nx/2) + (x >= nx/2).
+__device__ __forceinline__ int64_t slot_of(int64_t n, int ilv) {
+    if (ilv == 0) return n;
+    const int64_t y = n / ilv;
+    const int x = (int)(n - y * ilv);
+    const int h = ilv >> 1;
+    return y * ilv + (x < h ? 2 * x : 2 * (x - h) + 1);
+}
+
 // SplitMix64 (Steele, Lea & Flood 2014) of seed XOR counter -> [0, 1) with 53 bits.
 __device__ __forceinline__ double splitmix_unit(uint64_t seed, uint64_t counter) {
     uint64_t z = (seed ^ counter) + 0x9e3779b97f4a7c15ULL;
@@ -43,9 +54,10 @@ __device__ __forceinline__ double splitmix_unit(uint64_t seed, uint64_t counter)
 }
 
 template <typename S, typename C>
-__global__ void init_kernel(S* f, S* g, int64_t N, double B0, uint64_t seed, double amp) {
+__global__ void init_kernel(S* f, S* g, int64_t N, double B0, uint64_t seed, double amp, int ilv) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
+    const int64_t pn = slot_of(n, ilv);
     double ux = 0.0, uy = 0.0;
     if (amp != 0.0) {
         ux = amp * (2.0 * splitmix_unit(seed, 2ull * (uint64_t)n) - 1.0);
@@ -55,16 +67,16 @@ __global__ void init_kernel(S* f, S* g, int64_t N, double B0, uint64_t seed, dou
     for (int a = 0; a < 9; ++a) {
         const double eu = ex9(a) * ux + ey9(a) * uy;
         const double b = 3.0 * eu + 4.5 * eu * eu - usq;  // rho = 1, B = rest
-        store_s<S, C>(f + a * N + n, (C)(w9(a) * b));
+        store_s<S, C>(f + a * N + pn, (C)(w9(a) * b));
     }
     const double E = ux * B0;  // u_x B_y - u_y B_x at B = (0, B0)
     for (int a = 0; a < 5; ++a) {
-        store_s<S, C>(g + a * N + n, (C)(-3.0 * w5(a) * ey9(a) * E));
-        store_s<S, C>(g + (5 + a) * N + n, (C)(3.0 * w5(a) * ex9(a) * E));
+        store_s<S, C>(g + a * N + pn, (C)(-3.0 * w5(a) * ey9(a) * E));
+        store_s<S, C>(g + (5 + a) * N + pn, (C)(3.0 * w5(a) * ex9(a) * E));
     }
 }
 
-// FP64 moments of node n of a stored state: rho, u_x, u_y, B_x, B_y.
+// FP64 moments of the node stored in slot n of a state: rho, u_x, u_y, B_x, B_y.
 // Coupling 0: rho u = sum f~ e - F/2.  Coupling 1: the force includes J x B; the stored g carries
 // (1 - 1/tau_m) Lambda^(1) of the last collision, so with k' = 3/(tau_m - 1) and
 // D~ = Lambda~_yx - Lambda~_xy:  J_z = k' [D~ + 2 (B_y (j_x - F_ext/2) - B_x j_y)/rho] / (1 - k' |B|^2/rho).
@@ -106,11 +118,11 @@ __device__ __forceinline__ void node_moments(const S* f, const S* g, int64_t N, 
 }
 
 template <typename S, typename C>
-__global__ void moments_kernel(const S* f, const S* g, int64_t N, MomentModel mm, double* out) {
+__global__ void moments_kernel(const S* f, const S* g, int64_t N, MomentModel mm, double* out, int ilv) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     double m[5];
-    node_moments<S, C>(f, g, N, n, mm, m);
+    node_moments<S, C>(f, g, N, slot_of(n, ilv), mm, m);
 #pragma unroll
     for (int k = 0; k < 5; ++k) out[k * N + n] = m[k];
 }
@@ -135,14 +147,14 @@ __device__ __forceinline__ void block_sum(double v[K], double* sh) {
 
 template <typename S, typename C>
 __global__ void __launch_bounds__(kThreads) profiles_kernel(const S* f, const S* g, int nx, int ny, MomentModel mm,
-                                                           double* out) {
+                                                           double* out, int ilv) {
     __shared__ double sh[5 * kThreads];
     const int j = blockIdx.x;
     const int64_t N = (int64_t)nx * ny;
     double acc[5] = {0, 0, 0, 0, 0};
     for (int i = threadIdx.x; i < nx; i += kThreads) {
         double m[5];
-        node_moments<S, C>(f, g, N, (int64_t)j * nx + i, mm, m);
+        node_moments<S, C>(f, g, N, slot_of((int64_t)j * nx + i, ilv), mm, m);
 #pragma unroll
         for (int k = 0; k < 5; ++k) acc[k] += m[k];
     }
@@ -153,12 +165,13 @@ __global__ void __launch_bounds__(kThreads) profiles_kernel(const S* f, const S*
 
 template <typename S, typename C>
 __global__ void __launch_bounds__(kThreads) residual_partial_kernel(const S* f, const S* g, int64_t N,
-                                                                   MomentModel mm, double* snap, double* partial) {
+                                                                   MomentModel mm, double* snap, double* partial,
+                                                                   int ilv) {
     __shared__ double sh[4 * kThreads];
     double acc[4] = {0, 0, 0, 0};
     for (int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x; n < N; n += (int64_t)gridDim.x * kThreads) {
         double m[5];
-        node_moments<S, C>(f, g, N, n, mm, m);
+        node_moments<S, C>(f, g, N, slot_of(n, ilv), mm, m);
         const double du = m[1] - snap[n];
         const double db = m[3] - snap[N + n];
         acc[0] += du * du;
@@ -184,34 +197,38 @@ __global__ void __launch_bounds__(kThreads) residual_final_kernel(const double* 
 }
 
 template <typename S, typename C>
-__global__ void snapshot_kernel(const S* f, const S* g, int64_t N, MomentModel mm, double* snap) {
+__global__ void snapshot_kernel(const S* f, const S* g, int64_t N, MomentModel mm, double* snap, int ilv) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     double m[5];
-    node_moments<S, C>(f, g, N, n, mm, m);
+    node_moments<S, C>(f, g, N, slot_of(n, ilv), mm, m);
     snap[n] = m[1];
     snap[N + n] = m[3];
 }
 
 template <typename S, typename C>
-__global__ void to_abs_kernel(const S* f, const S* g, int64_t N, double B0, int coupling, double* fa, double* ga) {
+__global__ void to_abs_kernel(const S* f, const S* g, int64_t N, double B0, int coupling, double* fa, double* ga,
+                              int ilv) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    for (int a = 0; a < 9; ++a) fa[a * N + n] = (double)load_s<S, C>(f + a * N + n) + f_rest(a, B0, coupling);
+    const int64_t pn = slot_of(n, ilv);
+    for (int a = 0; a < 9; ++a) fa[a * N + n] = (double)load_s<S, C>(f + a * N + pn) + f_rest(a, B0, coupling);
     for (int a = 0; a < 5; ++a) {
-        ga[a * N + n] = (double)load_s<S, C>(g + a * N + n);
-        ga[(5 + a) * N + n] = (double)load_s<S, C>(g + (5 + a) * N + n) + w5(a) * B0;
+        ga[a * N + n] = (double)load_s<S, C>(g + a * N + pn);
+        ga[(5 + a) * N + n] = (double)load_s<S, C>(g + (5 + a) * N + pn) + w5(a) * B0;
     }
 }
 
 template <typename S, typename C>
-__global__ void from_abs_kernel(const double* fa, const double* ga, int64_t N, double B0, int coupling, S* f, S* g) {
+__global__ void from_abs_kernel(const double* fa, const double* ga, int64_t N, double B0, int coupling, S* f, S* g,
+                                int ilv) {
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    for (int a = 0; a < 9; ++a) store_s<S, C>(f + a * N + n, (C)(fa[a * N + n] - f_rest(a, B0, coupling)));
+    const int64_t pn = slot_of(n, ilv);
+    for (int a = 0; a < 9; ++a) store_s<S, C>(f + a * N + pn, (C)(fa[a * N + n] - f_rest(a, B0, coupling)));
     for (int a = 0; a < 5; ++a) {
-        store_s<S, C>(g + a * N + n, (C)ga[a * N + n]);
-        store_s<S, C>(g + (5 + a) * N + n, (C)(ga[(5 + a) * N + n] - w5(a) * B0));
+        store_s<S, C>(g + a * N + pn, (C)ga[a * N + n]);
+        store_s<S, C>(g + (5 + a) * N + pn, (C)(ga[(5 + a) * N + n] - w5(a) * B0));
     }
 }
 
@@ -241,22 +258,22 @@ inline unsigned grid_for(int64_t N) { return (unsigned)((N + kThreads - 1) / kTh
     } while (0)
 
 cudaError_t launch_init(int storage, void* f, void* g, int nx, int ny, double B0, uint64_t seed, double amp,
-                        cudaStream_t st) {
+                        cudaStream_t st, int ilv) {
     const int64_t N = (int64_t)nx * ny;
-    LKS_DISPATCH(storage, (init_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((S*)f, (S*)g, N, B0, seed, amp)));
+    LKS_DISPATCH(storage, (init_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((S*)f, (S*)g, N, B0, seed, amp, ilv)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                           int what, double* out, cudaStream_t st, int coupling, double tau_m) {
+                           int what, double* out, cudaStream_t st, int coupling, double tau_m, int ilv) {
     const int64_t N = (int64_t)nx * ny;
     const MomentModel mm{B0, Fx, tau_m, coupling};
     if (what == 0) {
         LKS_DISPATCH(storage, (moments_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N,
-                                                                                      mm, out)));
+                                                                                      mm, out, ilv)));
     } else {
         LKS_DISPATCH(storage, (profiles_kernel<S, C><<<ny, kThreads, 0, st>>>((const S*)f, (const S*)g, nx, ny, mm,
-                                                                              out)));
+                                                                              out, ilv)));
     }
     return cudaGetLastError();
 }
@@ -269,36 +286,37 @@ int residual_blocks(int64_t N) {
 }
 
 cudaError_t launch_residual(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                            double* snap, double* partial, double* out, cudaStream_t st, int coupling, double tau_m) {
+                            double* snap, double* partial, double* out, cudaStream_t st, int coupling, double tau_m,
+                            int ilv) {
     const int64_t N = (int64_t)nx * ny;
     const int nblk = residual_blocks(N);
     const MomentModel mm{B0, Fx, tau_m, coupling};
     LKS_DISPATCH(storage, (residual_partial_kernel<S, C><<<nblk, kThreads, 0, st>>>((const S*)f, (const S*)g, N,
-                                                                                    mm, snap, partial)));
+                                                                                    mm, snap, partial, ilv)));
     residual_final_kernel<<<1, kThreads, 0, st>>>(partial, nblk, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_snapshot(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                            double* snap, cudaStream_t st, int coupling, double tau_m) {
+                            double* snap, cudaStream_t st, int coupling, double tau_m, int ilv) {
     const int64_t N = (int64_t)nx * ny;
     const MomentModel mm{B0, Fx, tau_m, coupling};
     LKS_DISPATCH(storage, (snapshot_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N, mm,
-                                                                                   snap)));
+                                                                                   snap, ilv)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, double B0, double* fabs,
-                          double* gabs, cudaStream_t st, int coupling) {
+                          double* gabs, cudaStream_t st, int coupling, int ilv) {
     LKS_DISPATCH(storage, (to_abs_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N, B0,
-                                                                                 coupling, fabs, gabs)));
+                                                                                 coupling, fabs, gabs, ilv)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, double B0, void* f,
-                            void* g, cudaStream_t st, int coupling) {
+                            void* g, cudaStream_t st, int coupling, int ilv) {
     LKS_DISPATCH(storage, (from_abs_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>(fabs, gabs, N, B0, coupling,
-                                                                                   (S*)f, (S*)g)));
+                                                                                   (S*)f, (S*)g, ilv)));
     return cudaGetLastError();
 }
 

@@ -51,6 +51,14 @@ StepParams<double> make_step_params(int nx, int ny, int closure, double tau_f, d
 // Bytes per stored population for each lks_storage value.
 inline size_t storage_bytes(int storage) { return storage == 0 ? 8 : (storage == 1 ? 4 : 2); }
 
+// Storage order of a single lattice's populations: an in-place handle with 16-bit storage and even
+// nx keeps every row interleaved for its two-nodes-per-thread kernels (32-bit word w holds nodes
+// x = w and x = w + nx/2, so a shift by one node is a shift by one word); the value is the row
+// length the readout kernels need (0: plain node order, all other handles).
+inline int interleave_row(int storage, int nx, int inplace) {
+    return (inplace && storage >= 2 && (nx % 2) == 0) ? nx : 0;
+}
+
 // One fused step: (fin, gin) -> (fout, gout) on stream st.
 cudaError_t launch_step(int storage, int closure, const void* fin, const void* gin, void* fout, void* gout,
                         const StepParams<double>& p, cudaStream_t st);
@@ -60,12 +68,13 @@ cudaError_t launch_step_aa(int storage, int closure, int phase, void* f, void* g
 
 // Initial equilibrium state (deviation form) with the counter-based perturbation.
 cudaError_t launch_init(int storage, void* f, void* g, int nx, int ny, double B0, uint64_t seed, double amp,
-                        cudaStream_t st);
+                        cudaStream_t st, int ilv = 0);
 
 // Moments of a stored state: out[m*N + n] (what = 0) or x-averaged profiles out[m*ny + j] (what = 1).
 // coupling / tau_m: the moment model of the state (0: Maxwell stress; 1: Lorentz force, which needs tau_m).
 cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                           int what, double* out, cudaStream_t st, int coupling = 0, double tau_m = 1.0);
+                           int what, double* out, cudaStream_t st, int coupling = 0, double tau_m = 1.0,
+                           int ilv = 0);
 
 // Residual partial sums: nblk blocks write partial[4*blk + k] = (sum du^2, sum u^2, sum db^2, sum b^2)
 // and refresh the snapshot snap[0..N) = u_x, snap[N..2N) = B_x; then one block reduces in fixed order
@@ -73,14 +82,14 @@ cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, in
 int residual_blocks(int64_t N);
 cudaError_t launch_residual(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
                             double* snap, double* partial, double* out, cudaStream_t st, int coupling = 0,
-                            double tau_m = 1.0);
+                            double tau_m = 1.0, int ilv = 0);
 cudaError_t launch_snapshot(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
-                            double* snap, cudaStream_t st, int coupling = 0, double tau_m = 1.0);
+                            double* snap, cudaStream_t st, int coupling = 0, double tau_m = 1.0, int ilv = 0);
 
 // FP64 absolute populations <-> stored deviations.
 cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, double B0, double* fabs,
-                          double* gabs, cudaStream_t st, int coupling = 0);
+                          double* gabs, cudaStream_t st, int coupling = 0, int ilv = 0);
 cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, double B0, void* f,
-                            void* g, cudaStream_t st, int coupling = 0);
+                            void* g, cudaStream_t st, int coupling = 0, int ilv = 0);
 
 }  // namespace lks

@@ -28,51 +28,46 @@ __global__ void __launch_bounds__(256) step_kernel_aa(S* fb, S* gb, const StepPa
         aa_node_local<S, C, CLOSURE, COUPLING>(fb, gb, p, n, j);
 }
 
-// 16-bit storage, two nodes (x0, x0 + 1) per thread and one 32-bit word per population plane (nx
-// even), as the two-buffer pair kernel.  Phase 1 touches only the thread's own words.  Phase 0
-// pulls exactly as the pair kernel does and pushes every population into the opposite-direction
-// plane of its target node: pushes that stay in the column are whole words; a push to x + 1 fills
-// the word (x0, x0 + 1) with (left lane's node x0 - 1, own node x0) through a warp shuffle, a push
-// to x - 1 fills it with (own node x0 + 1, right lane's node x0 + 2); at a warp or row edge the lane
-// writes only its own half and the edge lane of the neighbouring pair the other one, as 16-bit
-// stores.  All shuffles run on all 32 lanes (lanes past the end on a clamped pair, stores masked),
-// also where a warp spans two rows.  Each element is written by one thread, after the thread
-// that reads it (itself, or through a shuffle fed by its loads) has read it.
+// 16-bit storage, two nodes per thread and one 32-bit word per population plane (nx even), with
+// the rows interleaved as for the two-buffer pair kernel: word w of a row holds nodes x = w and
+// x = w + nx/2.  A shift by one node in x is then a shift by one word (halves swapped at the
+// periodic row edge), so phase 0 pulls and pushes whole aligned words exactly as the one-node
+// in-place kernel does per node: the pulls of word w come from words w - 1 / w / w + 1 of the
+// neighbouring rows and the pushes go to the same words.  No two threads touch the same word
+// (each word a thread pushes into holds the two elements its own nodes pull in that direction),
+// and every thread reads its words before it writes them.  Phase 1 touches only its own words.
 template <typename S, int CLOSURE, int COUPLING, int PHASE, bool ROWS2D>
-__global__ void __launch_bounds__(256, PHASE == 0 ? 3 : 4) step_kernel_aa_pair(S* fb, S* gb, const StepParams<float> p) {
+__global__ void __launch_bounds__(256, (CLOSURE == 0 || PHASE == 0) ? 3 : 4) step_kernel_aa_pair(S* fb, S* gb, const StepParams<float> p) {
     typedef Packed<S> P;
-    const unsigned FULL = 0xffffffffu;
-    const int nx = p.nx, npr = nx >> 1;
-    const int64_t N = p.N, NP = N >> 1;
-    const int lane = threadIdx.x & 31;
-    int j, ip;
-    bool active;
+    const int H = p.nx >> 1;
+    const int64_t NP = p.N >> 1;
+    int j, w;
     if (ROWS2D) {
-        const int ip0 = blockIdx.x * blockDim.x + threadIdx.x;
-        active = ip0 < npr;
-        ip = active ? ip0 : npr - 1;
+        w = blockIdx.x * blockDim.x + threadIdx.x;
         j = blockIdx.y;
+        if (w >= H) return;
     } else {
         const unsigned q0 = blockIdx.x * blockDim.x + threadIdx.x;
-        active = (int64_t)q0 < NP;
-        const unsigned q1 = active ? q0 : (unsigned)(NP - 1);
-        j = (int)(q1 / (unsigned)npr);
-        ip = (int)(q1 - (unsigned)j * (unsigned)npr);
+        if ((int64_t)q0 >= NP) return;
+        j = (int)(q0 / (unsigned)H);
+        w = (int)(q0 - (unsigned)j * (unsigned)H);
     }
-    const int64_t q = (int64_t)j * npr + ip;
+    const int64_t q = (int64_t)j * H + w;
     const bool bottom = (j == 0), top = (j == p.ny - 1);
     uint32_t* fw = reinterpret_cast<uint32_t*>(fb);
     uint32_t* gxw = reinterpret_cast<uint32_t*>(gb);
     uint32_t* gyw = gxw + 5 * NP;
     float fA[9], fB[9], gxA[5], gxB[5], gyA[5], gyB[5];
+    auto take = [](uint32_t v, bool swap, float& A, float& B) {
+        if (swap) v = __byte_perm(v, 0, 0x1032);
+        A = P::lo(v);
+        B = P::hi(v);
+    };
 
     if (PHASE == 1) {
-        if (!active) return;  // no shuffles in this phase
         // direction a of both nodes from plane abar of the own word
         auto own = [&](const uint32_t* base, int plane, bool valid, float& A, float& B) {
-            const uint32_t w = valid ? base[plane * NP + q] : 0u;
-            A = P::lo(w);
-            B = P::hi(w);
+            take(valid ? base[plane * NP + q] : 0u, false, A, B);
         };
         const bool skip_up = CLOSURE == 1 && bottom, skip_down = CLOSURE == 1 && top;
         own(fw, 0, true, fA[0], fB[0]);
@@ -97,17 +92,17 @@ __global__ void __launch_bounds__(256, PHASE == 0 ? 3 : 4) step_kernel_aa_pair(S
         if (CLOSURE == 0) {
             // the wall slots hold the node's own raw outgoing populations
             if (bottom) {
-                const WallCoef<float>& w = p.bot;
-                fA[5] = fA[5] + w.du; fB[5] = fB[5] + w.du;
-                fA[6] = fA[6] - w.du; fB[6] = fB[6] - w.du;
-                gxA[2] = ffma(w.r, gxA[2], w.kx); gxB[2] = ffma(w.r, gxB[2], w.kx);
+                const WallCoef<float>& wc = p.bot;
+                fA[5] = fA[5] + wc.du; fB[5] = fB[5] + wc.du;
+                fA[6] = fA[6] - wc.du; fB[6] = fB[6] - wc.du;
+                gxA[2] = ffma(wc.r, gxA[2], wc.kx); gxB[2] = ffma(wc.r, gxB[2], wc.kx);
                 gyA[2] = -gyA[2]; gyB[2] = -gyB[2];
             }
             if (top) {
-                const WallCoef<float>& w = p.top;
-                fA[7] = fA[7] - w.du; fB[7] = fB[7] - w.du;
-                fA[8] = fA[8] + w.du; fB[8] = fB[8] + w.du;
-                gxA[4] = ffma(w.r, gxA[4], w.kx); gxB[4] = ffma(w.r, gxB[4], w.kx);
+                const WallCoef<float>& wc = p.top;
+                fA[7] = fA[7] - wc.du; fB[7] = fB[7] - wc.du;
+                fA[8] = fA[8] + wc.du; fB[8] = fB[8] + wc.du;
+                gxA[4] = ffma(wc.r, gxA[4], wc.kx); gxB[4] = ffma(wc.r, gxB[4], wc.kx);
                 gyA[4] = -gyA[4]; gyB[4] = -gyB[4];
             }
         } else {
@@ -130,78 +125,54 @@ __global__ void __launch_bounds__(256, PHASE == 0 ? 3 : 4) step_kernel_aa_pair(S
         for (int a = 0; a < 5; ++a) gyw[a * NP + q] = P::pack(gyA[a], gyB[a]);
         return;
     }
-    // ---- phase 0: pull (as the two-buffer pair kernel, coherent loads), close, collide ----
-    const int x0 = ip << 1;
-    const int64_t rc = (int64_t)j * npr, rs = rc - npr, rn = rc + npr;   // pair-row starts
-    const int64_t ec = (int64_t)j * nx, es = ec - nx, en = ec + nx;      // element-row starts
-    const bool left_edge = (lane == 0) || (ip == 0);
-    const bool right_edge = (lane == 31) || (ip == npr - 1);
-    const int xm = (x0 == 0) ? nx - 1 : x0 - 1;   // element left of the pair (periodic)
-    const int xp = (x0 + 2 == nx) ? 0 : x0 + 2;   // element right of the pair (periodic)
-    S* gxs = gb;
-    S* gys = gb + 5 * N;
-    auto Wd = [&](const uint32_t* base, int a, int64_t r) -> uint32_t { return base[a * NP + r + ip]; };
-    auto Ed = [&](const S* base, int a, int64_t re, int x) -> float {
-        return Loader<S, float, false>::ld(base + a * N + re + x);
-    };
-    auto pull_left = [&](const uint32_t* base, const S* ebase, int a, int64_t r, int64_t re, bool valid, float& A,
-                         float& B) {
-        const uint32_t w = valid ? Wd(base, a, r) : 0u;
-        const uint32_t wl = __shfl_up_sync(FULL, w, 1);
-        B = P::lo(w);
-        A = P::hi(wl);
-        if (valid && left_edge) A = Ed(ebase, a, re, xm);
-    };
-    auto pull_right = [&](const uint32_t* base, const S* ebase, int a, int64_t r, int64_t re, bool valid, float& A,
-                          float& B) {
-        const uint32_t w = valid ? Wd(base, a, r) : 0u;
-        const uint32_t wr = __shfl_down_sync(FULL, w, 1);
-        A = P::hi(w);
-        B = P::lo(wr);
-        if (valid && right_edge) B = Ed(ebase, a, re, xp);
-    };
-    auto pull_same = [&](const uint32_t* base, int a, int64_t r, bool valid, float& A, float& B) {
-        const uint32_t w = valid ? Wd(base, a, r) : 0u;
-        A = P::lo(w);
-        B = P::hi(w);
-    };
-    pull_same(fw, 0, rc, true, fA[0], fB[0]);
-    pull_left(fw, fb, 1, rc, ec, true, fA[1], fB[1]);
-    pull_right(fw, fb, 3, rc, ec, true, fA[3], fB[3]);
-    pull_same(fw, 2, rs, !bottom, fA[2], fB[2]);
-    pull_left(fw, fb, 5, rs, es, !bottom, fA[5], fB[5]);
-    pull_right(fw, fb, 6, rs, es, !bottom, fA[6], fB[6]);
-    pull_same(fw, 4, rn, !top, fA[4], fB[4]);
-    pull_right(fw, fb, 7, rn, en, !top, fA[7], fB[7]);
-    pull_left(fw, fb, 8, rn, en, !top, fA[8], fB[8]);
-    pull_same(gxw, 0, rc, true, gxA[0], gxB[0]);
-    pull_left(gxw, gxs, 1, rc, ec, true, gxA[1], gxB[1]);
-    pull_right(gxw, gxs, 3, rc, ec, true, gxA[3], gxB[3]);
-    pull_same(gxw, 2, rs, !bottom, gxA[2], gxB[2]);
-    pull_same(gxw, 4, rn, !top, gxA[4], gxB[4]);
-    pull_same(gyw, 0, rc, true, gyA[0], gyB[0]);
-    pull_left(gyw, gys, 1, rc, ec, true, gyA[1], gyB[1]);
-    pull_right(gyw, gys, 3, rc, ec, true, gyA[3], gyB[3]);
-    pull_same(gyw, 2, rs, !bottom, gyA[2], gyB[2]);
-    pull_same(gyw, 4, rn, !top, gyA[4], gyB[4]);
+    // ---- phase 0: pull (as the two-buffer pair kernel, coherent loads), close, collide, push ----
+    const int64_t rc = (int64_t)j * H, rs = rc - H, rn = rc + H;
+    const int wm = (w == 0) ? H - 1 : w - 1, wp = (w == H - 1) ? 0 : w + 1;
+    const bool sm = (w == 0), sp = (w == H - 1);
+    auto ps = [&](const uint32_t* base, int a, int64_t r, float& A, float& B) { take(base[a * NP + r + w], false, A, B); };
+    auto pl = [&](const uint32_t* base, int a, int64_t r, float& A, float& B) { take(base[a * NP + r + wm], sm, A, B); };
+    auto pr = [&](const uint32_t* base, int a, int64_t r, float& A, float& B) { take(base[a * NP + r + wp], sp, A, B); };
+    ps(fw, 0, rc, fA[0], fB[0]);
+    pl(fw, 1, rc, fA[1], fB[1]);
+    pr(fw, 3, rc, fA[3], fB[3]);
+    ps(gxw, 0, rc, gxA[0], gxB[0]);
+    pl(gxw, 1, rc, gxA[1], gxB[1]);
+    pr(gxw, 3, rc, gxA[3], gxB[3]);
+    ps(gyw, 0, rc, gyA[0], gyB[0]);
+    pl(gyw, 1, rc, gyA[1], gyB[1]);
+    pr(gyw, 3, rc, gyA[3], gyB[3]);
+    if (!bottom) {
+        ps(fw, 2, rs, fA[2], fB[2]);
+        pl(fw, 5, rs, fA[5], fB[5]);
+        pr(fw, 6, rs, fA[6], fB[6]);
+        ps(gxw, 2, rs, gxA[2], gxB[2]);
+        ps(gyw, 2, rs, gyA[2], gyB[2]);
+    }
+    if (!top) {
+        ps(fw, 4, rn, fA[4], fB[4]);
+        pr(fw, 7, rn, fA[7], fB[7]);
+        pl(fw, 8, rn, fA[8], fB[8]);
+        ps(gxw, 4, rn, gxA[4], gxB[4]);
+        ps(gyw, 4, rn, gyA[4], gyB[4]);
+    }
     if (CLOSURE == 0) {
         if (bottom) {
-            const WallCoef<float>& w = p.bot;
+            const WallCoef<float>& wc = p.bot;
             float a, b;
-            pull_same(fw, 4, rc, true, a, b); fA[2] = a; fB[2] = b;
-            pull_same(fw, 7, rc, true, a, b); fA[5] = a + w.du; fB[5] = b + w.du;
-            pull_same(fw, 8, rc, true, a, b); fA[6] = a - w.du; fB[6] = b - w.du;
-            pull_same(gxw, 4, rc, true, a, b); gxA[2] = ffma(w.r, a, w.kx); gxB[2] = ffma(w.r, b, w.kx);
-            pull_same(gyw, 4, rc, true, a, b); gyA[2] = -a; gyB[2] = -b;
+            ps(fw, 4, rc, a, b); fA[2] = a; fB[2] = b;
+            ps(fw, 7, rc, a, b); fA[5] = a + wc.du; fB[5] = b + wc.du;
+            ps(fw, 8, rc, a, b); fA[6] = a - wc.du; fB[6] = b - wc.du;
+            ps(gxw, 4, rc, a, b); gxA[2] = ffma(wc.r, a, wc.kx); gxB[2] = ffma(wc.r, b, wc.kx);
+            ps(gyw, 4, rc, a, b); gyA[2] = -a; gyB[2] = -b;
         }
         if (top) {
-            const WallCoef<float>& w = p.top;
+            const WallCoef<float>& wc = p.top;
             float a, b;
-            pull_same(fw, 2, rc, true, a, b); fA[4] = a; fB[4] = b;
-            pull_same(fw, 5, rc, true, a, b); fA[7] = a - w.du; fB[7] = b - w.du;
-            pull_same(fw, 6, rc, true, a, b); fA[8] = a + w.du; fB[8] = b + w.du;
-            pull_same(gxw, 2, rc, true, a, b); gxA[4] = ffma(w.r, a, w.kx); gxB[4] = ffma(w.r, b, w.kx);
-            pull_same(gyw, 2, rc, true, a, b); gyA[4] = -a; gyB[4] = -b;
+            ps(fw, 2, rc, a, b); fA[4] = a; fB[4] = b;
+            ps(fw, 5, rc, a, b); fA[7] = a - wc.du; fB[7] = b - wc.du;
+            ps(fw, 6, rc, a, b); fA[8] = a + wc.du; fB[8] = b + wc.du;
+            ps(gxw, 2, rc, a, b); gxA[4] = ffma(wc.r, a, wc.kx); gxB[4] = ffma(wc.r, b, wc.kx);
+            ps(gyw, 2, rc, a, b); gyA[4] = -a; gyB[4] = -b;
         }
     } else {
         if (bottom) {
@@ -215,58 +186,44 @@ __global__ void __launch_bounds__(256, PHASE == 0 ? 3 : 4) step_kernel_aa_pair(S
     }
     collide<float, COUPLING>(fA, gxA, gyA, p);
     collide<float, COUPLING>(fB, gxB, gyB, p);
-
-    // ---- push: A_b -> plane bbar at x + e_b; through a wall -> plane b at x ----
-    auto st16 = [&](S* ebase, int a, int64_t re, int x, float v) { store_s<S, float>(ebase + a * N + re + x, v); };
-    // same column, pair row r
-    auto push_same = [&](uint32_t* base, int a, int64_t r, bool valid, float A, float B) {
-        if (active && valid) base[a * NP + r + ip] = P::pack(A, B);
-    };
-    // to x + 1: element x0 <- left lane's B (node x0 - 1), x0 + 1 <- A, x0 + 2 <- B (edge lanes)
-    auto push_right = [&](uint32_t* base, S* ebase, int a, int64_t r, int64_t re, bool valid, float A, float B) {
-        const float Bl = __shfl_up_sync(FULL, B, 1);
-        if (!(active && valid)) return;
-        if (!left_edge) base[a * NP + r + ip] = P::pack(Bl, A);
-        else st16(ebase, a, re, x0 + 1, A);
-        if (right_edge) st16(ebase, a, re, xp, B);
-    };
-    // to x - 1: element x0 - 1 <- A (edge lanes), x0 <- B, x0 + 1 <- right lane's A (node x0 + 2)
-    auto push_left = [&](uint32_t* base, S* ebase, int a, int64_t r, int64_t re, bool valid, float A, float B) {
-        const float Ar = __shfl_down_sync(FULL, A, 1);
-        if (!(active && valid)) return;
-        if (!right_edge) base[a * NP + r + ip] = P::pack(B, Ar);
-        else st16(ebase, a, re, x0, B);
-        if (left_edge) st16(ebase, a, re, xm, A);
-    };
-    push_same(fw, 0, rc, true, fA[0], fB[0]);
-    push_right(fw, fb, 3, rc, ec, true, fA[1], fB[1]);
-    push_left(fw, fb, 1, rc, ec, true, fA[3], fB[3]);
-    push_same(fw, 4, rn, !top, fA[2], fB[2]);
-    push_same(fw, 2, rc, top, fA[2], fB[2]);
-    push_right(fw, fb, 7, rn, en, !top, fA[5], fB[5]);
-    push_same(fw, 5, rc, top, fA[5], fB[5]);
-    push_left(fw, fb, 8, rn, en, !top, fA[6], fB[6]);
-    push_same(fw, 6, rc, top, fA[6], fB[6]);
-    push_same(fw, 2, rs, !bottom, fA[4], fB[4]);
-    push_same(fw, 4, rc, bottom, fA[4], fB[4]);
-    push_left(fw, fb, 5, rs, es, !bottom, fA[7], fB[7]);
-    push_same(fw, 7, rc, bottom, fA[7], fB[7]);
-    push_right(fw, fb, 6, rs, es, !bottom, fA[8], fB[8]);
-    push_same(fw, 8, rc, bottom, fA[8], fB[8]);
-    push_same(gxw, 0, rc, true, gxA[0], gxB[0]);
-    push_right(gxw, gxs, 3, rc, ec, true, gxA[1], gxB[1]);
-    push_left(gxw, gxs, 1, rc, ec, true, gxA[3], gxB[3]);
-    push_same(gxw, 4, rn, !top, gxA[2], gxB[2]);
-    push_same(gxw, 2, rc, top, gxA[2], gxB[2]);
-    push_same(gxw, 2, rs, !bottom, gxA[4], gxB[4]);
-    push_same(gxw, 4, rc, bottom, gxA[4], gxB[4]);
-    push_same(gyw, 0, rc, true, gyA[0], gyB[0]);
-    push_right(gyw, gys, 3, rc, ec, true, gyA[1], gyB[1]);
-    push_left(gyw, gys, 1, rc, ec, true, gyA[3], gyB[3]);
-    push_same(gyw, 4, rn, !top, gyA[2], gyB[2]);
-    push_same(gyw, 2, rc, top, gyA[2], gyB[2]);
-    push_same(gyw, 2, rs, !bottom, gyA[4], gyB[4]);
-    push_same(gyw, 4, rc, bottom, gyA[4], gyB[4]);
+    // push: A_b -> plane bbar at x + e_b (the word the own nodes pull direction bbar from);
+    // through a wall -> plane b of the own word
+    auto put = [](uint32_t* at, bool swap, float A, float B) { *at = swap ? P::pack(B, A) : P::pack(A, B); };
+    put(fw + 0 * NP + rc + w, false, fA[0], fB[0]);
+    put(fw + 3 * NP + rc + wp, sp, fA[1], fB[1]);     // +x -> plane 3 at x + 1
+    put(fw + 1 * NP + rc + wm, sm, fA[3], fB[3]);     // -x -> plane 1 at x - 1
+    put(gxw + 0 * NP + rc + w, false, gxA[0], gxB[0]);
+    put(gxw + 3 * NP + rc + wp, sp, gxA[1], gxB[1]);
+    put(gxw + 1 * NP + rc + wm, sm, gxA[3], gxB[3]);
+    put(gyw + 0 * NP + rc + w, false, gyA[0], gyB[0]);
+    put(gyw + 3 * NP + rc + wp, sp, gyA[1], gyB[1]);
+    put(gyw + 1 * NP + rc + wm, sm, gyA[3], gyB[3]);
+    if (!top) {
+        put(fw + 4 * NP + rn + w, false, fA[2], fB[2]);
+        put(fw + 7 * NP + rn + wp, sp, fA[5], fB[5]);
+        put(fw + 8 * NP + rn + wm, sm, fA[6], fB[6]);
+        put(gxw + 4 * NP + rn + w, false, gxA[2], gxB[2]);
+        put(gyw + 4 * NP + rn + w, false, gyA[2], gyB[2]);
+    } else {
+        put(fw + 2 * NP + rc + w, false, fA[2], fB[2]);
+        put(fw + 5 * NP + rc + w, false, fA[5], fB[5]);
+        put(fw + 6 * NP + rc + w, false, fA[6], fB[6]);
+        put(gxw + 2 * NP + rc + w, false, gxA[2], gxB[2]);
+        put(gyw + 2 * NP + rc + w, false, gyA[2], gyB[2]);
+    }
+    if (!bottom) {
+        put(fw + 2 * NP + rs + w, false, fA[4], fB[4]);
+        put(fw + 5 * NP + rs + wm, sm, fA[7], fB[7]);
+        put(fw + 6 * NP + rs + wp, sp, fA[8], fB[8]);
+        put(gxw + 2 * NP + rs + w, false, gxA[4], gxB[4]);
+        put(gyw + 2 * NP + rs + w, false, gyA[4], gyB[4]);
+    } else {
+        put(fw + 4 * NP + rc + w, false, fA[4], fB[4]);
+        put(fw + 7 * NP + rc + w, false, fA[7], fB[7]);
+        put(fw + 8 * NP + rc + w, false, fA[8], fB[8]);
+        put(gxw + 4 * NP + rc + w, false, gxA[4], gxB[4]);
+        put(gyw + 4 * NP + rc + w, false, gyA[4], gyB[4]);
+    }
 }
 
 template <typename S, typename C, int PHASE, bool R2>
@@ -320,7 +277,7 @@ static cudaError_t launch_aa_phase(int storage, int closure, void* f, void* g, c
     if (storage == 0) return launch_aa_typed<double, double, PHASE>(f, g, pd, closure, st);
     const StepParams<float> pf = convert_params<float>(pd);
     if (storage == 1) return launch_aa_typed<float, float, PHASE>(f, g, pf, closure, st);
-    const bool pairs = (pd.nx % 2) == 0;  // two nodes per thread need whole pairs in every row
+    const bool pairs = interleave_row(storage, pd.nx, 1) != 0;  // interleaved rows: two nodes per thread
     if (storage == 2)
         return pairs ? launch_aa_pair<__nv_bfloat16, PHASE>(f, g, pf, closure, st)
                      : launch_aa_typed<__nv_bfloat16, float, PHASE>(f, g, pf, closure, st);

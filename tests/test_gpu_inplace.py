@@ -24,13 +24,24 @@ def lks():
 
 
 def _raw(lat, storage):
-    """The stored populations as raw bytes: f planes, then g planes (the first buffer of the
-    footprint, where a two-buffer handle's state sits after an even number of steps)."""
+    """The stored populations as raw bit patterns in node order: f planes, then g planes (the
+    first buffer of the footprint, where a two-buffer handle's state sits after an even number of
+    steps).  An in-place handle with 16-bit storage and even nx keeps its rows interleaved (word w
+    holds nodes w and w + nx/2), so node x sits in slot 2 (x mod nx/2) + (x >= nx/2)."""
     lat.sync()
-    n = lat.nx * lat.ny * STORAGE_BYTES[storage]
+    sb = STORAGE_BYTES[storage]
+    nx, ny = lat.nx, lat.ny
+    n = nx * ny * sb
     f_bytes = (9 * n + 255) // 256 * 256
     buf = lat._buf.cpu().numpy()
-    return np.concatenate([buf[: 9 * n], buf[f_bytes: f_bytes + 10 * n]])
+    dt = {8: np.uint64, 4: np.uint32, 2: np.uint16}[sb]
+    f = buf[: 9 * n].view(dt).reshape(9, ny, nx)
+    g = buf[f_bytes: f_bytes + 10 * n].view(dt).reshape(10, ny, nx)
+    if lat.inplace and sb == 2 and nx % 2 == 0:
+        h = nx // 2
+        slot = [2 * x if x < h else 2 * (x - h) + 1 for x in range(nx)]
+        f, g = f[:, :, slot], g[:, :, slot]
+    return np.concatenate([f.ravel(), g.ravel()])
 
 
 def _make(lks, nx, ny, closure, storage, coupling, inplace, c, u, amp=1e-3, Fx=2e-6, tau_m=0.8):
