@@ -648,21 +648,22 @@ def bench_serve(args):
 
 def bench_d3(args):
     """The three-dimensional channel alone: n^3 nodes (default 256^3), Hartmann-Couette set-up
-    (link-based walls, c = 1, top wall at 0.05, Ha = 20), FP32 or FP64 storage, K timed steps."""
+    (link-based walls, c = 1, top wall at 0.05, Ha = 20), FP64, FP32, BF16 or FP16 storage, K timed
+    steps.  Algorithmic bytes per node: 40 populations read and written once, 8, 4 or 2 bytes each."""
     import torch
     from paper_2112_13930_gb300 import build, lks, lks3d
     torch.cuda.set_device(0)
     build.build()
     lks.load()
     n = args.n if args.n != 4096 else 256
-    storage = args.storage if args.storage in ("f32", "f64") else "f32"
+    storage = args.storage if args.storage in ("f64", "f32", "bf16", "f16") else "f32"
     lat = lks3d.Lattice3D(n, n, n, 0.8, 0.8, 20.0 * 0.1 / (n / 2), 0.0, storage)
     lat.set_walls(1.0, 1.0, 0.0, 0.05)
     lat.step(args.warmup)
     stream = torch.cuda.current_stream()
     t = _time_steps(lat, args.steps, stream)
     nodes = n ** 3
-    bpn = 320 if storage == "f32" else 640
+    bpn = 80 * {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[storage]
     peak, _ = _peaks()
     achieved = bpn * nodes / (t / args.steps) / 1e9
     out = {"workload": "d3q19", "metric": METRIC, "unit": UNIT, "value": round(nodes * args.steps / t / 1e6, 1),

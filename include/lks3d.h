@@ -16,14 +16,18 @@
  *     (Eq. weightingfactor), plus the moving-wall term of Eq. movingwalllinkbasedclosure on B_x;
  *     the normal component B_y by anti-bounce-back to B0.
  * Populations are stored as deviations from the rest equilibrium (rho = 1, u = 0, B = (0, B0, 0))
- * in FP64 or FP32; FP32 storage computes in FP32.  Moments and residuals accumulate in FP64.
+ * in FP64, FP32, BF16 or FP16; FP64 storage computes in FP64, the others in FP32.  Moments and
+ * residuals accumulate in FP64.
  *
  * Layout: f[19][nz][ny][nx], g[3][7][nz][ny][nx] (component first), node n = (z ny + y) nx + x.
  * D3Q19 order: 0 rest; 1..6 = +x, -x, +y, -y, +z, -z; 7..18 = (1,1,0), (-1,-1,0), (1,-1,0),
  * (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).
  * D3Q7 order: the first seven of those.
  *
- * Status codes, streams, device-buffer ownership and error reporting follow lks.h.
+ * Status codes, streams, device-buffer ownership and error reporting follow lks.h.  With 16-bit
+ * storage, nx a multiple of 8 and nx <= 512 the step stages rows through shared memory with the
+ * bulk-copy engine; its waits are bounded (1 s), and a wait that ran out makes the next
+ * synchronising call (lks3_sync, lks3_moments, lks3_residual, lks3_get_state) return LKS_ETIMEOUT.
  */
 #ifndef LKS3D_H
 #define LKS3D_H
@@ -39,7 +43,7 @@ extern "C" {
 
 typedef struct lks3_params {
     int32_t nx, ny, nz;      /* nx, nz >= 1 (periodic); ny >= 2; nx*ny*nz <= 2^30 */
-    int32_t storage;         /* LKS_F64 or LKS_F32 */
+    int32_t storage;         /* lks_storage: FP64, FP32, BF16 or FP16 deviations */
     double tau_f;            /* > 1/2; nu = (tau_f - 1/2)/3 */
     double tau_m;            /* > 1/2; eta = (tau_m - 1/2)/4 on D3Q7 */
     double B0;               /* applied field along y */

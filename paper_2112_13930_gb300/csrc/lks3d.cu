@@ -26,6 +26,7 @@
 
 #include "../../include/lks3d.h"
 #include "lks_device.cuh"
+#include "lks_bulk.cuh"
 
 using lks::load_s;
 using lks::store_s;
@@ -111,75 +112,53 @@ Params3<C> make_params3(const lks3_params& p, double c_bot, double c_top, double
     return q;
 }
 
-// The fused step of one node.  S: storage type, C: compute type.
-template <typename S, typename C>
-__global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
-                                                    S* __restrict__ fout, S* __restrict__ gout, const Params3<C> p) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= p.nx) return;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int64_t N = p.N;
-    const int64_t n = ((int64_t)z * ny + y) * nx + x;
-    const bool bottom = (y == 0), top = (y == ny - 1);
-    const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};  // source x for e_x = +1, 0, -1
-    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
-    // source index of a pull along e: (x - e_x, y - e_y, z - e_z)
-    auto src = [&](int ex, int ey, int ez) -> int64_t {
-        return ((int64_t)zs[1 - ez] * ny + (y - ey)) * nx + xs[1 - ex];
-    };
-    auto ld = [](const S* ptr) -> C { return load_s<S, C>(ptr); };
+// Slot k of a node's 40 populations: k = a (0..18) for f_a, k = 19 + 7 i + a for g_a of component
+// i (x, y, z).  A slot whose direction enters the node through a wall (e_y = +1 in row 0, e_y = -1
+// in row ny-1) is filled by the loaders with the node's own stored population of the opposite
+// direction, to which wall_in3 adds the closure's terms.
+__host__ __device__ constexpr int slot_dir3(int k) { return k < 19 ? k : (k - 19) % 7; }
+__host__ __device__ constexpr int slot_plane3(int k, int a) { return k < 19 ? a : k - slot_dir3(k) + a - 19; }
 
-    C f[19], gx[7], gy[7], gz[7];
-#pragma unroll
-    for (int a = 0; a < 19; ++a) {
-        const int ey = EYa(a);
-        if ((ey == 1 && bottom) || (ey == -1 && top)) continue;  // closed below
-        f[a] = ld(fin + a * N + src(EXa(a), ey, EZa(a)));
-    }
-#pragma unroll
-    for (int a = 0; a < 7; ++a) {
-        const int ey = EYa(a);
-        if ((ey == 1 && bottom) || (ey == -1 && top)) continue;
-        const int64_t s = src(EXa(a), ey, EZa(a));
-        gx[a] = ld(gin + a * N + s);
-        gy[a] = ld(gin + (7 + a) * N + s);
-        gz[a] = ld(gin + (14 + a) * N + s);
-    }
-    // link-based walls: the node's own outgoing populations, bounced back
-    if (bottom) {  // incoming e_y = +1: 3, 7, 10, 15, 17 (D3Q19); 3 (D3Q7)
+// Link-based walls (Sec. VI; App. B.1): f by half-way bounce-back with Ladd's term on the
+// diagonals; B_x and B_z by the weighted (anti-)bounce-back with ratio r, plus the moving-wall term
+// on B_x; B_y by anti-bounce-back to B0 (deviation form: -v).
+template <typename C>
+__device__ __forceinline__ C wall_in3(const Params3<C>& p, bool bottom, bool top, int k, C v) {
+    if (bottom) {
         const Wall3<C>& w = p.bot;
-        f[3] = ld(fin + 4 * N + n);
-        f[7] = ld(fin + 8 * N + n) + w.du;
-        f[10] = ld(fin + 9 * N + n) - w.du;
-        f[15] = ld(fin + 16 * N + n);
-        f[17] = ld(fin + 18 * N + n);
-        gx[3] = w.r * ld(gin + 4 * N + n) + w.kx;
-        gy[3] = -ld(gin + (7 + 4) * N + n);
-        gz[3] = w.r * ld(gin + (14 + 4) * N + n);
+        if (k == 7) return v + w.du;
+        if (k == 10) return v - w.du;
+        if (k == 19 + 3) return w.r * v + w.kx;
+        if (k == 26 + 3) return -v;
+        if (k == 33 + 3) return w.r * v;
     }
-    if (top) {  // incoming e_y = -1: 4, 8, 9, 16, 18; 4
+    if (top) {
         const Wall3<C>& w = p.top;
-        f[4] = ld(fin + 3 * N + n);
-        f[8] = ld(fin + 7 * N + n) - w.du;
-        f[9] = ld(fin + 10 * N + n) + w.du;
-        f[16] = ld(fin + 15 * N + n);
-        f[18] = ld(fin + 17 * N + n);
-        gx[4] = w.r * ld(gin + 3 * N + n) + w.kx;
-        gy[4] = -ld(gin + (7 + 3) * N + n);
-        gz[4] = w.r * ld(gin + (14 + 3) * N + n);
+        if (k == 8) return v - w.du;
+        if (k == 9) return v + w.du;
+        if (k == 19 + 4) return w.r * v + w.kx;
+        if (k == 26 + 4) return -v;
+        if (k == 33 + 4) return w.r * v;
     }
-    // moments (a3)
+    return v;
+}
+
+// Moments, equilibria, source and collision of one node (a3-a5).  in(k) returns the streamed value
+// of slot k (wall terms included), out(k, v) takes the post-collision value of slot k; every slot is
+// read before it is written, so in and out may share storage.
+template <typename C, typename In, typename Out>
+__device__ __forceinline__ void collide3(const Params3<C>& p, In F, Out out) {
     C drho = C(0), jx = C(0), jy = C(0), jz = C(0);
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
-        drho += f[a];
-        if (EXa(a) == 1) jx += f[a];
-        if (EXa(a) == -1) jx -= f[a];
-        if (EYa(a) == 1) jy += f[a];
-        if (EYa(a) == -1) jy -= f[a];
-        if (EZa(a) == 1) jz += f[a];
-        if (EZa(a) == -1) jz -= f[a];
+        const C v = F(a);
+        drho += v;
+        if (EXa(a) == 1) jx += v;
+        if (EXa(a) == -1) jx -= v;
+        if (EYa(a) == 1) jy += v;
+        if (EYa(a) == -1) jy -= v;
+        if (EZa(a) == 1) jz += v;
+        if (EZa(a) == -1) jz -= v;
     }
     const C rho = C(1) + drho;
     const C inv = lks::recip(rho);
@@ -187,9 +166,9 @@ __global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, c
     C bx = C(0), dby = C(0), bz = C(0);
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
-        bx += gx[a];
-        dby += gy[a];
-        bz += gz[a];
+        bx += F(19 + a);
+        dby += F(26 + a);
+        bz += F(33 + a);
     }
     const C B0 = p.B0, by = B0 + dby;
     // equilibria, source and collision of f (a4-a5)
@@ -207,25 +186,215 @@ __global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, c
         const C mag = C(4.5) * w * (C(0.5) * e2 * q - eBm * eBp - q * C(1.0 / 6.0));
         const C feq = w * (drho + rho * bm1) + mag;
         const C sa = p.src * C(3) * ((C)ex - ux) * p.Fx * w * (C(1) + bm1);
-        store_s<S, C>(fout + a * N + n, p.om1f * f[a] + p.om_f * feq + sa);
+        out(a, p.om1f * F(a) + p.om_f * feq + sa);
     }
     // g, per component i: g' = (1 - w_m) dg + w_m W (dB_i +- 4 E_di), E_di = u_d B_i - B_d u_i
     const C W0 = C(0.25), W1 = C(0.125), om = p.om_m, o1 = p.om1m;
-    auto comp = [&](C* g, C dBi, C Bi, C ui, S* out) {
+    auto comp = [&](int k0, C dBi, C Bi, C ui) {
         const C Ex = ux * Bi - bx * ui, Ey = uy * Bi - by * ui, Ez = uz * Bi - bz * ui;
-        store_s<S, C>(out + 0 * N + n, o1 * g[0] + om * W0 * dBi);
-        store_s<S, C>(out + 1 * N + n, o1 * g[1] + om * W1 * (dBi + C(4) * Ex));
-        store_s<S, C>(out + 2 * N + n, o1 * g[2] + om * W1 * (dBi - C(4) * Ex));
-        store_s<S, C>(out + 3 * N + n, o1 * g[3] + om * W1 * (dBi + C(4) * Ey));
-        store_s<S, C>(out + 4 * N + n, o1 * g[4] + om * W1 * (dBi - C(4) * Ey));
-        store_s<S, C>(out + 5 * N + n, o1 * g[5] + om * W1 * (dBi + C(4) * Ez));
-        store_s<S, C>(out + 6 * N + n, o1 * g[6] + om * W1 * (dBi - C(4) * Ez));
+        out(k0 + 0, o1 * F(k0 + 0) + om * W0 * dBi);
+        out(k0 + 1, o1 * F(k0 + 1) + om * W1 * (dBi + C(4) * Ex));
+        out(k0 + 2, o1 * F(k0 + 2) + om * W1 * (dBi - C(4) * Ex));
+        out(k0 + 3, o1 * F(k0 + 3) + om * W1 * (dBi + C(4) * Ey));
+        out(k0 + 4, o1 * F(k0 + 4) + om * W1 * (dBi - C(4) * Ey));
+        out(k0 + 5, o1 * F(k0 + 5) + om * W1 * (dBi + C(4) * Ez));
+        out(k0 + 6, o1 * F(k0 + 6) + om * W1 * (dBi - C(4) * Ez));
     };
-    comp(gx, bx, bx, ux, gout);
-    comp(gy, dby, by, uy, gout + 7 * N);
-    comp(gz, bz, bz, uz, gout + 14 * N);
+    comp(19, bx, bx, ux);
+    comp(26, dby, by, uy);
+    comp(33, bz, bz, uz);
 }
 
+// The fused step of one node per thread.  S: storage type, C: compute type.
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
+                                                    S* __restrict__ fout, S* __restrict__ gout, const Params3<C> p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= p.nx) return;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int64_t N = p.N;
+    const int64_t n = ((int64_t)z * ny + y) * nx + x;
+    const bool bottom = (y == 0), top = (y == ny - 1);
+    const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};  // source x for e_x = +1, 0, -1
+    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+    // source index of a pull along e: (x - e_x, y - e_y, z - e_z)
+    auto src = [&](int ex, int ey, int ez) -> int64_t {
+        return ((int64_t)zs[1 - ez] * ny + (y - ey)) * nx + xs[1 - ex];
+    };
+    C v[40];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        const int ey = EYa(a);
+        if ((ey == 1 && bottom) || (ey == -1 && top)) continue;  // filled below
+        v[a] = load_s<S, C>(fin + a * N + src(EXa(a), ey, EZa(a)));
+    }
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+        const int ey = EYa(a);
+        if ((ey == 1 && bottom) || (ey == -1 && top)) continue;
+        const int64_t s = src(EXa(a), ey, EZa(a));
+        v[19 + a] = load_s<S, C>(gin + a * N + s);
+        v[26 + a] = load_s<S, C>(gin + (7 + a) * N + s);
+        v[33 + a] = load_s<S, C>(gin + (14 + a) * N + s);
+    }
+    // wall rows: the node's own populations of the opposite directions, with the closure's terms
+    if (bottom) {  // entering along e_y = +1: 3, 7, 10, 15, 17 (D3Q19); 3 (D3Q7)
+#pragma unroll
+        for (int k = 0; k < 40; ++k) {
+            const int a = slot_dir3(k);
+            if (EYa(a) != 1) continue;
+            v[k] = wall_in3<C>(p, true, false, k, load_s<S, C>((k < 19 ? fin : gin) + slot_plane3(k, opp(a)) * N + n));
+        }
+    }
+    if (top) {  // entering along e_y = -1: 4, 8, 9, 16, 18; 4
+#pragma unroll
+        for (int k = 0; k < 40; ++k) {
+            const int a = slot_dir3(k);
+            if (EYa(a) != -1) continue;
+            v[k] = wall_in3<C>(p, false, true, k, load_s<S, C>((k < 19 ? fin : gin) + slot_plane3(k, opp(a)) * N + n));
+        }
+    }
+    collide3<C>(p, [&](int k) -> C { return v[k]; },
+                [&](int k, C val) { store_s<S, C>((k < 19 ? fout : gout) + slot_plane3(k, slot_dir3(k)) * N + n, val); });
+}
+
+// 16-bit storage staged through shared memory by the bulk-copy engine.  A task is R whole rows
+// (y0 .. y0 + R' - 1, R' <= R, at one z; R nx <= kTaskNodes3).  For slot k the rows it pulls from,
+// (y - e_y, z - e_z) of plane a_k, are R' consecutive rows in memory, so a producer warp fetches
+// each slot with one bulk copy of R' nx elements (two where the task holds a wall row and e_y != 0:
+// that row takes the node's own row of the opposite plane), one slot per lane, into one of
+// kStages3 shared-memory stages, completing on the stage's `full` barrier.  The periodic x pull is
+// an index wrap within the staged row.  Sixteen consumer warps take one node per thread: 40 values
+// from shared memory, collide3, 40 stores; each warp then arrives on the stage's `empty` barrier,
+// which the producer waits for before it refills the stage, so kStages3 - 1 tasks' reads are in
+// flight while one is computed.  Rows must be 16-byte aligned: nx a multiple of 8, and nx <=
+// kTaskNodes3.  A wait that runs out (kWaitNs) sets *err and ends that warp's loop; the producer
+// then waits, within the same limit, for the last copies it issued to each stage before it returns.
+constexpr int kTaskNodes3 = 512;                 // consumer threads, one node each
+constexpr int kConsumerWarps3 = kTaskNodes3 / 32;
+constexpr int kThreads3 = kTaskNodes3 + 32;      // consumers + the producer warp
+constexpr int kStages3 = 5;
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
+
+inline int rows_per_task3(int nx, int ny) { return std::max(1, std::min(ny, kTaskNodes3 / nx)); }
+inline size_t staged_smem3(int nx, int ny) { return 128 + (size_t)kStages3 * 40 * rows_per_task3(nx, ny) * nx * 2; }
+
+template <typename S>
+__global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
+                                                                    S* __restrict__ fout, S* __restrict__ gout,
+                                                                    const Params3<float> p, int R, int* err) {
+    extern __shared__ __align__(128) unsigned char sm3[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm3);
+    uint64_t* empty = full + kStages3;
+    S* stage0 = reinterpret_cast<S*>(sm3 + 128);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int64_t N = p.N;
+    const int tpp = (ny + R - 1) / R;                 // tasks per z plane
+    const int64_t ntask = (int64_t)nz * tpp;
+    const int64_t G = gridDim.x, t0 = blockIdx.x;
+    const int64_t nmine = t0 < ntask ? (ntask - 1 - t0) / G + 1 : 0;  // tasks t0, t0 + G, ...
+    const size_t slot_elems = (size_t)R * nx, stage_elems = 40 * slot_elems;
+    if (tid == 0) {
+        for (int s = 0; s < kStages3; ++s) {
+            lks::mbar_init(&full[s], 1);
+            lks::mbar_init(&empty[s], kConsumerWarps3);
+        }
+        lks::mbar_init_fence();
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps3) {  // producer: lane l fetches slots l and l + 32
+        int ex2[2], ey2[2], ez2[2];
+        const S* bn[2];  // plane of the slot's own direction
+        const S* bw[2];  // plane of the opposite direction (wall rows)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int k = lane + 32 * i < 40 ? lane + 32 * i : 39;
+            const int a = slot_dir3(k);
+            ex2[i] = EXa(a);
+            ey2[i] = EYa(a);
+            ez2[i] = EZa(a);
+            const S* base = k < 19 ? fin : gin;
+            bn[i] = base + slot_plane3(k, a) * N;
+            bw[i] = base + slot_plane3(k, opp(a)) * N;
+        }
+        (void)ex2;
+        int64_t it = 0;
+        for (; it < nmine; ++it) {
+            const int s = (int)(it % kStages3);
+            const int64_t u = it / kStages3;
+            if (u > 0 && !lks::mbar_wait_bounded(&empty[s], (uint32_t)(u - 1) & 1u, kWaitNs)) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            const int64_t t = t0 + it * G;
+            const int z = (int)(t / tpp), y0 = (int)(t % tpp) * R;
+            const int Rt = min(R, ny - y0);
+            const uint32_t row_bytes = (uint32_t)nx * 2u;
+            if (lane == 0) lks::mbar_arrive_expect_tx(&full[s], 40u * (uint32_t)Rt * row_bytes);
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int k = lane + 32 * i;
+                if (k >= 40) continue;
+                const int ey = ey2[i], ez = ez2[i];
+                const int zsrc = ez == 1 ? (z == 0 ? nz - 1 : z - 1) : ez == -1 ? (z == nz - 1 ? 0 : z + 1) : z;
+                const int64_t rsrc = (int64_t)zsrc * ny, rown = (int64_t)z * ny;
+                S* dst = stage0 + (size_t)s * stage_elems + (size_t)k * slot_elems;
+                if (ey == 1 && y0 == 0) {  // row 0 is a wall row: own row 0, opposite plane
+                    lks::bulk_g2s(dst, bw[i] + rown * nx, row_bytes, &full[s]);
+                    if (Rt > 1) lks::bulk_g2s(dst + nx, bn[i] + rsrc * nx, (uint32_t)(Rt - 1) * row_bytes, &full[s]);
+                } else if (ey == -1 && y0 + Rt == ny) {  // row ny - 1 is a wall row
+                    if (Rt > 1) lks::bulk_g2s(dst, bn[i] + (rsrc + y0 + 1) * nx, (uint32_t)(Rt - 1) * row_bytes, &full[s]);
+                    lks::bulk_g2s(dst + (size_t)(Rt - 1) * nx, bw[i] + (rown + ny - 1) * nx, row_bytes, &full[s]);
+                } else {
+                    lks::bulk_g2s(dst, bn[i] + (rsrc + y0 - ey) * nx, (uint32_t)Rt * row_bytes, &full[s]);
+                }
+            }
+        }
+        // no copy may be left in flight into this block's shared memory: wait for the last phase
+        // issued to each stage (already complete unless a consumer gave up)
+        for (int s = 0; s < kStages3; ++s) {
+            if (it <= s) continue;
+            const int64_t u_last = (it - 1 - s) / kStages3;
+            if (!lks::mbar_wait_bounded(&full[s], (uint32_t)u_last & 1u, kWaitNs) && lane == 0) atomicExch(err, 1);
+        }
+        return;
+    }
+
+    // consumers: thread tid is node x = tid % nx of task row j = tid / nx
+    const int j = tid / nx, x = tid - j * nx;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    for (int64_t it = 0; it < nmine; ++it) {
+        const int s = (int)(it % kStages3);
+        if (!lks::mbar_wait_bounded(&full[s], (uint32_t)(it / kStages3) & 1u, kWaitNs)) {
+            atomicExch(err, 1);
+            break;
+        }
+        const int64_t t = t0 + it * G;
+        const int z = (int)(t / tpp), y0 = (int)(t % tpp) * R;
+        const int y = y0 + j;
+        if (j < R && y < ny) {
+            const bool bottom = (y == 0), top = (y == ny - 1);
+            const S* st = stage0 + (size_t)s * stage_elems + (size_t)j * nx;
+            auto in = [&](int k) -> float {
+                const int a = slot_dir3(k), ex = EXa(a), ey = EYa(a);
+                const bool wall = (ey == 1 && bottom) || (ey == -1 && top);
+                const int xs = (wall || ex == 0) ? x : (ex == 1 ? xm : xp);
+                const float v = lks::Loader<S, float, false>::ld(st + k * slot_elems + xs);
+                return wall_in3<float>(p, bottom, top, k, v);
+            };
+            const int64_t n = ((int64_t)z * ny + y) * nx + x;
+            collide3<float>(p, in, [&](int k, float v) {
+                store_s<S, float>((k < 19 ? fout : gout) + slot_plane3(k, slot_dir3(k)) * N + n, v);
+            });
+        }
+        __syncwarp();
+        if (lane == 0) lks::mbar_arrive(&empty[s]);
+    }
+}
 
 // FP64 moments of the stored state of node n: rho = 1 + sum d, rho u = sum d e - F/2, B.
 template <typename S>
@@ -393,7 +562,7 @@ const char* validate3(const lks3_params* p) {
     if (p->ny < 2) return "ny must be >= 2";
     if (p->ny > 65535 || p->nz > 65535) return "ny and nz must be <= 65535";
     if ((int64_t)p->nx * p->ny * p->nz > ((int64_t)1 << 30)) return "nx*ny*nz exceeds 2^30 nodes";
-    if (p->storage != LKS_F64 && p->storage != LKS_F32) return "storage must be LKS_F64 or LKS_F32";
+    if (p->storage < LKS_F64 || p->storage > LKS_F16_DEV) return "storage must be one of lks_storage";
     if (!(p->tau_f > 0.5) || !isfinite(p->tau_f)) return "tau_f must be finite and > 1/2";
     if (!(p->tau_m > 0.5) || !isfinite(p->tau_m)) return "tau_m must be finite and > 1/2";
     if (!isfinite(p->B0) || !isfinite(p->Fx)) return "B0 and Fx must be finite";
@@ -401,13 +570,13 @@ const char* validate3(const lks3_params* p) {
 }
 
 struct Layout3 {
-    size_t f_bytes, g_bytes, off_f[2], off_g[2], off_snap, off_partial, off_out, off_prof, off_rest, total;
+    size_t f_bytes, g_bytes, off_f[2], off_g[2], off_snap, off_partial, off_out, off_prof, off_rest, off_flag, total;
 };
 
 Layout3 layout3(const lks3_params* p) {
     Layout3 L;
     const size_t N = (size_t)p->nx * p->ny * p->nz;
-    const size_t sb = p->storage == LKS_F64 ? 8 : 4;
+    const size_t sb = p->storage == LKS_F64 ? 8 : (p->storage == LKS_F32 ? 4 : 2);
     L.f_bytes = align3(19 * N * sb);
     L.g_bytes = align3(21 * N * sb);
     size_t o = 0;
@@ -427,6 +596,8 @@ Layout3 layout3(const lks3_params* p) {
     o += align3(7 * (size_t)p->ny * sizeof(double));
     L.off_rest = o;
     o += align3(19 * sizeof(double));
+    L.off_flag = o;  // set by a staged step whose stage wait ran out
+    o += align3(sizeof(int));
     L.total = o;
     return L;
 }
@@ -443,6 +614,9 @@ struct lks3_handle {
     void* g[2] = {nullptr, nullptr};
     int cur = 0;
     double *snap = nullptr, *partial = nullptr, *dout = nullptr, *prof = nullptr, *rest = nullptr;
+    int* flag = nullptr;
+    bool staged = false;       // 16-bit storage with nx % 8 == 0: step3_staged_kernel
+    unsigned staged_grid = 0;  // resident blocks of it on the device
     double* host4 = nullptr;  // pinned
     double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
     int64_t steps = 0;
@@ -463,34 +637,99 @@ lks_status cuda3(lks3_handle* h, cudaError_t e, const char* where) {
     return fail3(h, LKS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// After a synchronisation: LKS_ETIMEOUT if a staged step gave up waiting for its copies.
+lks_status flag_check3(lks3_handle* h, const char* where) {
+    if (!h->staged) return LKS_OK;
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, h->flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda3(h, e, where);
+    if (v) return fail3(h, LKS_ETIMEOUT, std::string(where) + ": a staged step's shared-memory wait ran out");
+    return LKS_OK;
+}
+
 unsigned grid_for(int64_t N) { return (unsigned)std::min<int64_t>((N + 255) / 256, 152 * 16); }
+
+// Storage type S and compute type C of a handle.
+#define LKS3_DISPATCH(storage, ...)      \
+    do {                                 \
+        if ((storage) == LKS_F64) {      \
+            typedef double S;            \
+            typedef double C;            \
+            __VA_ARGS__;                    \
+        } else if ((storage) == LKS_F32) { \
+            typedef float S;             \
+            typedef float C;             \
+            __VA_ARGS__;                    \
+        } else if ((storage) == LKS_BF16_DEV) { \
+            typedef __nv_bfloat16 S;     \
+            typedef float C;             \
+            __VA_ARGS__;                    \
+        } else {                         \
+            typedef __half S;            \
+            typedef float C;             \
+            __VA_ARGS__;                    \
+        }                                \
+    } while (0)
+
+template <typename S>
+void launch_staged3(lks3_handle* h, int src) {
+    const lks3_params& p = h->p;
+    const int R = rows_per_task3(p.nx, p.ny);
+    const int64_t ntask = (int64_t)p.nz * ((p.ny + R - 1) / R);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntask, h->staged_grid);
+    const Params3<float> q = make_params3<float>(p, h->c_bot, h->c_top, h->u_bot, h->u_top);
+    step3_staged_kernel<S><<<grid, kThreads3, staged_smem3(p.nx, p.ny), h->stream>>>(
+        (const S*)h->f[src], (const S*)h->g[src], (S*)h->f[src ^ 1], (S*)h->g[src ^ 1], q, R, h->flag);
+}
+
+// Opt the staged kernel of the handle's storage into its shared memory and size its grid.
+cudaError_t prepare_staged3(lks3_handle* h) {
+    int dev = 0, sms = 0, occ = 0;
+    const size_t smem = staged_smem3(h->p.nx, h->p.ny);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (h->p.storage == LKS_BF16_DEV) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step3_staged_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step3_staged_kernel<__nv_bfloat16>, kThreads3, smem);
+    } else {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step3_staged_kernel<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step3_staged_kernel<__half>, kThreads3, smem);
+    }
+    if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
+    h->staged_grid = (unsigned)(sms * occ);
+    return e;
+}
 
 cudaError_t launch_step3(lks3_handle* h) {
     const lks3_params& p = h->p;
     const dim3 grid((p.nx + 255) / 256, p.ny, p.nz);
     const int src = h->cur;
-    if (p.storage == LKS_F64) {
-        const Params3<double> q = make_params3<double>(p, h->c_bot, h->c_top, h->u_bot, h->u_top);
-        step3_kernel<double, double><<<grid, 256, 0, h->stream>>>((const double*)h->f[src], (const double*)h->g[src],
-                                                                  (double*)h->f[src ^ 1], (double*)h->g[src ^ 1], q);
-    } else {
-        const Params3<float> q = make_params3<float>(p, h->c_bot, h->c_top, h->u_bot, h->u_top);
-        step3_kernel<float, float><<<grid, 256, 0, h->stream>>>((const float*)h->f[src], (const float*)h->g[src],
-                                                                (float*)h->f[src ^ 1], (float*)h->g[src ^ 1], q);
+    if (h->staged) {
+        if (p.storage == LKS_BF16_DEV)
+            launch_staged3<__nv_bfloat16>(h, src);
+        else
+            launch_staged3<__half>(h, src);
+        return cudaGetLastError();
     }
+    LKS3_DISPATCH(p.storage, {
+        const Params3<C> q = make_params3<C>(p, h->c_bot, h->c_top, h->u_bot, h->u_top);
+        step3_kernel<S, C><<<grid, 256, 0, h->stream>>>((const S*)h->f[src], (const S*)h->g[src], (S*)h->f[src ^ 1],
+                                                        (S*)h->g[src ^ 1], q);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_snapshot3(lks3_handle* h) {
     const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
-    if (h->p.storage == LKS_F64)
-        residual3_partial<double><<<kRedBlocks, 256, 0, h->stream>>>((const double*)h->f[h->cur],
-                                                                     (const double*)h->g[h->cur], N, h->p.B0, h->p.Fx,
-                                                                     h->snap, h->partial);
-    else
-        residual3_partial<float><<<kRedBlocks, 256, 0, h->stream>>>((const float*)h->f[h->cur],
-                                                                    (const float*)h->g[h->cur], N, h->p.B0, h->p.Fx,
-                                                                    h->snap, h->partial);
+    LKS3_DISPATCH(h->p.storage,
+                  (residual3_partial<S><<<kRedBlocks, 256, 0, h->stream>>>((const S*)h->f[h->cur], (const S*)h->g[h->cur],
+                                                                           N, h->p.B0, h->p.Fx, h->snap, h->partial)));
     return cudaGetLastError();
 }
 
@@ -537,12 +776,16 @@ lks_status lks3_create(const lks3_params* p, lks3_handle** out) {
     h->dout = (double*)(h->base + h->L.off_out);
     h->prof = (double*)(h->base + h->L.off_prof);
     h->rest = (double*)(h->base + h->L.off_rest);
+    h->flag = (int*)(h->base + h->L.off_flag);
+    h->staged = (p->storage == LKS_BF16_DEV || p->storage == LKS_F16_DEV) && p->nx % 8 == 0 && p->nx <= kTaskNodes3;
     double rest[19];
     for (int a = 0; a < 19; ++a) rest[a] = f_rest(a, p->B0);
     e = cudaHostAlloc((void**)&h->host4, 4 * sizeof(double), cudaHostAllocDefault);
     // rest state: all deviations zero
     if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, h->L.f_bytes, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->g[0], 0, h->L.g_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess && h->staged) e = prepare_staged3(h);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->rest, rest, sizeof(rest), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = launch_snapshot3(h);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // rest[] is on this stack frame
@@ -586,14 +829,8 @@ lks_status lks3_moments(lks3_handle* h, int what, double* host_out) {
     const int64_t N = (int64_t)p.nx * p.ny * p.nz;
     cudaError_t e;
     if (what == LKS_MOMENTS_PROFILES) {
-        if (p.storage == LKS_F64)
-            profiles3_kernel<double><<<p.ny, 256, 0, h->stream>>>((const double*)h->f[h->cur],
-                                                                  (const double*)h->g[h->cur], p.nx, p.ny, p.nz, p.B0,
-                                                                  p.Fx, h->prof);
-        else
-            profiles3_kernel<float><<<p.ny, 256, 0, h->stream>>>((const float*)h->f[h->cur],
-                                                                 (const float*)h->g[h->cur], p.nx, p.ny, p.nz, p.B0,
-                                                                 p.Fx, h->prof);
+        LKS3_DISPATCH(p.storage, (profiles3_kernel<S><<<p.ny, 256, 0, h->stream>>>(
+                                     (const S*)h->f[h->cur], (const S*)h->g[h->cur], p.nx, p.ny, p.nz, p.B0, p.Fx, h->prof)));
         e = cudaGetLastError();
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(host_out, h->prof, 7 * (size_t)p.ny * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -604,12 +841,8 @@ lks_status lks3_moments(lks3_handle* h, int what, double* host_out) {
             cudaGetLastError();
             return fail3(h, LKS_ENOMEM, "cudaMalloc of the moment staging buffer failed");
         }
-        if (p.storage == LKS_F64)
-            moments3_kernel<double><<<grid_for(N), 256, 0, h->stream>>>((const double*)h->f[h->cur],
-                                                                        (const double*)h->g[h->cur], N, p.B0, p.Fx, tmp);
-        else
-            moments3_kernel<float><<<grid_for(N), 256, 0, h->stream>>>((const float*)h->f[h->cur],
-                                                                       (const float*)h->g[h->cur], N, p.B0, p.Fx, tmp);
+        LKS3_DISPATCH(p.storage, (moments3_kernel<S><<<grid_for(N), 256, 0, h->stream>>>(
+                                     (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, p.B0, p.Fx, tmp)));
         e = cudaGetLastError();
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(host_out, tmp, 7 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -620,7 +853,7 @@ lks_status lks3_moments(lks3_handle* h, int what, double* host_out) {
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda3(h, e, "lks3_moments");
-    return LKS_OK;
+    return flag_check3(h, "lks3_moments");
 }
 
 lks_status lks3_residual(lks3_handle* h, double* r_u, double* r_b) {
@@ -633,6 +866,7 @@ lks_status lks3_residual(lks3_handle* h, double* r_u, double* r_b) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->host4, h->dout, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda3(h, e, "lks3_residual");
+    if (lks_status fs = flag_check3(h, "lks3_residual")) return fs;
     const double* s = h->host4;
     const double ru = s[1] > 1e-30 * 1e-30 ? sqrt(s[0] / s[1]) : 0.0;
     const double rb = s[3] > 1e-30 * 1e-30 ? sqrt(s[2] / s[3]) : 0.0;
@@ -678,12 +912,9 @@ lks_status lks3_get_state(lks3_handle* h, double* host_f, double* host_g) {
         cudaGetLastError();
         return fail3(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
     }
-    if (h->p.storage == LKS_F64)
-        to_abs3_kernel<double, double><<<grid_for(N), 256, 0, h->stream>>>(
-            (const double*)h->f[h->cur], (const double*)h->g[h->cur], N, h->rest, h->p.B0, tmp, tmp + 19 * N);
-    else
-        to_abs3_kernel<float, float><<<grid_for(N), 256, 0, h->stream>>>(
-            (const float*)h->f[h->cur], (const float*)h->g[h->cur], N, h->rest, h->p.B0, tmp, tmp + 19 * N);
+    LKS3_DISPATCH(h->p.storage, (to_abs3_kernel<S, C><<<grid_for(N), 256, 0, h->stream>>>(
+                                    (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, h->rest, h->p.B0, tmp,
+                                    tmp + 19 * N)));
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, 19 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess)
@@ -691,7 +922,7 @@ lks_status lks3_get_state(lks3_handle* h, double* host_f, double* host_g) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda3(h, e, "lks3_get_state");
-    return LKS_OK;
+    return flag_check3(h, "lks3_get_state");
 }
 
 lks_status lks3_set_state(lks3_handle* h, const double* host_f, const double* host_g) {
@@ -708,12 +939,8 @@ lks_status lks3_set_state(lks3_handle* h, const double* host_f, const double* ho
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tmp + 19 * N, host_g, 21 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) {
-        if (h->p.storage == LKS_F64)
-            from_abs3_kernel<double, double><<<grid_for(N), 256, 0, h->stream>>>(
-                tmp, tmp + 19 * N, N, h->rest, h->p.B0, (double*)h->f[h->cur], (double*)h->g[h->cur]);
-        else
-            from_abs3_kernel<float, float><<<grid_for(N), 256, 0, h->stream>>>(
-                tmp, tmp + 19 * N, N, h->rest, h->p.B0, (float*)h->f[h->cur], (float*)h->g[h->cur]);
+        LKS3_DISPATCH(h->p.storage, (from_abs3_kernel<S, C><<<grid_for(N), 256, 0, h->stream>>>(
+                                        tmp, tmp + 19 * N, N, h->rest, h->p.B0, (S*)h->f[h->cur], (S*)h->g[h->cur])));
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = launch_snapshot3(h);
@@ -728,7 +955,7 @@ lks_status lks3_sync(lks3_handle* h) {
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda3(h, e, "lks3_sync");
-    return LKS_OK;
+    return flag_check3(h, "lks3_sync");
 }
 
 lks_status lks3_destroy(lks3_handle* h) {

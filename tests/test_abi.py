@@ -165,7 +165,7 @@ def test_every_3d_symbol_is_exported(lib):
     (dict(nx=4, ny=1, nz=1), False),
     (dict(nx=0, ny=8, nz=4), False),
     (dict(nx=4, ny=8, nz=0), False),
-    (dict(nx=4, ny=8, nz=4, storage="bf16"), False),
+    (dict(nx=4, ny=8, nz=4, storage="bf16"), True),
     (dict(nx=4, ny=8, nz=4, tau_m=0.5), False),
     (dict(nx=1024, ny=1024, nz=1025), False),       # above 2^30 nodes
 ])

@@ -4,8 +4,10 @@ FP64 storage: moments per field within 1e-11 of max|field| and populations withi
 largest deviation from rest, after 1 and after 40 steps from the same perturbed state, on lattices
 with a ragged x block (300 = 256 + 44), nx = 1, ny = 2 (both rows are wall rows) and every wall
 setting (insulating, finite, perfectly conducting, moving).  FP32 storage: within 1e-4 of the field
-scale after 40 steps (FP32 rounding of deviations ~1e-3 over a few tens of steps).  Steady state:
-closed-form Hartmann profiles with the D3Q7 diffusivity."""
+scale after 40 steps (FP32 rounding of deviations ~1e-3 over a few tens of steps).  FP32, BF16 and
+FP16 storage after one step: populations within 8 u_s of the largest deviation from rest (u_s the
+storage's unit roundoff), and FP16 over 2000 steps of a Hartmann flow within the bounds of the
+two-dimensional channel.  Steady state: closed-form Hartmann profiles with the D3Q7 diffusivity."""
 import math
 
 import numpy as np
@@ -118,4 +120,70 @@ def test_steady_hartmann_profiles(l3, ha, c):
     u, b = gpu.profiles()
     ua, ba = an.hartmann_profiles(gpu.y(), a, ha, c, fx, tau, tm2)
     assert an.rel_l2(u, ua) < 5e-3 and an.rel_l2(b, ba) < 5e-3
+    gpu.close()
+
+
+# One step of a 16-bit (or FP32) handle against the FP64 oracle from the same state: the stored
+# deviations carry a rounding error <= u_s |d| each, the collision maps them with coefficients of
+# magnitude <= 1 (|1 - 1/tau_f| = 0.25, |1 - 1/tau_m| = 0.43, equilibrium weights summing to 1), the
+# FP32 moments, equilibria and wall terms add a few roundings of that size and the result is
+# rounded once more: max|d_gpu - d_oracle| <= 8 u_s max|d|.
+ONE_STEP = {"f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+# 16-bit storage with nx a multiple of 8 and nx <= 512 is staged through shared memory in tasks of
+# R = min(ny, 512 // nx) whole rows: nx = 8 (R = ny: both wall rows in one task), 16 with nz = 1
+# (the z pull wraps onto the same plane), 128 with ny = 10 (R = 4, a ragged last task of 2 rows),
+# 264 (R = 1) and 512 (the widest staged rows).  Other nx run one node per thread: 37, 300, 2, 4,
+# 518 and 520 (wider than a task).
+STORAGE_CASES = CASES[:2] + [
+    (2, 5, 3, (0.2, 1.0), (0.01, -0.02)),
+    (518, 3, 2, (math.inf, 0.0), (0.0, 0.03)),
+    (4, 2, 7, (0.5, 0.5), (0.0, -0.03)),
+    (8, 4, 3, (0.3, 2.0), (0.02, 0.0)),
+    (264, 3, 2, (1.0, math.inf), (0.0, 0.04)),
+    (16, 5, 1, (0.0, 0.7), (-0.03, 0.02)),
+    (128, 10, 3, (0.4, 0.4), (0.01, 0.02)),
+    (512, 3, 2, (2.0, 0.0), (0.0, -0.01)),
+    (520, 2, 2, (0.1, 0.9), (0.02, 0.0)),
+]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("case", STORAGE_CASES)
+def test_reduced_precision_one_step(l3, case, storage):
+    nx, ny, nz, c, u = case
+    o, gpu, f_rest, g_rest = _pair(l3, nx, ny, nz, c, u, storage, seed=5)
+    o.step(1)
+    gpu.step(1)
+    fg, gg = gpu.get_state()
+    df = float(np.max(np.abs(o.f - f_rest)))
+    dg = float(np.max(np.abs(o.g - g_rest)))
+    assert np.max(np.abs(fg - o.f)) <= 8 * ONE_STEP[storage] * df
+    assert np.max(np.abs(gg - o.g)) <= 8 * ONE_STEP[storage] * dg
+    gpu.close()
+
+
+# Long run: each step adds a relative error ~u_s to every stored deviation; the error of u_x and
+# B_x behaves like a random walk damped on the diffusive time a^2/nu, plus the loss of sub-ulp
+# increments.  FP16 bounds relative to max|field| as in the two-dimensional channel: 1e-1 for u_x,
+# 5e-2 for B_x; FP32 1e-4 for both.
+@pytest.mark.parametrize("storage,bounds", [("f32", (1e-4, 1e-4)), ("f16", (1e-1, 5e-2))])
+def test_reduced_precision_long_run(l3, storage, bounds):
+    nx, ny, nz, ha, c, tau = 8, 33, 2, 10.0, 0.5, 0.8
+    a = ny / 2
+    tm2 = 0.5 + 0.75 * (tau - 0.5)
+    b0 = an.b0_from_ha(ha, a, tau, tm2)
+    fx = an.force_for_centre_speed(0.01, ha, c, a, tau)
+    o = oracle.Oracle3D(nx, ny, nz, tau, tau, b0, fx, c, c, 0.0, 0.0)
+    rng = np.random.default_rng(11)
+    o.f += 1e-3 * rng.uniform(-1, 1, o.f.shape) * np.abs(o.f)
+    gpu = l3.Lattice3D(nx, ny, nz, tau, tau, b0, fx, storage)
+    gpu.set_walls(c, c)
+    gpu.set_state(o.f, o.g)
+    o.step(2000)
+    gpu.step(2000)
+    mo, mg = o.moments(), gpu.moments()
+    assert np.max(np.abs(mg[1] - mo[1])) <= bounds[0] * np.max(np.abs(mo[1]))
+    assert np.max(np.abs(mg[4] - mo[4])) <= bounds[1] * np.max(np.abs(mo[4]))
     gpu.close()
