@@ -27,6 +27,8 @@
 #include "../../include/lks3d.h"
 #include "lks_device.cuh"
 #include "lks_bulk.cuh"
+#include "lks_packed.cuh"
+#include "lks_vec.cuh"
 
 using lks::load_s;
 using lks::store_s;
@@ -70,8 +72,10 @@ template <typename C>
 struct Params3 {
     int32_t nx, ny, nz;
     int64_t N;
-    C om_f, om1f, om_m, om1m, src;  // 1/tau_f, 1 - 1/tau_f, 1/tau_m, 1 - 1/tau_m, 1 - 1/(2 tau_f)
-    C B0, Fx;
+    C om_f, om1f, om_m, om1m;  // 1/tau_f, 1 - 1/tau_f, 1/tau_m, 1 - 1/tau_m
+    C B0, Fx, hFx, twoB0;      // hFx = F/2, twoB0 = 2 B0
+    C Ks[3];                   // (1 - 1/(2 tau_f)) 3 F w for |e|^2 = 0, 1, 2 (source term)
+    C omW0, omW1, omW1x4;      // w_m W_0, w_m W, 4 w_m W (D3Q7)
     Wall3<C> bot, top;
 };
 
@@ -86,9 +90,17 @@ Params3<C> make_params3(const lks3_params& p, double c_bot, double c_top, double
     q.om1f = (C)(1.0 - 1.0 / p.tau_f);
     q.om_m = (C)(1.0 / p.tau_m);
     q.om1m = (C)(1.0 - 1.0 / p.tau_m);
-    q.src = (C)(1.0 - 0.5 / p.tau_f);
     q.B0 = (C)p.B0;
     q.Fx = (C)p.Fx;
+    q.hFx = (C)(0.5 * p.Fx);
+    q.twoB0 = (C)(2.0 * p.B0);
+    const double src = 1.0 - 0.5 / p.tau_f;
+    q.Ks[0] = (C)(src * 3.0 * p.Fx / 3.0);
+    q.Ks[1] = (C)(src * 3.0 * p.Fx / 18.0);
+    q.Ks[2] = (C)(src * 3.0 * p.Fx / 36.0);
+    q.omW0 = (C)(0.25 / p.tau_m);
+    q.omW1 = (C)(0.125 / p.tau_m);
+    q.omW1x4 = (C)(0.5 / p.tau_m);
     const double a = 0.5 * p.ny;
     auto wall = [&](double c, double U, double ey) {
         Wall3<C> w;
@@ -121,88 +133,145 @@ __host__ __device__ constexpr int slot_plane3(int k, int a) { return k < 19 ? a 
 
 // Link-based walls (Sec. VI; App. B.1): f by half-way bounce-back with Ladd's term on the
 // diagonals; B_x and B_z by the weighted (anti-)bounce-back with ratio r, plus the moving-wall term
-// on B_x; B_y by anti-bounce-back to B0 (deviation form: -v).
-template <typename C>
-__device__ __forceinline__ C wall_in3(const Params3<C>& p, bool bottom, bool top, int k, C v) {
+// on B_x; B_y by anti-bounce-back to B0 (deviation form: -v).  V: one node (C) or a pair (float2).
+template <typename V, typename C>
+__device__ __forceinline__ V wall_in3(const Params3<C>& p, bool bottom, bool top, int k, V v) {
+    using namespace lks;
+    typedef VecOf<V> K;
     if (bottom) {
         const Wall3<C>& w = p.bot;
-        if (k == 7) return v + w.du;
-        if (k == 10) return v - w.du;
-        if (k == 19 + 3) return w.r * v + w.kx;
-        if (k == 26 + 3) return -v;
-        if (k == 33 + 3) return w.r * v;
+        if (k == 7) return vadd(v, K::set(w.du));
+        if (k == 10) return vsub(v, K::set(w.du));
+        if (k == 19 + 3) return vfma(K::set(w.r), v, K::set(w.kx));
+        if (k == 26 + 3) return vneg(v);
+        if (k == 33 + 3) return vmul(K::set(w.r), v);
     }
     if (top) {
         const Wall3<C>& w = p.top;
-        if (k == 8) return v - w.du;
-        if (k == 9) return v + w.du;
-        if (k == 19 + 4) return w.r * v + w.kx;
-        if (k == 26 + 4) return -v;
-        if (k == 33 + 4) return w.r * v;
+        if (k == 8) return vsub(v, K::set(w.du));
+        if (k == 9) return vadd(v, K::set(w.du));
+        if (k == 19 + 4) return vfma(K::set(w.r), v, K::set(w.kx));
+        if (k == 26 + 4) return vneg(v);
+        if (k == 33 + 4) return vmul(K::set(w.r), v);
     }
     return v;
 }
 
-// Moments, equilibria, source and collision of one node (a3-a5).  in(k) returns the streamed value
-// of slot k (wall terms included), out(k, v) takes the post-collision value of slot k; every slot is
-// read before it is written, so in and out may share storage.
-template <typename C, typename In, typename Out>
+// e_a . (vx, vy, vz) for a != 0: the signed sum of the nonzero components, in the order x, y, z.
+template <typename V>
+__device__ __forceinline__ V edot3(int a, V vx, V vy, V vz) {
+    using namespace lks;
+    const int e[3] = {EXa(a), EYa(a), EZa(a)};
+    const V c[3] = {vx, vy, vz};
+    V r = c[0];
+    bool first = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (e[d] == 0) continue;
+        r = first ? (e[d] > 0 ? c[d] : vneg(c[d])) : (e[d] > 0 ? vadd(r, c[d]) : vsub(r, c[d]));
+        first = false;
+    }
+    return r;
+}
+
+// Moments, equilibria, source and collision of one node or of a pair of nodes (a3-a5).  F(k) returns
+// the streamed value of slot k (wall terms included), out(k, v) takes the post-collision value of
+// slot k.  With the rest (rho = 1, u = 0, B = (0, B0, 0)) subtracted, per direction a of D3Q19
+//   f^eq_a - f^rest_a = w_a (drho + rho b_a) + 4.5 w_a [ (|e_a|^2/2 - 1/6) q - (e_a.B)^2 + (e_a.B_rest)^2 ]
+// with b_a = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2 and q = |B|^2 - B0^2; the source is
+// (1 - 1/(2 tau_f)) 3 w_a (e_a - u).F (1 + b_a); and per component i of B on D3Q7
+//   g'_ai = (1 - w_m) g_ai + w_m W_a (dB_i + 4 e_ad E_di),  E_di = u_d B_i - B_d u_i  (E_ii = 0).
+template <typename V, typename C, typename In, typename Out>
 __device__ __forceinline__ void collide3(const Params3<C>& p, In F, Out out) {
-    C drho = C(0), jx = C(0), jy = C(0), jz = C(0);
+    using namespace lks;
+    typedef VecOf<V> K;
+    V f[19];
 #pragma unroll
-    for (int a = 0; a < 19; ++a) {
-        const C v = F(a);
-        drho += v;
-        if (EXa(a) == 1) jx += v;
-        if (EXa(a) == -1) jx -= v;
-        if (EYa(a) == 1) jy += v;
-        if (EYa(a) == -1) jy -= v;
-        if (EZa(a) == 1) jz += v;
-        if (EZa(a) == -1) jz -= v;
-    }
-    const C rho = C(1) + drho;
-    const C inv = lks::recip(rho);
-    const C ux = (jx + C(0.5) * p.Fx) * inv, uy = jy * inv, uz = jz * inv;
-    C bx = C(0), dby = C(0), bz = C(0);
+    for (int a = 0; a < 19; ++a) f[a] = F(a);
+    V drho = f[0];
 #pragma unroll
-    for (int a = 0; a < 7; ++a) {
-        bx += F(19 + a);
-        dby += F(26 + a);
-        bz += F(33 + a);
-    }
-    const C B0 = p.B0, by = B0 + dby;
-    // equilibria, source and collision of f (a4-a5)
-    const C q = bx * bx + bz * bz + dby * (C(2) * B0 + dby);  // |B|^2 - B0^2
-    const C usq = ux * ux + uy * uy + uz * uz;
+    for (int a = 1; a < 19; ++a) drho = vadd(drho, f[a]);
+    auto jsum = [&](int d) -> V {
+        V pos = f[0], neg = f[0];
+        bool pf = true, nf = true;
 #pragma unroll
-    for (int a = 0; a < 19; ++a) {
-        const int ex = EXa(a), ey = EYa(a), ez = EZa(a);
-        const C w = (C)w19(a);
-        const C e2 = (C)(ex * ex + ey * ey + ez * ez);
-        const C eu = (C)ex * ux + (C)ey * uy + (C)ez * uz;
-        const C eBm = (C)ex * bx + (C)ey * dby + (C)ez * bz;  // e.B - e_y B0
-        const C eBp = eBm + (C)(2 * ey) * B0;                 // e.B + e_y B0
-        const C bm1 = (C(3) + C(4.5) * eu) * eu - C(1.5) * usq;
-        const C mag = C(4.5) * w * (C(0.5) * e2 * q - eBm * eBp - q * C(1.0 / 6.0));
-        const C feq = w * (drho + rho * bm1) + mag;
-        const C sa = p.src * C(3) * ((C)ex - ux) * p.Fx * w * (C(1) + bm1);
-        out(a, p.om1f * F(a) + p.om_f * feq + sa);
-    }
-    // g, per component i: g' = (1 - w_m) dg + w_m W (dB_i +- 4 E_di), E_di = u_d B_i - B_d u_i
-    const C W0 = C(0.25), W1 = C(0.125), om = p.om_m, o1 = p.om1m;
-    auto comp = [&](int k0, C dBi, C Bi, C ui) {
-        const C Ex = ux * Bi - bx * ui, Ey = uy * Bi - by * ui, Ez = uz * Bi - bz * ui;
-        out(k0 + 0, o1 * F(k0 + 0) + om * W0 * dBi);
-        out(k0 + 1, o1 * F(k0 + 1) + om * W1 * (dBi + C(4) * Ex));
-        out(k0 + 2, o1 * F(k0 + 2) + om * W1 * (dBi - C(4) * Ex));
-        out(k0 + 3, o1 * F(k0 + 3) + om * W1 * (dBi + C(4) * Ey));
-        out(k0 + 4, o1 * F(k0 + 4) + om * W1 * (dBi - C(4) * Ey));
-        out(k0 + 5, o1 * F(k0 + 5) + om * W1 * (dBi + C(4) * Ez));
-        out(k0 + 6, o1 * F(k0 + 6) + om * W1 * (dBi - C(4) * Ez));
+        for (int a = 1; a < 19; ++a) {
+            const int e = d == 0 ? EXa(a) : (d == 1 ? EYa(a) : EZa(a));
+            if (e == 1) {
+                pos = pf ? f[a] : vadd(pos, f[a]);
+                pf = false;
+            }
+            if (e == -1) {
+                neg = nf ? f[a] : vadd(neg, f[a]);
+                nf = false;
+            }
+        }
+        return vsub(pos, neg);
     };
-    comp(19, bx, bx, ux);
-    comp(26, dby, by, uy);
-    comp(33, bz, bz, uz);
+    const V jx = jsum(0), jy = jsum(1), jz = jsum(2);
+    const V rho = vadd(K::set(C(1)), drho);
+    const V inv = vrecip(rho);
+    const V ux = vmul(vadd(jx, K::set(p.hFx)), inv), uy = vmul(jy, inv), uz = vmul(jz, inv);
+    V g[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) g[k] = F(19 + k);
+    V bx = g[0], dby = g[7], bz = g[14];
+#pragma unroll
+    for (int a = 1; a < 7; ++a) {
+        bx = vadd(bx, g[a]);
+        dby = vadd(dby, g[7 + a]);
+        bz = vadd(bz, g[14 + a]);
+    }
+    const V by = vadd(K::set(p.B0), dby);
+    const V q = vfma(bx, bx, vfma(bz, bz, vmul(dby, vadd(K::set(p.twoB0), dby))));  // |B|^2 - B0^2
+    const V usq = vfma(ux, ux, vfma(uy, uy, vmul(uz, uz)));
+    const V us15 = vmul(K::set(C(1.5)), usq);
+    // 4.5 w (|e|^2/2 - 1/6) q for |e|^2 = 0, 1, 2
+    const V cq0 = vmul(K::set(C(-0.25)), q), cq1 = vmul(K::set(C(1.0 / 12.0)), q), cq2 = vmul(K::set(C(5.0 / 48.0)), q);
+    const V om1f = K::set(p.om1f), omf = K::set(p.om_f), one = K::set(C(1));
+#pragma unroll
+    for (int a = 0; a < 19; ++a) {
+        const int ex = EXa(a), ey = EYa(a);
+        const int e2 = ex * ex + ey * ey + EZa(a) * EZa(a);
+        V bm1, mag;
+        if (a == 0) {
+            bm1 = vneg(us15);
+            mag = cq0;
+        } else {
+            const V eu = edot3<V>(a, ux, uy, uz);
+            const V eBm = edot3<V>(a, bx, dby, bz);  // e.B - e_y B0
+            const V eBp = ey == 0 ? eBm : vadd(eBm, K::set(ey > 0 ? p.twoB0 : -p.twoB0));  // e.B + e_y B0
+            bm1 = vsub(vmul(vfma(K::set(C(4.5)), eu, K::set(C(3))), eu), us15);
+            mag = vfma(K::set(C(e2 == 1 ? -0.25 : -0.125)), vmul(eBm, eBp), e2 == 1 ? cq1 : cq2);
+        }
+        const C w = (C)w19(a);
+        const V feq = vfma(K::set(w), vfma(rho, bm1, drho), mag);
+        const V exu = ex == 0 ? vneg(ux) : vsub(K::set(C(ex)), ux);
+        const V sa = vmul(vmul(K::set(p.Ks[e2]), exu), vadd(one, bm1));
+        out(a, vfma(om1f, f[a], vfma(omf, feq, sa)));
+    }
+    const V o1 = K::set(p.om1m), ow0 = K::set(p.omW0), ow1 = K::set(p.omW1);
+    const V u[3] = {ux, uy, uz}, B[3] = {bx, by, bz};
+    auto comp = [&](int i, V dBi) {
+        const int k0 = 19 + 7 * i;
+        const V* gi = g + 7 * i;
+        const V b1 = vmul(ow1, dBi);
+        out(k0, vfma(o1, gi[0], vmul(ow0, dBi)));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d == i) {
+                out(k0 + 1 + 2 * d, vfma(o1, gi[1 + 2 * d], b1));
+                out(k0 + 2 + 2 * d, vfma(o1, gi[2 + 2 * d], b1));
+            } else {
+                const V E = vfma(u[d], B[i], vneg(vmul(B[d], u[i])));
+                out(k0 + 1 + 2 * d, vfma(o1, gi[1 + 2 * d], vfma(K::set(p.omW1x4), E, b1)));
+                out(k0 + 2 + 2 * d, vfma(o1, gi[2 + 2 * d], vfma(K::set(-p.omW1x4), E, b1)));
+            }
+        }
+    };
+    comp(0, bx);
+    comp(1, dby);
+    comp(2, bz);
 }
 
 // The fused step of one node per thread.  S: storage type, C: compute type.
@@ -244,7 +313,7 @@ __global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, c
         for (int k = 0; k < 40; ++k) {
             const int a = slot_dir3(k);
             if (EYa(a) != 1) continue;
-            v[k] = wall_in3<C>(p, true, false, k, load_s<S, C>((k < 19 ? fin : gin) + slot_plane3(k, opp(a)) * N + n));
+            v[k] = wall_in3<C, C>(p, true, false, k, load_s<S, C>((k < 19 ? fin : gin) + slot_plane3(k, opp(a)) * N + n));
         }
     }
     if (top) {  // entering along e_y = -1: 4, 8, 9, 16, 18; 4
@@ -252,10 +321,10 @@ __global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, c
         for (int k = 0; k < 40; ++k) {
             const int a = slot_dir3(k);
             if (EYa(a) != -1) continue;
-            v[k] = wall_in3<C>(p, false, true, k, load_s<S, C>((k < 19 ? fin : gin) + slot_plane3(k, opp(a)) * N + n));
+            v[k] = wall_in3<C, C>(p, false, true, k, load_s<S, C>((k < 19 ? fin : gin) + slot_plane3(k, opp(a)) * N + n));
         }
     }
-    collide3<C>(p, [&](int k) -> C { return v[k]; },
+    collide3<C, C>(p, [&](int k) -> C { return v[k]; },
                 [&](int k, C val) { store_s<S, C>((k < 19 ? fout : gout) + slot_plane3(k, slot_dir3(k)) * N + n, val); });
 }
 
@@ -265,15 +334,16 @@ __global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, c
 // each slot with one bulk copy of R' nx elements (two where the task holds a wall row and e_y != 0:
 // that row takes the node's own row of the opposite plane), one slot per lane, into one of
 // kStages3 shared-memory stages, completing on the stage's `full` barrier.  The periodic x pull is
-// an index wrap within the staged row.  Sixteen consumer warps take one node per thread: 40 values
-// from shared memory, collide3, 40 stores; each warp then arrives on the stage's `empty` barrier,
+// an index wrap within the staged row.  Eight consumer warps take the task's nodes: 40 values from
+// shared memory, collide3, 40 stores; each warp then arrives on the stage's `empty` barrier,
 // which the producer waits for before it refills the stage, so kStages3 - 1 tasks' reads are in
-// flight while one is computed.  Rows must be 16-byte aligned: nx a multiple of 8, and nx <=
-// kTaskNodes3.  A wait that runs out (kWaitNs) sets *err and ends that warp's loop; the producer
+// flight while one is computed.  Each consumer thread takes two x-adjacent nodes (x even) as one
+// float2 (packed FP32 arithmetic), reading 32-bit words of the staged rows and storing one word
+// per plane.  Rows must be 16-byte aligned: nx a multiple of 8, and nx <= kTaskNodes3.  A wait that runs out (kWaitNs) sets *err and ends that warp's loop; the producer
 // then waits, within the same limit, for the last copies it issued to each stage before it returns.
-constexpr int kTaskNodes3 = 512;                 // consumer threads, one node each
-constexpr int kConsumerWarps3 = kTaskNodes3 / 32;
-constexpr int kThreads3 = kTaskNodes3 + 32;      // consumers + the producer warp
+constexpr int kTaskNodes3 = 512;                 // nodes of a task: consumer threads x 2
+constexpr int kConsumerWarps3 = kTaskNodes3 / 64;
+constexpr int kThreads3 = kTaskNodes3 / 2 + 32;  // consumers + the producer warp
 constexpr int kStages3 = 5;
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 
@@ -364,9 +434,12 @@ __global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __r
         return;
     }
 
-    // consumers: thread tid is node x = tid % nx of task row j = tid / nx
-    const int j = tid / nx, x = tid - j * nx;
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    // consumers: thread tid holds nodes x, x + 1 (x = 2 tid mod nx, even) of task row j = 2 tid / nx
+    typedef lks::Packed<S> P;
+    const int j = (2 * tid) / nx, x = 2 * tid - j * nx;
+    const int nw = nx / 2, xw = x / 2;                        // words per row, the pair's word
+    const int xwm = xw == 0 ? nw - 1 : xw - 1, xwp = xw == nw - 1 ? 0 : xw + 1;
+    const size_t slot_words = slot_elems / 2;
     for (int64_t it = 0; it < nmine; ++it) {
         const int s = (int)(it % kStages3);
         if (!lks::mbar_wait_bounded(&full[s], (uint32_t)(it / kStages3) & 1u, kWaitNs)) {
@@ -378,17 +451,26 @@ __global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __r
         const int y = y0 + j;
         if (j < R && y < ny) {
             const bool bottom = (y == 0), top = (y == ny - 1);
-            const S* st = stage0 + (size_t)s * stage_elems + (size_t)j * nx;
-            auto in = [&](int k) -> float {
+            const uint32_t* st = reinterpret_cast<const uint32_t*>(stage0 + (size_t)s * stage_elems + (size_t)j * nx);
+            auto in = [&](int k) -> float2 {
                 const int a = slot_dir3(k), ex = EXa(a), ey = EYa(a);
                 const bool wall = (ey == 1 && bottom) || (ey == -1 && top);
-                const int xs = (wall || ex == 0) ? x : (ex == 1 ? xm : xp);
-                const float v = lks::Loader<S, float, false>::ld(st + k * slot_elems + xs);
-                return wall_in3<float>(p, bottom, top, k, v);
+                const uint32_t* row = st + k * slot_words;
+                uint32_t w;
+                if (wall || ex == 0)
+                    w = row[xw];
+                else if (ex == 1)  // x <- x - 1 (high half of the word before), x + 1 <- x
+                    w = __byte_perm(row[xwm], row[xw], 0x5432);
+                else  // x <- x + 1, x + 1 <- x + 2 (low half of the word after)
+                    w = __byte_perm(row[xw], row[xwp], 0x5432);
+                return wall_in3<float2, float>(p, bottom, top, k, make_float2(P::lo(w), P::hi(w)));
             };
             const int64_t n = ((int64_t)z * ny + y) * nx + x;
-            collide3<float>(p, in, [&](int k, float v) {
-                store_s<S, float>((k < 19 ? fout : gout) + slot_plane3(k, slot_dir3(k)) * N + n, v);
+            uint32_t* fo = reinterpret_cast<uint32_t*>(fout + n);
+            uint32_t* go = reinterpret_cast<uint32_t*>(gout + n);
+            collide3<float2, float>(p, in, [&](int k, float2 v) {
+                const size_t off = (size_t)slot_plane3(k, slot_dir3(k)) * (size_t)N / 2;
+                (k < 19 ? fo : go)[off] = P::pack(v.x, v.y);
             });
         }
         __syncwarp();
