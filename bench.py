@@ -388,6 +388,19 @@ def bench_ours(args):
                                            "frac": round(a3 / peak, 4), "bytes_per_node": 320}}
         l3.close()
         del l3
+        # the same channel with BF16 deviations (rows staged through shared memory by bulk copies)
+        l3 = lks3d.Lattice3D(n3, n3, n3, phys["tau_f"], phys["tau_m"], 20.0 * 0.1 / (n3 / 2), 0.0, "bf16")
+        l3.set_walls(phys["c"], phys["c"], 0.0, phys["u_w"])
+        l3.step(3)
+        barrier()
+        t3 = max_over_ranks(_time_steps(l3, k3, stream))
+        v3 = nodes3 * k3 * ws / t3 / 1e6
+        a3 = 160 * nodes3 / (t3 / k3) / 1e9
+        extra["d3q19_bf16"] = {"value": round(v3, 1), "unit": UNIT, "steps": k3,
+                               "roofline": {"bound": "hbm", "achieved": round(a3, 1), "peak": peak, "unit": "GB/s",
+                                            "frac": round(a3 / peak, 4), "bytes_per_node": 160}}
+        l3.close()
+        del l3
         torch.cuda.empty_cache()
 
     cpu = None
@@ -666,10 +679,17 @@ def bench_d3(args):
     bpn = 80 * {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[storage]
     peak, _ = _peaks()
     achieved = bpn * nodes / (t / args.steps) / 1e9
-    out = {"workload": "d3q19", "metric": METRIC, "unit": UNIT, "value": round(nodes * args.steps / t / 1e6, 1),
+    v = nodes * args.steps / t / 1e6
+    out = {"workload": "d3q19", "metric": METRIC, "unit": UNIT, "value": round(v, 1),
            "config": {"n": n, "storage": storage, "steps": args.steps, "bytes_per_node": bpn},
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(achieved / peak, 4)}}
+    if storage == "f64":  # FP64 arithmetic, not HBM, bounds this kernel on GB300
+        ipn = FP64_PIPE_INSTR_PER_NODE_3D
+        out["roofline_fp64_pipe"] = {"bound": "fp64 pipe", "instr_per_node": ipn,
+                                     "achieved": round(ipn * v * 1e6 / 1e12, 4), "peak": FP64_PIPE_PEAK / 1e12,
+                                     "unit": "T FP64 instr/s", "frac": round(ipn * v * 1e6 / FP64_PIPE_PEAK, 4),
+                                     "source": "profiles/step3_kernel_f64_128cube_fp64_pipe.md"}
     lat.close()
     print(json.dumps(out), flush=True)
     return 0
@@ -761,6 +781,7 @@ FP64_FLOPS_PER_NODE = 212
 # FP64 pipe instructions per node of the FP64 step kernel (ncu sm__inst_executed_pipe_fp64.sum x 32
 # / nodes at 2048^2) and the pipe's nominal rate (1.25 TFLOP/s = 0.625e12 DFMA/s on GB300)
 FP64_PIPE_INSTR_PER_NODE = 153
+FP64_PIPE_INSTR_PER_NODE_3D = 378
 FP64_PIPE_PEAK = 0.625e12
 
 

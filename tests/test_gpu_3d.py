@@ -187,3 +187,23 @@ def test_reduced_precision_long_run(l3, storage, bounds):
     assert np.max(np.abs(mg[1] - mo[1])) <= bounds[0] * np.max(np.abs(mo[1]))
     assert np.max(np.abs(mg[4] - mo[4])) <= bounds[1] * np.max(np.abs(mo[4]))
     gpu.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_staged_pair_path_bitwise_equals_one_node_kernel(l3, storage):
+    """16-bit storage with nx = 40 runs the staged kernel (two nodes per thread, packed FP32x2
+    arithmetic), nx = 37 the one-node kernel.  On a flow that depends on y only (rest start, body
+    force, moving wall) every (x, z) column of both must be bit-identical: the per-node arithmetic
+    is the same sequence of individually rounded operations."""
+    out = []
+    for nx in (37, 40):
+        g = l3.Lattice3D(nx, 21, 3, 0.7, 0.9, 0.02, 2e-5, storage)
+        g.set_walls(0.4, math.inf, 0.0, 0.04)
+        g.step(150)
+        f, gg = g.get_state()
+        assert np.all(f == f[..., :1]) and np.all(f == f[:, :1])
+        assert np.all(gg == gg[..., :1]) and np.all(gg == gg[:, :, :1])
+        assert np.max(np.abs(f[:, 0, :, 0] - f[:, 0, :1, 0])) > 0  # the flow is not the rest state
+        out.append((f[:, 0, :, 0].copy(), gg[:, :, 0, :, 0].copy()))
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
