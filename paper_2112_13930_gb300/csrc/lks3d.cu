@@ -339,16 +339,19 @@ __global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, c
 // which the producer waits for before it refills the stage, so kStages3 - 1 tasks' reads are in
 // flight while one is computed.  Each consumer thread takes two x-adjacent nodes (x even) as one
 // float2 (packed FP32 arithmetic), reading 32-bit words of the staged rows and storing one word
-// per plane.  Rows must be 16-byte aligned: nx a multiple of 8, and nx <= kTaskNodes3.  A wait that runs out (kWaitNs) sets *err and ends that warp's loop; the producer
-// then waits, within the same limit, for the last copies it issued to each stage before it returns.
+// per plane.  Each slot takes a fixed kTaskNodes3 elements of a stage, so the slot offsets are
+// constants.  Rows must be 16-byte aligned: nx a multiple of 8, and nx <= kTaskNodes3.  A wait
+// that runs out (kWaitNs) sets *err and ends that warp's loop; the producer then waits, within the
+// same limit, for the last copies it issued to each stage before it returns.
 constexpr int kTaskNodes3 = 512;                 // nodes of a task: consumer threads x 2
 constexpr int kConsumerWarps3 = kTaskNodes3 / 64;
 constexpr int kThreads3 = kTaskNodes3 / 2 + 32;  // consumers + the producer warp
 constexpr int kStages3 = 5;
+constexpr int kStageElems3 = 40 * kTaskNodes3;   // a slot takes kTaskNodes3 elements of a stage
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 
 inline int rows_per_task3(int nx, int ny) { return std::max(1, std::min(ny, kTaskNodes3 / nx)); }
-inline size_t staged_smem3(int nx, int ny) { return 128 + (size_t)kStages3 * 40 * rows_per_task3(nx, ny) * nx * 2; }
+inline size_t staged_smem3() { return 128 + (size_t)kStages3 * kStageElems3 * 2; }
 
 template <typename S>
 __global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
@@ -365,7 +368,6 @@ __global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __r
     const int64_t ntask = (int64_t)nz * tpp;
     const int64_t G = gridDim.x, t0 = blockIdx.x;
     const int64_t nmine = t0 < ntask ? (ntask - 1 - t0) / G + 1 : 0;  // tasks t0, t0 + G, ...
-    const size_t slot_elems = (size_t)R * nx, stage_elems = 40 * slot_elems;
     if (tid == 0) {
         for (int s = 0; s < kStages3; ++s) {
             lks::mbar_init(&full[s], 1);
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __r
                 const int ey = ey2[i], ez = ez2[i];
                 const int zsrc = ez == 1 ? (z == 0 ? nz - 1 : z - 1) : ez == -1 ? (z == nz - 1 ? 0 : z + 1) : z;
                 const int64_t rsrc = (int64_t)zsrc * ny, rown = (int64_t)z * ny;
-                S* dst = stage0 + (size_t)s * stage_elems + (size_t)k * slot_elems;
+                S* dst = stage0 + s * kStageElems3 + k * kTaskNodes3;
                 if (ey == 1 && y0 == 0) {  // row 0 is a wall row: own row 0, opposite plane
                     lks::bulk_g2s(dst, bw[i] + rown * nx, row_bytes, &full[s]);
                     if (Rt > 1) lks::bulk_g2s(dst + nx, bn[i] + rsrc * nx, (uint32_t)(Rt - 1) * row_bytes, &full[s]);
@@ -439,7 +441,6 @@ __global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __r
     const int j = (2 * tid) / nx, x = 2 * tid - j * nx;
     const int nw = nx / 2, xw = x / 2;                        // words per row, the pair's word
     const int xwm = xw == 0 ? nw - 1 : xw - 1, xwp = xw == nw - 1 ? 0 : xw + 1;
-    const size_t slot_words = slot_elems / 2;
     for (int64_t it = 0; it < nmine; ++it) {
         const int s = (int)(it % kStages3);
         if (!lks::mbar_wait_bounded(&full[s], (uint32_t)(it / kStages3) & 1u, kWaitNs)) {
@@ -451,11 +452,11 @@ __global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __r
         const int y = y0 + j;
         if (j < R && y < ny) {
             const bool bottom = (y == 0), top = (y == ny - 1);
-            const uint32_t* st = reinterpret_cast<const uint32_t*>(stage0 + (size_t)s * stage_elems + (size_t)j * nx);
+            const uint32_t* st = reinterpret_cast<const uint32_t*>(stage0 + s * kStageElems3 + j * nx);
             auto in = [&](int k) -> float2 {
                 const int a = slot_dir3(k), ex = EXa(a), ey = EYa(a);
                 const bool wall = (ey == 1 && bottom) || (ey == -1 && top);
-                const uint32_t* row = st + k * slot_words;
+                const uint32_t* row = st + k * (kTaskNodes3 / 2);
                 uint32_t w;
                 if (wall || ex == 0)
                     w = row[xw];
@@ -760,14 +761,14 @@ void launch_staged3(lks3_handle* h, int src) {
     const int64_t ntask = (int64_t)p.nz * ((p.ny + R - 1) / R);
     const unsigned grid = (unsigned)std::min<int64_t>(ntask, h->staged_grid);
     const Params3<float> q = make_params3<float>(p, h->c_bot, h->c_top, h->u_bot, h->u_top);
-    step3_staged_kernel<S><<<grid, kThreads3, staged_smem3(p.nx, p.ny), h->stream>>>(
+    step3_staged_kernel<S><<<grid, kThreads3, staged_smem3(), h->stream>>>(
         (const S*)h->f[src], (const S*)h->g[src], (S*)h->f[src ^ 1], (S*)h->g[src ^ 1], q, R, h->flag);
 }
 
 // Opt the staged kernel of the handle's storage into its shared memory and size its grid.
 cudaError_t prepare_staged3(lks3_handle* h) {
     int dev = 0, sms = 0, occ = 0;
-    const size_t smem = staged_smem3(h->p.nx, h->p.ny);
+    const size_t smem = staged_smem3();
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (h->p.storage == LKS_BF16_DEV) {
