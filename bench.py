@@ -781,7 +781,7 @@ FP64_FLOPS_PER_NODE = 212
 # FP64 pipe instructions per node of the FP64 step kernel (ncu sm__inst_executed_pipe_fp64.sum x 32
 # / nodes at 2048^2) and the pipe's nominal rate (1.25 TFLOP/s = 0.625e12 DFMA/s on GB300)
 FP64_PIPE_INSTR_PER_NODE = 153
-FP64_PIPE_INSTR_PER_NODE_3D = 378
+FP64_PIPE_INSTR_PER_NODE_3D = 336
 FP64_PIPE_PEAK = 0.625e12
 
 

@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <new>
 #include <string>
 
@@ -75,6 +76,7 @@ struct Params3 {
     C om_f, om1f, om_m, om1m;  // 1/tau_f, 1 - 1/tau_f, 1/tau_m, 1 - 1/tau_m
     C B0, Fx, hFx, twoB0;      // hFx = F/2, twoB0 = 2 B0
     C Ks[3];                   // (1 - 1/(2 tau_f)) 3 F w for |e|^2 = 0, 1, 2 (source term)
+    C cB[3];                   // 4.5 w (-1) 2 B0 for |e|^2 = 0, 1, 2 (Maxwell stress, e_y = +1)
     C omW0, omW1, omW1x4;      // w_m W_0, w_m W, 4 w_m W (D3Q7)
     Wall3<C> bot, top;
 };
@@ -98,6 +100,9 @@ Params3<C> make_params3(const lks3_params& p, double c_bot, double c_top, double
     q.Ks[0] = (C)(src * 3.0 * p.Fx / 3.0);
     q.Ks[1] = (C)(src * 3.0 * p.Fx / 18.0);
     q.Ks[2] = (C)(src * 3.0 * p.Fx / 36.0);
+    q.cB[0] = (C)0;
+    q.cB[1] = (C)(-0.25 * 2.0 * p.B0);
+    q.cB[2] = (C)(-0.125 * 2.0 * p.B0);
     q.omW0 = (C)(0.25 / p.tau_m);
     q.omW1 = (C)(0.125 / p.tau_m);
     q.omW1x4 = (C)(0.5 / p.tau_m);
@@ -174,6 +179,18 @@ __device__ __forceinline__ V edot3(int a, V vx, V vy, V vz) {
     return r;
 }
 
+// Sum of n values as a balanced tree of additions (depth ceil(log2 n)); v is overwritten.
+template <int N, typename V>
+__device__ __forceinline__ V tree_sum3(V (&v)[N]) {
+#pragma unroll
+    for (int width = N; width > 1; width = (width + 1) / 2) {
+#pragma unroll
+        for (int i = 0; i < width / 2; ++i) v[i] = lks::vadd(v[2 * i], v[2 * i + 1]);
+        if (width & 1) v[width / 2] = v[width - 1];
+    }
+    return v[0];
+}
+
 // Moments, equilibria, source and collision of one node or of a pair of nodes (a3-a5).  F(k) returns
 // the streamed value of slot k (wall terms included), out(k, v) takes the post-collision value of
 // slot k.  With the rest (rho = 1, u = 0, B = (0, B0, 0)) subtracted, per direction a of D3Q19
@@ -188,25 +205,35 @@ __device__ __forceinline__ void collide3(const Params3<C>& p, In F, Out out) {
     V f[19];
 #pragma unroll
     for (int a = 0; a < 19; ++a) f[a] = F(a);
-    V drho = f[0];
+    // Moments.  FP64 (bound by the FP64 pipe's latency and rate) sums as balanced trees; FP32 and
+    // the FP32x2 pairs keep left-to-right sums, which need fewer live registers in the staged
+    // kernel.  The one-node and two-node FP32 paths use the same order, so they agree bit for bit.
+    constexpr bool kTree = std::is_same<C, double>::value;
+    auto sum_of = [&](auto& v) -> V {
+        constexpr int n = sizeof(v) / sizeof(v[0]);
+        if constexpr (kTree) {
+            return tree_sum3(v);
+        } else {
+            V r = v[0];
 #pragma unroll
-    for (int a = 1; a < 19; ++a) drho = vadd(drho, f[a]);
+            for (int i = 1; i < n; ++i) r = vadd(r, v[i]);
+            return r;
+        }
+    };
+    V t19[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) t19[a] = f[a];
+    const V drho = sum_of(t19);
     auto jsum = [&](int d) -> V {
-        V pos = f[0], neg = f[0];
-        bool pf = true, nf = true;
+        V pos[5], neg[5];
+        int np = 0, nn = 0;
 #pragma unroll
         for (int a = 1; a < 19; ++a) {
             const int e = d == 0 ? EXa(a) : (d == 1 ? EYa(a) : EZa(a));
-            if (e == 1) {
-                pos = pf ? f[a] : vadd(pos, f[a]);
-                pf = false;
-            }
-            if (e == -1) {
-                neg = nf ? f[a] : vadd(neg, f[a]);
-                nf = false;
-            }
+            if (e == 1) pos[np++] = f[a];
+            if (e == -1) neg[nn++] = f[a];
         }
-        return vsub(pos, neg);
+        return vsub(sum_of(pos), sum_of(neg));
     };
     const V jx = jsum(0), jy = jsum(1), jz = jsum(2);
     const V rho = vadd(K::set(C(1)), drho);
@@ -215,39 +242,46 @@ __device__ __forceinline__ void collide3(const Params3<C>& p, In F, Out out) {
     V g[21];
 #pragma unroll
     for (int k = 0; k < 21; ++k) g[k] = F(19 + k);
-    V bx = g[0], dby = g[7], bz = g[14];
+    V t7[3][7];
 #pragma unroll
-    for (int a = 1; a < 7; ++a) {
-        bx = vadd(bx, g[a]);
-        dby = vadd(dby, g[7 + a]);
-        bz = vadd(bz, g[14 + a]);
-    }
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < 7; ++a) t7[i][a] = g[7 * i + a];
+    const V bx = sum_of(t7[0]), dby = sum_of(t7[1]), bz = sum_of(t7[2]);
     const V by = vadd(K::set(p.B0), dby);
     const V q = vfma(bx, bx, vfma(bz, bz, vmul(dby, vadd(K::set(p.twoB0), dby))));  // |B|^2 - B0^2
     const V usq = vfma(ux, ux, vfma(uy, uy, vmul(uz, uz)));
-    const V us15 = vmul(K::set(C(1.5)), usq);
+    const V nus15 = vmul(K::set(C(-1.5)), usq);
     // 4.5 w (|e|^2/2 - 1/6) q for |e|^2 = 0, 1, 2
     const V cq0 = vmul(K::set(C(-0.25)), q), cq1 = vmul(K::set(C(1.0 / 12.0)), q), cq2 = vmul(K::set(C(5.0 / 48.0)), q);
-    const V om1f = K::set(p.om1f), omf = K::set(p.om_f), one = K::set(C(1));
+    // source prefactors K_|e|^2 (e_x - u_x) for the (|e|^2, e_x) that occur
+    const V onemux = vsub(K::set(C(1)), ux), monemux = vsub(K::set(C(-1)), ux);
+    const V kx0[3] = {vmul(K::set(-p.Ks[0]), ux), vmul(K::set(-p.Ks[1]), ux), vmul(K::set(-p.Ks[2]), ux)};
+    const V kxp[3] = {kx0[0], vmul(K::set(p.Ks[1]), onemux), vmul(K::set(p.Ks[2]), onemux)};
+    const V kxm[3] = {kx0[0], vmul(K::set(p.Ks[1]), monemux), vmul(K::set(p.Ks[2]), monemux)};
+    const V om1f = K::set(p.om1f), omf = K::set(p.om_f);
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
         const int ex = EXa(a), ey = EYa(a);
         const int e2 = ex * ex + ey * ey + EZa(a) * EZa(a);
         V bm1, mag;
         if (a == 0) {
-            bm1 = vneg(us15);
+            bm1 = nus15;
             mag = cq0;
         } else {
             const V eu = edot3<V>(a, ux, uy, uz);
             const V eBm = edot3<V>(a, bx, dby, bz);  // e.B - e_y B0
-            const V eBp = ey == 0 ? eBm : vadd(eBm, K::set(ey > 0 ? p.twoB0 : -p.twoB0));  // e.B + e_y B0
-            bm1 = vsub(vmul(vfma(K::set(C(4.5)), eu, K::set(C(3))), eu), us15);
-            mag = vfma(K::set(C(e2 == 1 ? -0.25 : -0.125)), vmul(eBm, eBp), e2 == 1 ? cq1 : cq2);
+            // b = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2
+            bm1 = vfma(vfma(K::set(C(4.5)), eu, K::set(C(3))), eu, nus15);
+            // -4.5 w (e.B - e_y B0)(e.B + e_y B0) + 4.5 w (|e|^2/2 - 1/6) q
+            const C cE = C(e2 == 1 ? -0.25 : -0.125);
+            const V t = ey == 0 ? vmul(K::set(cE), eBm) : vfma(K::set(cE), eBm, K::set(ey > 0 ? p.cB[e2] : -p.cB[e2]));
+            mag = vfma(t, eBm, e2 == 1 ? cq1 : cq2);
         }
         const C w = (C)w19(a);
         const V feq = vfma(K::set(w), vfma(rho, bm1, drho), mag);
-        const V exu = ex == 0 ? vneg(ux) : vsub(K::set(C(ex)), ux);
-        const V sa = vmul(vmul(K::set(p.Ks[e2]), exu), vadd(one, bm1));
+        const V kxe = ex == 0 ? kx0[e2] : (ex > 0 ? kxp[e2] : kxm[e2]);
+        const V sa = vfma(kxe, bm1, kxe);  // K (e_x - u_x) (1 + b)
         out(a, vfma(om1f, f[a], vfma(omf, feq, sa)));
     }
     const V o1 = K::set(p.om1m), ow0 = K::set(p.omW0), ow1 = K::set(p.omW1);
@@ -453,26 +487,35 @@ __global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __r
         if (j < R && y < ny) {
             const bool bottom = (y == 0), top = (y == ny - 1);
             const uint32_t* st = reinterpret_cast<const uint32_t*>(stage0 + s * kStageElems3 + j * nx);
-            auto in = [&](int k) -> float2 {
-                const int a = slot_dir3(k), ex = EXa(a), ey = EYa(a);
-                const bool wall = (ey == 1 && bottom) || (ey == -1 && top);
-                const uint32_t* row = st + k * (kTaskNodes3 / 2);
-                uint32_t w;
-                if (wall || ex == 0)
-                    w = row[xw];
-                else if (ex == 1)  // x <- x - 1 (high half of the word before), x + 1 <- x
-                    w = __byte_perm(row[xwm], row[xw], 0x5432);
-                else  // x <- x + 1, x + 1 <- x + 2 (low half of the word after)
-                    w = __byte_perm(row[xw], row[xwp], 0x5432);
-                return wall_in3<float2, float>(p, bottom, top, k, make_float2(P::lo(w), P::hi(w)));
-            };
             const int64_t n = ((int64_t)z * ny + y) * nx + x;
             uint32_t* fo = reinterpret_cast<uint32_t*>(fout + n);
             uint32_t* go = reinterpret_cast<uint32_t*>(gout + n);
-            collide3<float2, float>(p, in, [&](int k, float2 v) {
-                const size_t off = (size_t)slot_plane3(k, slot_dir3(k)) * (size_t)N / 2;
-                (k < 19 ? fo : go)[off] = P::pack(v.x, v.y);
-            });
+            // rows without a wall (all but two per z plane) take a path with no wall logic
+            auto body = [&](auto walls) {
+                constexpr bool W = decltype(walls)::value;
+                auto in = [&](int k) -> float2 {
+                    const int a = slot_dir3(k), ex = EXa(a), ey = EYa(a);
+                    const bool wall = W && ((ey == 1 && bottom) || (ey == -1 && top));
+                    const uint32_t* row = st + k * (kTaskNodes3 / 2);
+                    uint32_t w;
+                    if (wall || ex == 0)
+                        w = row[xw];
+                    else if (ex == 1)  // x <- x - 1 (high half of the word before), x + 1 <- x
+                        w = __byte_perm(row[xwm], row[xw], 0x5432);
+                    else  // x <- x + 1, x + 1 <- x + 2 (low half of the word after)
+                        w = __byte_perm(row[xw], row[xwp], 0x5432);
+                    const float2 v = make_float2(P::lo(w), P::hi(w));
+                    return W ? wall_in3<float2, float>(p, bottom, top, k, v) : v;
+                };
+                collide3<float2, float>(p, in, [&](int k, float2 v) {
+                    const size_t off = (size_t)slot_plane3(k, slot_dir3(k)) * (size_t)N / 2;
+                    (k < 19 ? fo : go)[off] = P::pack(v.x, v.y);
+                });
+            };
+            if (bottom || top)
+                body(std::true_type{});
+            else
+                body(std::false_type{});
         }
         __syncwarp();
         if (lane == 0) lks::mbar_arrive(&empty[s]);
