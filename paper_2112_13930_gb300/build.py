@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblks.so")
-SOURCES = ["lks_step.cu", "lks_step_aa.cu", "lks_aux.cu", "lks_api.cu", "lks_batch.cu", "lks3d.cu"]
+SOURCES = ["lks_step.cu", "lks_step_aa.cu", "lks_step_staged.cu", "lks_aux.cu", "lks_api.cu", "lks_batch.cu", "lks3d.cu"]
 HEADERS = ["lks_device.cuh", "lks_aa.cuh", "lks_packed.cuh", "lks_bulk.cuh", "lks_vec.cuh", "lks_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

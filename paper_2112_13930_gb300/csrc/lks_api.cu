@@ -32,7 +32,7 @@ struct NvtxRange {
 };
 
 struct Layout {
-    size_t f_bytes, g_bytes, off_fa, off_ga, off_fb, off_gb, off_snap, off_partial, off_out, off_prof, total;
+    size_t f_bytes, g_bytes, off_fa, off_ga, off_fb, off_gb, off_snap, off_partial, off_out, off_prof, off_flag, total;
 };
 
 Layout make_layout(const lks_params* p) {
@@ -55,6 +55,7 @@ Layout make_layout(const lks_params* p) {
     L.off_partial = o; o += align_up(4 * (size_t)lks::residual_blocks((int64_t)N) * sizeof(double));
     L.off_out = o; o += align_up(8 * sizeof(double));
     L.off_prof = o; o += align_up(5 * (size_t)p->ny * sizeof(double));
+    L.off_flag = o; o += align_up(sizeof(int));  // set by a staged step whose bounded wait ran out
     L.total = o;
     return L;
 }
@@ -173,6 +174,9 @@ struct lks_handle {
     double* prof = nullptr;
     double* node_stage = nullptr;  // lazily allocated 5*N doubles for per-node host moments
     double* host_small = nullptr;  // pinned 8 doubles
+    int* flag = nullptr;
+    bool staged = false;              // two-buffer, 16-bit, nx % 8 == 0, nx >= 1024: the staged step
+    lks::StagedStep ss = {nullptr, 0};
     double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
     StepParams<double> sp;
     int64_t steps = 0;
@@ -196,6 +200,16 @@ lks_status cuda_fail(lks_handle* h, cudaError_t e, const char* where) {
     return fail(h, LKS_ECUDA, m);
 }
 
+// After a synchronisation: LKS_ETIMEOUT if a staged step gave up waiting for its copies.
+lks_status staged_check(lks_handle* h, const char* where) {
+    if (!h->staged) return LKS_OK;
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, h->flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, where);
+    if (v) return fail(h, LKS_ETIMEOUT, std::string(where) + ": a staged step's shared-memory wait ran out");
+    return LKS_OK;
+}
+
 void refresh_params(lks_handle* h) {
     const lks_params& p = h->p;
     h->sp = lks::make_step_params(p.nx, p.ny, p.closure, p.tau_f, p.tau_m, p.B0, p.Fx, h->c_bot, h->c_top, h->u_bot,
@@ -214,7 +228,8 @@ void drop_graphs(lks_handle* h) {
 // phase `src` of a pair (0: pull and push to the neighbours, 1: own slots) on their one buffer.
 cudaError_t step_once(lks_handle* h, int src, cudaStream_t st) {
     if (h->p.inplace) return lks::launch_step_aa(h->p.storage, h->p.closure, src, h->f[0], h->g[0], h->sp, st);
-    return lks::launch_step(h->p.storage, h->p.closure, h->f[src], h->g[src], h->f[src ^ 1], h->g[src ^ 1], h->sp, st);
+    return lks::launch_step(h->p.storage, h->p.closure, h->f[src], h->g[src], h->f[src ^ 1], h->g[src ^ 1], h->sp, st,
+                            h->staged ? &h->ss : nullptr);
 }
 
 // Capture kGraphSteps steps starting from buffer `start` into an executable graph.
@@ -287,8 +302,15 @@ lks_status lks_create(const lks_params* p, lks_handle** out) {
     h->partial = (double*)(h->base + h->L.off_partial);
     h->dout = (double*)(h->base + h->L.off_out);
     h->prof = (double*)(h->base + h->L.off_prof);
+    h->flag = (int*)(h->base + h->L.off_flag);
     e = cudaHostAlloc((void**)&h->host_small, 8 * sizeof(double), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess && lks::staged_step_applies(p->storage, p->nx, p->inplace)) {
+        e = lks::prepare_staged_step(p->storage, &h->ss.grid);
+        h->ss.err = h->flag;
+        h->staged = e == cudaSuccess;
+    }
     if (e != cudaSuccess) {
         lks_destroy(h);
         return cuda_fail(nullptr, e, "lks_create");
@@ -386,7 +408,7 @@ lks_status lks_moments(lks_handle* h, int what, double* host_out) {
     cudaError_t e = cudaMemcpyAsync(host_out, dst, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_moments");
-    return LKS_OK;
+    return staged_check(h, "lks_moments");
 }
 
 lks_status lks_residual(lks_handle* h, double* r_u, double* r_b) {
@@ -399,6 +421,7 @@ lks_status lks_residual(lks_handle* h, double* r_u, double* r_b) {
         e = cudaMemcpyAsync(h->host_small, h->dout, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_residual");
+    if (lks_status fs = staged_check(h, "lks_residual")) return fs;
     const double* s = h->host_small;
     for (int k = 0; k < 4; ++k)
         if (!isfinite(s[k])) return fail(h, LKS_EUNSTABLE, "the state became non-finite");
@@ -456,7 +479,7 @@ lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_get_state");
-    return LKS_OK;
+    return staged_check(h, "lks_get_state");
 }
 
 lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host_g) {
@@ -492,7 +515,7 @@ lks_status lks_sync(lks_handle* h) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_sync");
-    return LKS_OK;
+    return staged_check(h, "lks_sync");
 }
 
 lks_status lks_destroy(lks_handle* h) {

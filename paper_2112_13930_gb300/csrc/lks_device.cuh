@@ -11,6 +11,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lks {
 
 // Coefficients of one wall's closure, precomputed on the host in FP64.
@@ -92,14 +94,46 @@ __device__ __forceinline__ double recip(double rho) {
 }
 __device__ __forceinline__ float recip(float rho) { return __frcp_rn(rho); }
 
+// Two nodes at once: float2 values with the packed FP32 instructions of sm_100 and later (add, mul,
+// fma on .f32x2), each half rounded exactly as the scalar float operation above, so the collision
+// code below, written once, gives a node the same bits alone (float) or in a pair (float2).  A
+// float operand is used in both halves.  These take part only when an operand is a float2.
+__device__ __forceinline__ float2 pair_of(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pair_of(float2 a) { return a; }
+template <typename... T>
+struct HasPair : std::false_type {};
+template <typename T0, typename... T>
+struct HasPair<T0, T...>
+    : std::integral_constant<bool, std::is_same<T0, float2>::value || HasPair<T...>::value> {};
+template <typename... T>
+using IfPair = typename std::enable_if<HasPair<T...>::value, int>::type;
+
+template <typename A, typename B, IfPair<A, B> = 0>
+__device__ __forceinline__ float2 fmul(A a, B b) { return __fmul2_rn(pair_of(a), pair_of(b)); }
+template <typename A, typename B, typename D, IfPair<A, B, D> = 0>
+__device__ __forceinline__ float2 ffma(A a, B b, D c) { return __ffma2_rn(pair_of(a), pair_of(b), pair_of(c)); }
+template <typename A, typename B, IfPair<A, B> = 0>
+__device__ __forceinline__ float2 operator+(A a, B b) { return __fadd2_rn(pair_of(a), pair_of(b)); }
+// a - b as b * (-1) + a: the product is exact, so the one rounding is that of a - b
+template <typename A, typename B, IfPair<A, B> = 0>
+__device__ __forceinline__ float2 operator-(A a, B b) {
+    return __ffma2_rn(pair_of(b), make_float2(-1.0f, -1.0f), pair_of(a));
+}
+__device__ __forceinline__ float2 operator-(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 operator/(float2 a, float2 b) { return make_float2(a.x / b.x, a.y / b.y); }
+__device__ __forceinline__ float2 recip(float2 rho) { return make_float2(recip(rho.x), recip(rho.y)); }
+// zero of a node value type
+template <typename V> __device__ __forceinline__ V zero_of() { return V(0); }
+template <> __device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.0f, 0.0f); }
+
 // a4-a5 for g (Eqs. geqmagneticfield, LKSformagneticfield): g' = (1 - w_m) g + w_m g^eq,dev with
 //   g^eq_x = W (Bx - 3 e_y E),  g^eq,dev_y = W (dBy + 3 e_x E),  E = u_x B_y - u_y B_x.
-template <typename C>
-__device__ __forceinline__ void collide_g(C gx[5], C gy[5], C ux, C uy, C bx, C by, C dby, const StepParams<C>& p) {
-    const C om1m = p.om1m;
-    const C ce = fmul(p.owm1, fmul(C(3), ffma(ux, by, -fmul(uy, bx))));
-    const C cb0 = fmul(p.owm0, bx), cb1 = fmul(p.owm1, bx);
-    const C cd0 = fmul(p.owm0, dby), cd1 = fmul(p.owm1, dby);
+template <typename C, typename V>
+__device__ __forceinline__ void collide_g(V gx[5], V gy[5], V ux, V uy, V bx, V by, V dby, const StepParams<C>& p) {
+    const auto om1m = p.om1m;
+    const auto ce = fmul(p.owm1, fmul(C(3), ffma(ux, by, -fmul(uy, bx))));
+    const auto cb0 = fmul(p.owm0, bx), cb1 = fmul(p.owm1, bx);
+    const auto cd0 = fmul(p.owm0, dby), cd1 = fmul(p.owm1, dby);
     gx[0] = ffma(om1m, gx[0], cb0);
     gx[1] = ffma(om1m, gx[1], cb1);
     gx[2] = ffma(om1m, gx[2], cb1 - ce);
@@ -122,21 +156,21 @@ __device__ __forceinline__ void collide_g(C gx[5], C gy[5], C ux, C uy, C bx, C 
 // source (Sec. V): S_a = 3 (e_a - u) . F  f^eq,hyd_a / rho
 // g^eq (Eq. geqmagneticfield): g^eq_ax = W_a (B_x - 3 e_ay E), g^eq_ay = W_a (B_y + 3 e_ax E),
 //   E = u_x B_y - u_y B_x.
-template <typename C>
-__device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const StepParams<C>& p) {
-    const C half = C(0.5), three = C(3), four5 = C(4.5), one5 = C(1.5);
+template <typename C, typename V>
+__device__ __forceinline__ void collide_node(V f[9], V gx[5], V gy[5], const StepParams<C>& p) {
+    const auto half = C(0.5), three = C(3), four5 = C(4.5), one5 = C(1.5);
 
     // a3: moments
-    const C drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    const C rho = C(1) + drho;
-    const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const C inv_rho = recip(rho);
-    const C ux = fmul(ffma(half, p.Fx, jx), inv_rho);
-    const C uy = fmul(jy, inv_rho);
-    const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
-    const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
-    const C by = p.B0 + dby;
+    const auto drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const auto rho = C(1) + drho;
+    const auto jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const auto jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const auto inv_rho = recip(rho);
+    const auto ux = fmul(ffma(half, p.Fx, jx), inv_rho);
+    const auto uy = fmul(jy, inv_rho);
+    const auto bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
+    const auto dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
+    const auto by = p.B0 + dby;
 
     // a4-a5 for f.  Post-collision deviation:
     //   f' = (1 - w) f + w f^eq,dev + (1 - 1/(2 tau)) S
@@ -144,20 +178,20 @@ __device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const Ste
     //   S_a = 3 (e_ax - u_x) F_x w_a (1 + bm1_a)
     // Maxwell-stress part M_a with q = B_y^2 - B0^2 = dby (2 B0 + dby):
     //   a=1,3: 2.25 w1 (q - Bx^2)   a=2,4: -2.25 w1 (q - Bx^2)   a=5,7: -9 w5 Bx By   a=6,8: +9 w5 Bx By
-    const C q = fmul(dby, p.B0 + by);
-    const C om13 = fmul(p.owf1, fmul(C(2.25), ffma(-bx, bx, q)));   // omega * M_1 = omega * M_3 = -omega * M_2
-    const C omxy = fmul(p.owf5, fmul(fmul(C(9), bx), by));         // omega * M_6 = omega * M_8 = -omega * M_5
-    const C usq = fmul(one5, ffma(ux, ux, fmul(uy, uy)));
-    const C s0 = fmul(p.sw0, -ux);                                  // source prefactors per e_x and weight
-    const C s1p = fmul(p.sw1, C(1) - ux), s1z = fmul(p.sw1, -ux), s1m = fmul(p.sw1, C(-1) - ux);
-    const C s5p = fmul(p.sw5, C(1) - ux), s5m = fmul(p.sw5, C(-1) - ux);
-    const C om1 = p.om1f;
+    const auto q = fmul(dby, p.B0 + by);
+    const auto om13 = fmul(p.owf1, fmul(C(2.25), ffma(-bx, bx, q)));   // omega * M_1 = omega * M_3 = -omega * M_2
+    const auto omxy = fmul(p.owf5, fmul(fmul(C(9), bx), by));         // omega * M_6 = omega * M_8 = -omega * M_5
+    const auto usq = fmul(one5, ffma(ux, ux, fmul(uy, uy)));
+    const auto s0 = fmul(p.sw0, -ux);                                  // source prefactors per e_x and weight
+    const auto s1p = fmul(p.sw1, C(1) - ux), s1z = fmul(p.sw1, -ux), s1m = fmul(p.sw1, C(-1) - ux);
+    const auto s5p = fmul(p.sw5, C(1) - ux), s5m = fmul(p.sw5, C(-1) - ux);
+    const auto om1 = p.om1f;
 #define LKS_DIR(A, EU, OW, OMAG, SA)                                                    \
     {                                                                                   \
-        const C eu = (EU);                                                              \
-        const C bm1 = ffma(ffma(four5, eu, three), eu, -usq);                           \
-        const C ofeq = ffma((OW), ffma(rho, bm1, drho), (OMAG));                        \
-        const C src = ffma((SA), bm1, (SA));                                            \
+        const auto eu = (EU);                                                              \
+        const auto bm1 = ffma(ffma(four5, eu, three), eu, -usq);                           \
+        const auto ofeq = ffma((OW), ffma(rho, bm1, drho), (OMAG));                        \
+        const auto src = ffma((SA), bm1, (SA));                                            \
         f[A] = ffma(om1, f[A], ofeq + src);                                             \
     }
     LKS_DIR(0, C(0), p.owf0, C(0), s0)
@@ -181,62 +215,62 @@ __device__ __forceinline__ void collide_node(C f[9], C gx[5], C gy[5], const Ste
 //              Pi_10 = rho U - F_x/2, Pi_01 = -F_y/2 with F = F_ext + J x B, J_z from the closed g
 //              at u = (U, 0) (J_z = 3 omega_m (Lambda_yx - Lambda_xy + 2 U B_y)); Pi_20 = rho (c^2 + U^2).
 // In both, the rest state satisfies the closure exactly, so the deviations need no constant terms.
-template <typename C, int COUPLING>
-__device__ __forceinline__ void wall_force_halves(const C gx[5], const C gy[5], C bx, C by, C U,
-                                                  const StepParams<C>& p, C& hfx, C& hfy) {
+template <typename C, int COUPLING, typename V>
+__device__ __forceinline__ void wall_force_halves(const V gx[5], const V gy[5], V bx, V by, C U,
+                                                  const StepParams<C>& p, V& hfx, V& hfy) {
     if (COUPLING == 1) {
-        const C jz = fmul(fmul(C(3), p.omega_m), ffma(fmul(C(2), U), by, (gx[2] - gx[4]) - (gy[1] - gy[3])));
+        const auto jz = fmul(fmul(C(3), p.omega_m), ffma(fmul(C(2), U), by, (gx[2] - gx[4]) - (gy[1] - gy[3])));
         hfx = fmul(C(0.5), ffma(-jz, by, p.Fx));
         hfy = fmul(C(0.5), fmul(jz, bx));
     } else {
-        hfx = C(0);
-        hfy = C(0);
+        hfx = zero_of<V>();
+        hfy = zero_of<V>();
     }
 }
 
-template <typename C, int COUPLING>
-__device__ __forceinline__ void moment_closure_bottom(C f[9], C gx[5], C gy[5], const WallCoef<C>& w,
+template <typename C, int COUPLING, typename V>
+__device__ __forceinline__ void moment_closure_bottom(V f[9], V gx[5], V gy[5], const WallCoef<C>& w,
                                                       const StepParams<C>& p) {
-    const C half = C(0.5), cs2 = C(1.0 / 3.0);
-    const C B0 = p.B0;
+    const auto half = C(0.5), cs2 = C(1.0 / 3.0);
+    const auto B0 = p.B0;
     gx[2] = ffma(w.r, gx[4], -fmul(w.bc, (gx[0] + gx[1]) + gx[3])) + w.kx;
     gy[2] = -(((gy[0] + gy[1]) + gy[3]) + gy[4]);
-    const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
-    const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
-    const C U = w.U;
-    C hfx, hfy;
+    const auto bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
+    const auto dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
+    const auto U = w.U;
+    V hfx, hfy;
     wall_force_halves<C, COUPLING>(gx, gy, bx, B0 + dby, U, p, hfx, hfy);
-    const C drho = ffma(C(2), (f[4] + f[7]) + f[8], (f[0] + f[1]) + f[3]) - hfy;
-    const C rho = C(1) + drho;
+    const auto drho = ffma(C(2), (f[4] + f[7]) + f[8], (f[0] + f[1]) + f[3]) - hfy;
+    const auto rho = C(1) + drho;
     // P - P_rest
-    const C uu = fmul(U, U);
-    C dP = ffma(drho, cs2 + uu, uu);
+    const auto uu = fmul(U, U);
+    auto dP = ffma(drho, cs2 + uu, uu);
     if (COUPLING == 0) dP = dP + ffma(-fmul(half, bx), bx, fmul(dby, ffma(half, dby, B0)));
-    const C rU = ffma(rho, U, -hfx);
+    const auto rU = ffma(rho, U, -hfx);
     f[2] = ((-dP + (f[1] + f[3])) + f[4]) + fmul(C(2), f[7] + f[8]) - hfy;
     f[5] = ffma(half, dP + rU, -(f[1] + f[8]));
     f[6] = ffma(half, dP - rU, -(f[3] + f[7]));
 }
 
 // Top: unknown f4, f7, f8, g4.
-template <typename C, int COUPLING>
-__device__ __forceinline__ void moment_closure_top(C f[9], C gx[5], C gy[5], const WallCoef<C>& w,
+template <typename C, int COUPLING, typename V>
+__device__ __forceinline__ void moment_closure_top(V f[9], V gx[5], V gy[5], const WallCoef<C>& w,
                                                    const StepParams<C>& p) {
-    const C half = C(0.5), cs2 = C(1.0 / 3.0);
-    const C B0 = p.B0;
+    const auto half = C(0.5), cs2 = C(1.0 / 3.0);
+    const auto B0 = p.B0;
     gx[4] = ffma(w.r, gx[2], -fmul(w.bc, (gx[0] + gx[1]) + gx[3])) + w.kx;
     gy[4] = -(((gy[0] + gy[1]) + gy[2]) + gy[3]);
-    const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
-    const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
-    const C U = w.U;
-    C hfx, hfy;
+    const auto bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
+    const auto dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
+    const auto U = w.U;
+    V hfx, hfy;
     wall_force_halves<C, COUPLING>(gx, gy, bx, B0 + dby, U, p, hfx, hfy);
-    const C drho = ffma(C(2), (f[2] + f[5]) + f[6], (f[0] + f[1]) + f[3]) + hfy;
-    const C rho = C(1) + drho;
-    const C uu = fmul(U, U);
-    C dP = ffma(drho, cs2 + uu, uu);
+    const auto drho = ffma(C(2), (f[2] + f[5]) + f[6], (f[0] + f[1]) + f[3]) + hfy;
+    const auto rho = C(1) + drho;
+    const auto uu = fmul(U, U);
+    auto dP = ffma(drho, cs2 + uu, uu);
     if (COUPLING == 0) dP = dP + ffma(-fmul(half, bx), bx, fmul(dby, ffma(half, dby, B0)));
-    const C rU = ffma(rho, U, -hfx);
+    const auto rU = ffma(rho, U, -hfx);
     f[4] = ((-dP + (f[1] + f[2])) + f[3]) + fmul(C(2), f[5] + f[6]) + hfy;
     f[7] = ffma(half, dP - rU, -(f[3] + f[6]));
     f[8] = ffma(half, dP + rU, -(f[1] + f[5]));
@@ -247,39 +281,39 @@ __device__ __forceinline__ void moment_closure_top(C f[9], C gx[5], C gy[5], con
 // half shift of rho u.  Lambda^(1) = Lambda - Lambda^(0)(u) and u = (j + F/2)/rho depend on each
 // other linearly; with k = 3 omega_m and D = Lambda_yx - Lambda_xy the exact solution is
 //   J_z = k [D + 2 (B_y (j_x + F_ext/2) - B_x j_y)/rho] / (1 + k |B|^2 / rho).
-template <typename C>
-__device__ __forceinline__ void collide_node_lorentz(C f[9], C gx[5], C gy[5], const StepParams<C>& p) {
-    const C half = C(0.5), three = C(3), four5 = C(4.5), one5 = C(1.5);
-    const C drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    const C rho = C(1) + drho;
-    const C jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    const C jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const C inv_rho = recip(rho);
-    const C bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
-    const C dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
-    const C by = p.B0 + dby;
-    const C k = fmul(three, p.omega_m);
-    const C D = (gx[2] - gx[4]) - (gy[1] - gy[3]);
-    const C jxp = ffma(half, p.Fx, jx);
-    const C num = fmul(k, ffma(fmul(C(2), inv_rho), ffma(by, jxp, -fmul(bx, jy)), D));
-    const C den = ffma(fmul(k, inv_rho), ffma(bx, bx, fmul(by, by)), C(1));
-    const C jz = num / den;
-    const C Fx = ffma(-jz, by, p.Fx), Fy = fmul(jz, bx);
-    const C ux = fmul(ffma(half, Fx, jx), inv_rho);
-    const C uy = fmul(ffma(half, Fy, jy), inv_rho);
-    const C usq = fmul(one5, ffma(ux, ux, fmul(uy, uy)));
-    const C ax = fmul(p.src3, Fx), ay = fmul(p.src3, Fy);
+template <typename C, typename V>
+__device__ __forceinline__ void collide_node_lorentz(V f[9], V gx[5], V gy[5], const StepParams<C>& p) {
+    const auto half = C(0.5), three = C(3), four5 = C(4.5), one5 = C(1.5);
+    const auto drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const auto rho = C(1) + drho;
+    const auto jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const auto jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const auto inv_rho = recip(rho);
+    const auto bx = ((gx[0] + gx[1]) + (gx[2] + gx[3])) + gx[4];
+    const auto dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
+    const auto by = p.B0 + dby;
+    const auto k = fmul(three, p.omega_m);
+    const auto D = (gx[2] - gx[4]) - (gy[1] - gy[3]);
+    const auto jxp = ffma(half, p.Fx, jx);
+    const auto num = fmul(k, ffma(fmul(C(2), inv_rho), ffma(by, jxp, -fmul(bx, jy)), D));
+    const auto den = ffma(fmul(k, inv_rho), ffma(bx, bx, fmul(by, by)), C(1));
+    const auto jz = num / den;
+    const auto Fx = ffma(-jz, by, p.Fx), Fy = fmul(jz, bx);
+    const auto ux = fmul(ffma(half, Fx, jx), inv_rho);
+    const auto uy = fmul(ffma(half, Fy, jy), inv_rho);
+    const auto usq = fmul(one5, ffma(ux, ux, fmul(uy, uy)));
+    const auto ax = fmul(p.src3, Fx), ay = fmul(p.src3, Fy);
     // (e_x - u_x) a_x and (e_y - u_y) a_y for e = -1, 0, +1
-    const C px0 = fmul(-ux, ax), pxp = fmul(C(1) - ux, ax), pxm = fmul(C(-1) - ux, ax);
-    const C py0 = fmul(-uy, ay), pyp = fmul(C(1) - uy, ay), pym = fmul(C(-1) - uy, ay);
-    const C w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w5 = C(1.0 / 36.0);
-    const C om1 = p.om1f;
+    const auto px0 = fmul(-ux, ax), pxp = fmul(C(1) - ux, ax), pxm = fmul(C(-1) - ux, ax);
+    const auto py0 = fmul(-uy, ay), pyp = fmul(C(1) - uy, ay), pym = fmul(C(-1) - uy, ay);
+    const auto w0 = C(4.0 / 9.0), w1 = C(1.0 / 9.0), w5 = C(1.0 / 36.0);
+    const auto om1 = p.om1f;
 #define LKS_DIRL(A, EU, OW, W, PX, PY)                                                  \
     {                                                                                   \
-        const C eu = (EU);                                                              \
-        const C bm1 = ffma(ffma(four5, eu, three), eu, -usq);                           \
-        const C ofeq = fmul((OW), ffma(rho, bm1, drho));                                \
-        const C sa = fmul((W), (PX) + (PY));                                            \
+        const auto eu = (EU);                                                              \
+        const auto bm1 = ffma(ffma(four5, eu, three), eu, -usq);                           \
+        const auto ofeq = fmul((OW), ffma(rho, bm1, drho));                                \
+        const auto sa = fmul((W), (PX) + (PY));                                            \
         f[A] = ffma(om1, f[A], ofeq + ffma(sa, bm1, sa));                               \
     }
     LKS_DIRL(0, C(0), p.owf0, w0, px0, py0)
@@ -295,8 +329,8 @@ __device__ __forceinline__ void collide_node_lorentz(C f[9], C gx[5], C gy[5], c
     collide_g(gx, gy, ux, uy, bx, by, dby, p);
 }
 
-template <typename C, int COUPLING>
-__device__ __forceinline__ void collide(C f[9], C gx[5], C gy[5], const StepParams<C>& p) {
+template <typename C, int COUPLING, typename V>
+__device__ __forceinline__ void collide(V f[9], V gx[5], V gy[5], const StepParams<C>& p) {
     if (COUPLING == 1)
         collide_node_lorentz<C>(f, gx, gy, p);
     else

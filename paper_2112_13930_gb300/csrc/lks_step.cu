@@ -241,10 +241,12 @@ static cudaError_t launch_typed(const void* fin, const void* gin, void* fout, vo
 }
 
 cudaError_t launch_step(int storage, int closure, const void* fin, const void* gin, void* fout, void* gout,
-                        const StepParams<double>& pd, cudaStream_t st) {
+                        const StepParams<double>& pd, cudaStream_t st, const StagedStep* ss) {
     if (storage == 0) return launch_typed<double, double>(fin, gin, fout, gout, pd, closure, st);
     StepParams<float> pf = convert_params<float>(pd);
     if (storage == 1) return launch_typed<float, float>(fin, gin, fout, gout, pf, closure, st);
+    if (ss && staged_step_applies(storage, pd.nx, 0))
+        return launch_step_staged(storage, closure, fin, gin, fout, gout, pf, *ss, st);
     const bool pairs = (pd.nx % 2) == 0;  // two nodes per thread need whole pairs in every row
     if (storage == 2)
         return pairs ? launch_pair<__nv_bfloat16>(fin, gin, fout, gout, pf, closure, st)

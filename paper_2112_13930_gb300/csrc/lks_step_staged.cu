@@ -1,0 +1,291 @@
+// lks_step_staged.cu -- the fused step of one lattice with 16-bit deviation storage, rows staged
+// through shared memory by the bulk-copy engine (two-buffer handles; nx a multiple of 8 and at least
+// kSegX).  Hot-path steps a1-a6 as in step_node_with (lks_device.cuh), with the same per-node
+// arithmetic: the results agree bit for bit with the one- and two-node kernels.
+//
+// A task is a row segment of up to kSegX nodes (x0 .. x0 + T - 1 of row y).  For each of the 19
+// population slots (f_0..8, g_x0..4, g_y0..4) a producer warp copies, one slot per lane, the segment
+// of the row the slot pulls from (y - e_y; a link-closure wall row takes its own row of the opposite
+// plane; a moment-closure wall row fetches nothing for the slots it reconstructs) into one of
+// kStages shared-memory stages, with a 16-byte halo on each side for the x-shifted slots (periodic in
+// x: wrapped copies at the row ends), completing on the stage's `full` mbarrier.  Sixteen consumer
+// warps take two x-adjacent nodes per thread as one float2 (packed FP32x2 arithmetic): 19 words of
+// the staged rows (byte_perm for the x shift), the wall closure, the collision, 19 packed words
+// stored; each warp then arrives on the stage's `empty` mbarrier, which the producer waits for
+// before it refills the stage.  Every wait is bounded (kWaitNs); one that runs out sets *err and
+// ends that warp's loop, and the producer waits, within the same limit, for its last copies to each
+// stage before it returns.
+//
+// One block of 16 consumer warps per SM with 1024-node tasks (2 KB copies) beat two blocks of 8
+// warps with 512-node tasks at 4096^2: 76-80 against 71-72 GLUPS (the copies per byte halve).  Rows
+// without a wall run a compile-time path without the closure code (BF16, moment closure: 79.8
+// against 76.1 GLUPS).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "lks_bulk.cuh"
+#include "lks_device.cuh"
+#include "lks_internal.h"
+#include "lks_packed.cuh"
+
+namespace lks {
+namespace {
+
+constexpr int kSegX = 1024;                      // nodes of a task: consumer threads x 2
+constexpr int kHaloW = 4;                        // halo words (8 elements = 16 bytes) per side
+constexpr int kSlotW = kSegX / 2 + 2 * kHaloW;   // words of a staged slot row
+constexpr int kSlots = 19;
+constexpr int kStages = 5;
+constexpr int kStageW = kSlots * kSlotW;
+constexpr int kConsumerWarps = kSegX / 64;
+constexpr int kThreads = kSegX / 2 + 32;         // consumers + the producer warp
+constexpr uint64_t kWaitNs = 1000000000ull;      // 1 s
+constexpr size_t kSmem = 128 + (size_t)kStages * kStageW * 4;
+
+// D2Q9 (f) and D2Q5 (g) directions of slot k: k < 9 is f_k, 9..13 is g_x,k-9, 14..18 is g_y,k-14.
+__host__ __device__ constexpr int dir_of(int k) { return k < 9 ? k : (k < 14 ? k - 9 : k - 14); }
+__host__ __device__ constexpr int ex9(int a) { return (a == 1 || a == 5 || a == 8) ? 1 : (a == 3 || a == 6 || a == 7) ? -1 : 0; }
+__host__ __device__ constexpr int ey9(int a) { return (a == 2 || a == 5 || a == 6) ? 1 : (a == 4 || a == 7 || a == 8) ? -1 : 0; }
+__host__ __device__ constexpr int opp9(int a) { return a == 0 ? 0 : (a <= 4 ? (a + 1) % 4 + 1 : (a + 1) % 4 + 5); }
+// plane of slot k's population table for direction a (f: a; g_x: a; g_y: 5 + a)
+__host__ __device__ constexpr int plane_of(int k, int a) { return k < 9 ? a : (k < 14 ? a : 5 + a); }
+
+template <typename S, int CLOSURE, int COUPLING>
+__global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __restrict__ fin, const S* __restrict__ gin,
+                                                                   S* __restrict__ fout, S* __restrict__ gout,
+                                                                   const StepParams<float> p, int* err) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm);
+    uint64_t* empty = full + kStages;
+    uint32_t* stage0 = reinterpret_cast<uint32_t*>(sm + 128);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nx = p.nx, ny = p.ny;
+    const int64_t N = p.N;
+    const int nseg = (nx + kSegX - 1) / kSegX;
+    const int64_t ntask = (int64_t)ny * nseg;
+    const int64_t G = gridDim.x, t0 = blockIdx.x;
+    const int64_t nmine = t0 < ntask ? (ntask - 1 - t0) / G + 1 : 0;  // tasks t0, t0 + G, ...
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps) {  // producer: lane k < 19 fetches slot k
+        const int k = lane < kSlots ? lane : 0;
+        const int a = dir_of(k), ex = ex9(a), ey = ey9(a);
+        const S* base = k < 9 ? fin : gin;
+        const S* bn = base + (int64_t)plane_of(k, a) * N;        // the slot's own direction
+        const S* bw = base + (int64_t)plane_of(k, opp9(a)) * N;  // the opposite one (link walls)
+        int64_t it = 0;
+        for (; it < nmine; ++it) {
+            const int s = (int)(it % kStages);
+            const int64_t u = it / kStages;
+            if (u > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)(u - 1) & 1u, kWaitNs)) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            const int64_t t = t0 + it * G;
+            const int y = (int)(t / nseg), x0 = (int)(t % nseg) * kSegX;
+            const int T = min(kSegX, nx - x0);
+            const bool wall = (ey == 1 && y == 0) || (ey == -1 && y == ny - 1);
+            uint32_t* dst = stage0 + s * kStageW + k * kSlotW;
+            // this lane's copies: (global element offset, shared word offset, elements)
+            int64_t g0 = 0, g1 = 0, g2 = 0;
+            int w0 = 0, w1 = 0, w2 = 0, n0 = 0, n1 = 0, n2 = 0;
+            if (lane < kSlots) {
+                if (wall) {
+                    if (CLOSURE == 0) {  // link: own row, opposite plane
+                        g0 = (int64_t)y * nx + x0;
+                        w0 = kHaloW;
+                        n0 = T;
+                    }
+                } else {
+                    const int64_t row = (int64_t)(y - ey) * nx;
+                    if (ex == 0) {
+                        g0 = row + x0, w0 = kHaloW, n0 = T;
+                    } else if (x0 >= 8 && x0 + T + 8 <= nx) {  // both halos in one copy
+                        g0 = row + x0 - 8, w0 = 0, n0 = T + 16;
+                    } else {
+                        g0 = row + x0, w0 = kHaloW, n0 = T;
+                        if (ex == 1) g1 = row + (x0 == 0 ? nx - 8 : x0 - 8), w1 = 0, n1 = 8;
+                        else g2 = row + (x0 + T == nx ? 0 : x0 + T), w2 = kHaloW + T / 2, n2 = 8;
+                    }
+                }
+            }
+            const uint32_t mine = 2u * (uint32_t)(n0 + n1 + n2);
+            const uint32_t bytes = __reduce_add_sync(0xffffffffu, mine);
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], bytes);
+            __syncwarp();
+            const S* src = (wall && CLOSURE == 0) ? bw : bn;
+            if (n0) bulk_g2s(dst + w0, src + g0, 2u * n0, &full[s]);
+            if (n1) bulk_g2s(dst + w1, src + g1, 2u * n1, &full[s]);
+            if (n2) bulk_g2s(dst + w2, src + g2, 2u * n2, &full[s]);
+        }
+        // no copy may be left in flight into this block's shared memory: wait for the last phase
+        // issued to each stage (already complete unless a consumer gave up)
+        for (int s = 0; s < kStages; ++s) {
+            if (it <= s) continue;
+            const int64_t u_last = (it - 1 - s) / kStages;
+            if (!mbar_wait_bounded(&full[s], (uint32_t)u_last & 1u, kWaitNs) && lane == 0) atomicExch(err, 1);
+        }
+        return;
+    }
+
+    // consumers: thread tid holds nodes x0 + 2 tid and x0 + 2 tid + 1 of the task's row
+    typedef Packed<S> P;
+    const int xw = kHaloW + tid;
+    for (int64_t it = 0; it < nmine; ++it) {
+        const int s = (int)(it % kStages);
+        if (!mbar_wait_bounded(&full[s], (uint32_t)(it / kStages) & 1u, kWaitNs)) {
+            atomicExch(err, 1);
+            break;
+        }
+        const int64_t t = t0 + it * G;
+        const int y = (int)(t / nseg), x0 = (int)(t % nseg) * kSegX;
+        const int T = min(kSegX, nx - x0);
+        if (2 * tid < T) {
+            const bool bottom = (y == 0), top = (y == ny - 1);
+            const uint32_t* st = stage0 + s * kStageW;
+            // rows without a wall (all but two) take a path with no closure code
+            auto body = [&](auto walls) {
+                constexpr bool W = decltype(walls)::value;
+                float2 v[kSlots];
+#pragma unroll
+                for (int k = 0; k < kSlots; ++k) {
+                    const int a = dir_of(k), ex = ex9(a), ey = ey9(a);
+                    const bool wall = W && ((ey == 1 && bottom) || (ey == -1 && top));
+                    const uint32_t* row = st + k * kSlotW;
+                    uint32_t w;
+                    if (wall || ex == 0)
+                        w = row[xw];
+                    else if (ex == 1)  // x <- x - 1 (high half of the word before), x + 1 <- x
+                        w = __byte_perm(row[xw - 1], row[xw], 0x5432);
+                    else  // x <- x + 1, x + 1 <- x + 2 (low half of the word after)
+                        w = __byte_perm(row[xw], row[xw + 1], 0x5432);
+                    v[k] = make_float2(P::lo(w), P::hi(w));
+                }
+                float2 f[9], gx[5], gy[5];
+#pragma unroll
+                for (int a = 0; a < 9; ++a) f[a] = v[a];
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    gx[a] = v[9 + a];
+                    gy[a] = v[14 + a];
+                }
+                // a2: wall closures (the link slots hold the node's own outgoing populations)
+                if (W) {
+                    if (CLOSURE == 0) {
+                        if (bottom) {
+                            const WallCoef<float>& w = p.bot;
+                            f[5] = f[5] + w.du;
+                            f[6] = f[6] - w.du;
+                            gx[2] = ffma(w.r, gx[2], w.kx);
+                            gy[2] = -gy[2];
+                        }
+                        if (top) {
+                            const WallCoef<float>& w = p.top;
+                            f[7] = f[7] - w.du;
+                            f[8] = f[8] + w.du;
+                            gx[4] = ffma(w.r, gx[4], w.kx);
+                            gy[4] = -gy[4];
+                        }
+                    } else {
+                        if (bottom) moment_closure_bottom<float, COUPLING>(f, gx, gy, p.bot, p);
+                        if (top) moment_closure_top<float, COUPLING>(f, gx, gy, p.top, p);
+                    }
+                }
+                // a3-a5 for both nodes, a6
+                collide<float, COUPLING>(f, gx, gy, p);
+                const int64_t q = ((int64_t)y * nx + x0) / 2 + tid;  // the pair's word in every plane
+                uint32_t* fo = reinterpret_cast<uint32_t*>(fout);
+                uint32_t* go = reinterpret_cast<uint32_t*>(gout);
+                const int64_t NP = N / 2;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) fo[a * NP + q] = P::pack(f[a].x, f[a].y);
+#pragma unroll
+                for (int a = 0; a < 5; ++a) go[a * NP + q] = P::pack(gx[a].x, gx[a].y);
+#pragma unroll
+                for (int a = 0; a < 5; ++a) go[(5 + a) * NP + q] = P::pack(gy[a].x, gy[a].y);
+            };
+            if (bottom || top)
+                body(std::true_type{});
+            else
+                body(std::false_type{});
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
+template <typename S, int CLOSURE, int COUPLING>
+cudaError_t prepare_one(int* blocks) {
+    cudaError_t e = cudaFuncSetAttribute(step_kernel_staged<S, CLOSURE, COUPLING>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    int occ = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel_staged<S, CLOSURE, COUPLING>, kThreads, kSmem);
+    if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
+    *blocks = occ;
+    return e;
+}
+
+template <typename S>
+cudaError_t prepare_typed(int* blocks) {
+    int b[4] = {0, 0, 0, 0};
+    cudaError_t e = prepare_one<S, 0, 0>(&b[0]);
+    if (e == cudaSuccess) e = prepare_one<S, 1, 0>(&b[1]);
+    if (e == cudaSuccess) e = prepare_one<S, 0, 1>(&b[2]);
+    if (e == cudaSuccess) e = prepare_one<S, 1, 1>(&b[3]);
+    *blocks = std::min(std::min(b[0], b[1]), std::min(b[2], b[3]));
+    return e;
+}
+
+template <typename S>
+void launch_typed_staged(const void* fin, const void* gin, void* fout, void* gout, const StepParams<float>& p,
+                         int closure, const StagedStep& ss, cudaStream_t st) {
+    const int64_t ntask = (int64_t)p.ny * ((p.nx + kSegX - 1) / kSegX);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntask, ss.grid);
+    const S* fi = (const S*)fin;
+    const S* gi = (const S*)gin;
+    S* fo = (S*)fout;
+    S* go = (S*)gout;
+    if (p.coupling == 0) {
+        if (closure == 0) step_kernel_staged<S, 0, 0><<<grid, kThreads, kSmem, st>>>(fi, gi, fo, go, p, ss.err);
+        else step_kernel_staged<S, 1, 0><<<grid, kThreads, kSmem, st>>>(fi, gi, fo, go, p, ss.err);
+    } else {
+        if (closure == 0) step_kernel_staged<S, 0, 1><<<grid, kThreads, kSmem, st>>>(fi, gi, fo, go, p, ss.err);
+        else step_kernel_staged<S, 1, 1><<<grid, kThreads, kSmem, st>>>(fi, gi, fo, go, p, ss.err);
+    }
+}
+
+}  // namespace
+
+bool staged_step_applies(int storage, int nx, int inplace) {
+    return storage >= 2 && !inplace && nx % 8 == 0 && nx >= kSegX;
+}
+
+cudaError_t prepare_staged_step(int storage, unsigned* grid) {
+    int dev = 0, sms = 0, blocks = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = storage == 2 ? prepare_typed<__nv_bfloat16>(&blocks) : prepare_typed<__half>(&blocks);
+    *grid = (unsigned)(sms * blocks);
+    return e;
+}
+
+cudaError_t launch_step_staged(int storage, int closure, const void* fin, const void* gin, void* fout, void* gout,
+                               const StepParams<float>& p, const StagedStep& ss, cudaStream_t st) {
+    if (storage == 2)
+        launch_typed_staged<__nv_bfloat16>(fin, gin, fout, gout, p, closure, ss, st);
+    else
+        launch_typed_staged<__half>(fin, gin, fout, gout, p, closure, ss, st);
+    return cudaGetLastError();
+}
+
+}  // namespace lks

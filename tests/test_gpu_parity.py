@@ -249,11 +249,13 @@ def test_full_size_perturbed_fp64_sampled_rows(lks):
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
 @pytest.mark.parametrize("closure", ["link", "moment"])
 def test_pair_kernel_bitwise_equals_single_node_kernel(lks, storage, closure):
-    """16-bit storage with even nx runs the two-nodes-per-thread kernel, odd nx the one-node kernel.
-    On an x-independent flow (rest start, body force and moving wall) every column of both must be
-    bit-identical: the per-node arithmetic is the same."""
+    """16-bit storage with even nx runs the two-nodes-per-thread kernel, odd nx the one-node kernel,
+    and nx a multiple of 8 of at least 1024 the staged kernel (rows through shared memory, packed
+    FP32x2 arithmetic): 1032 (a full and a ragged segment, wrapped halos), 2056 (a middle segment
+    with both halos in one copy).  On an x-independent flow (rest start, body force and moving wall)
+    every column of all of them must be bit-identical: the per-node arithmetic is the same."""
     out = []
-    for nx in (37, 38, 64):
+    for nx in (37, 38, 64, 1032, 2056):
         g = lks.Lattice(nx, 21, 0.7, 0.9, 0.02, 2e-5, closure, storage)
         g.set_walls(0.4, math.inf, 0.0, 0.04)
         g.step(150)
@@ -267,13 +269,15 @@ def test_pair_kernel_bitwise_equals_single_node_kernel(lks, storage, closure):
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
-def test_pair_kernel_perturbed_matches_oracle_one_step(lks, storage):
-    """Perturbed lattice with even nx spanning several warps and rows that do not fill a warp:
-    one step against the oracle within the one-step bound of the storage type."""
-    for nx, ny in ((38, 7), (130, 5), (2, 9)):
-        o, g = _pair(lks, nx, ny, "moment", storage, B0=0.02, Fx=1e-5, c=(0.4, 3.0), u=(0.0, 0.04), seed=3,
+@pytest.mark.parametrize("closure", ["link", "moment"])
+def test_pair_kernel_perturbed_matches_oracle_one_step(lks, storage, closure):
+    """Perturbed lattice with even nx spanning several warps and rows that do not fill a warp, and
+    the staged kernel's segment layouts (1032, 2056): one step against the oracle within the one-step
+    bound of the storage type."""
+    for nx, ny in ((38, 7), (130, 5), (2, 9), (1032, 6), (2056, 3)):
+        o, g = _pair(lks, nx, ny, closure, storage, B0=0.02, Fx=1e-5, c=(0.4, 3.0), u=(0.0, 0.04), seed=3,
                      amp=1e-2)
-        o0 = oracle.Oracle(nx, ny, 0.8, 0.8, 0.02, 1e-5, oracle.MOMENT)
+        o0 = oracle.Oracle(nx, ny, 0.8, 0.8, 0.02, 1e-5, oracle.LINK if closure == "link" else oracle.MOMENT)
         o.step(1)
         g.step(1)
         fg, gg = g.get_state()
@@ -343,7 +347,7 @@ def test_lorentz_reduced_precision(lks, storage, closure):
 
 def test_lorentz_pair_kernel_bitwise(lks):
     out = []
-    for nx in (37, 38):
+    for nx in (37, 38, 1032):
         g = lks.Lattice(nx, 21, 0.7, 0.9, 0.02, 2e-5, "moment", "f16", coupling="lorentz")
         g.set_walls(0.4, math.inf, 0.0, 0.04)
         g.step(150)
