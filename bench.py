@@ -148,8 +148,24 @@ def run_oracle_sample(n, seconds, phys):
             break
     dt = time.perf_counter() - t0
     mlups = n * n * steps / dt / 1e6
-    return {"value": round(mlups, 3), "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
-            "sample": "%d full steps of the %dx%d lattice (FP64, OpenMP over rows), %.1f s" % (steps, n, n, dt)}
+    cores = oracle.threads_used()
+    out = {"value": round(mlups, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d full steps of the %dx%d lattice (FP64, OpenMP over rows), %.1f s" % (steps, n, n, dt)}
+    # the same oracle on one thread: whole steps for about half the budget (at least one)
+    oracle.set_threads(1)
+    try:
+        s1, t0 = 0, time.perf_counter()
+        while True:
+            o.step(1)
+            s1 += 1
+            if time.perf_counter() - t0 >= seconds / 2:
+                break
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    out["single_thread"] = {"value": round(n * n * s1 / dt1 / 1e6, 3), "unit": UNIT, "cores": 1,
+                            "sample": "%d full steps of the %dx%d lattice, %.1f s" % (s1, n, n, dt1)}
+    return out
 
 
 def bench_reference(args):
