@@ -175,7 +175,7 @@ struct lks_handle {
     double* node_stage = nullptr;  // lazily allocated 5*N doubles for per-node host moments
     double* host_small = nullptr;  // pinned 8 doubles
     int* flag = nullptr;
-    bool staged = false;              // two-buffer, 16-bit, nx % 8 == 0, nx >= 1024: the staged step
+    bool staged = false;              // 16-bit, nx % 8 == 0, nx >= 1024: the staged kernels
     lks::StagedStep ss = {nullptr, 0};
     double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
     StepParams<double> sp;
@@ -227,7 +227,9 @@ void drop_graphs(lks_handle* h) {
 // One step.  Two-buffer handles step from buffer `src` into the other; in-place handles take
 // phase `src` of a pair (0: pull and push to the neighbours, 1: own slots) on their one buffer.
 cudaError_t step_once(lks_handle* h, int src, cudaStream_t st) {
-    if (h->p.inplace) return lks::launch_step_aa(h->p.storage, h->p.closure, src, h->f[0], h->g[0], h->sp, st);
+    if (h->p.inplace)
+        return lks::launch_step_aa(h->p.storage, h->p.closure, src, h->f[0], h->g[0], h->sp, st,
+                                   h->staged ? &h->ss : nullptr);
     return lks::launch_step(h->p.storage, h->p.closure, h->f[src], h->g[src], h->f[src ^ 1], h->g[src ^ 1], h->sp, st,
                             h->staged ? &h->ss : nullptr);
 }
@@ -307,7 +309,7 @@ lks_status lks_create(const lks_params* p, lks_handle** out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
     if (e == cudaSuccess && lks::staged_step_applies(p->storage, p->nx, p->inplace)) {
-        e = lks::prepare_staged_step(p->storage, &h->ss.grid);
+        e = lks::prepare_staged_step(p->storage, p->inplace, &h->ss.grid);
         h->ss.err = h->flag;
         h->staged = e == cudaSuccess;
     }

@@ -240,14 +240,21 @@ __device__ __forceinline__ void moment_closure_bottom(V f[9], V gx[5], V gy[5], 
     const auto U = w.U;
     V hfx, hfy;
     wall_force_halves<C, COUPLING>(gx, gy, bx, B0 + dby, U, p, hfx, hfy);
-    const auto drho = ffma(C(2), (f[4] + f[7]) + f[8], (f[0] + f[1]) + f[3]) - hfy;
+    // With the Maxwell coupling the force halves are zero and left out (a constant zero in an fma
+    // lets the compiler turn it into a product it may fuse with the next sum, and the one- and
+    // two-node forms would then round differently).
+    V drho = ffma(C(2), (f[4] + f[7]) + f[8], (f[0] + f[1]) + f[3]);
+    if constexpr (COUPLING == 1) drho = drho - hfy;
     const auto rho = C(1) + drho;
     // P - P_rest
     const auto uu = fmul(U, U);
     auto dP = ffma(drho, cs2 + uu, uu);
     if (COUPLING == 0) dP = dP + ffma(-fmul(half, bx), bx, fmul(dby, ffma(half, dby, B0)));
-    const auto rU = ffma(rho, U, -hfx);
-    f[2] = ((-dP + (f[1] + f[3])) + f[4]) + fmul(C(2), f[7] + f[8]) - hfy;
+    V rU;
+    if constexpr (COUPLING == 1) rU = ffma(rho, U, -hfx);
+    else rU = fmul(rho, U);
+    f[2] = ((-dP + (f[1] + f[3])) + f[4]) + fmul(C(2), f[7] + f[8]);
+    if constexpr (COUPLING == 1) f[2] = f[2] - hfy;
     f[5] = ffma(half, dP + rU, -(f[1] + f[8]));
     f[6] = ffma(half, dP - rU, -(f[3] + f[7]));
 }
@@ -265,13 +272,17 @@ __device__ __forceinline__ void moment_closure_top(V f[9], V gx[5], V gy[5], con
     const auto U = w.U;
     V hfx, hfy;
     wall_force_halves<C, COUPLING>(gx, gy, bx, B0 + dby, U, p, hfx, hfy);
-    const auto drho = ffma(C(2), (f[2] + f[5]) + f[6], (f[0] + f[1]) + f[3]) + hfy;
+    V drho = ffma(C(2), (f[2] + f[5]) + f[6], (f[0] + f[1]) + f[3]);
+    if constexpr (COUPLING == 1) drho = drho + hfy;
     const auto rho = C(1) + drho;
     const auto uu = fmul(U, U);
     auto dP = ffma(drho, cs2 + uu, uu);
     if (COUPLING == 0) dP = dP + ffma(-fmul(half, bx), bx, fmul(dby, ffma(half, dby, B0)));
-    const auto rU = ffma(rho, U, -hfx);
-    f[4] = ((-dP + (f[1] + f[2])) + f[3]) + fmul(C(2), f[5] + f[6]) + hfy;
+    V rU;
+    if constexpr (COUPLING == 1) rU = ffma(rho, U, -hfx);
+    else rU = fmul(rho, U);
+    f[4] = ((-dP + (f[1] + f[2])) + f[3]) + fmul(C(2), f[5] + f[6]);
+    if constexpr (COUPLING == 1) f[4] = f[4] + hfy;
     f[7] = ffma(half, dP - rU, -(f[3] + f[6]));
     f[8] = ffma(half, dP + rU, -(f[1] + f[5]));
 }

@@ -59,19 +59,22 @@ inline int interleave_row(int storage, int nx, int inplace) {
     return (inplace && storage >= 2 && (nx % 2) == 0) ? nx : 0;
 }
 
-// The staged 16-bit step (lks_step_staged.cu): rows staged through shared memory by bulk copies.
-// It applies to two-buffer handles with 16-bit storage, nx a multiple of 8 and nx >= 1024; err is a
-// device word set when one of its bounded waits runs out, grid the number of resident blocks.
+// The staged 16-bit steps (lks_step_staged.cu): rows staged through shared memory by bulk copies.
+// They apply to 16-bit storage with nx a multiple of 8 and nx >= 1024: the whole step of a
+// two-buffer handle, phase 0 of an in-place handle's pair of steps.  err is a device word set when
+// one of their bounded waits runs out, grid the number of resident blocks.
 struct StagedStep {
     int* err;
     unsigned grid;
 };
 bool staged_step_applies(int storage, int nx, int inplace);
-// Opt the storage type's staged kernels into their shared memory (before any graph capture) and
-// return the grid that keeps one wave of blocks resident.
-cudaError_t prepare_staged_step(int storage, unsigned* grid);
+// Opt the storage type's staged kernels (two-buffer or in-place) into their shared memory (before any
+// graph capture) and return the grid that keeps one wave of blocks resident.
+cudaError_t prepare_staged_step(int storage, int inplace, unsigned* grid);
 cudaError_t launch_step_staged(int storage, int closure, const void* fin, const void* gin, void* fout, void* gout,
                                const StepParams<float>& p, const StagedStep& ss, cudaStream_t st);
+cudaError_t launch_step_aa_staged(int storage, int closure, void* f, void* g, const StepParams<float>& p,
+                                  const StagedStep& ss, cudaStream_t st);
 
 // One fused step: (fin, gin) -> (fout, gout) on stream st; with ss, 16-bit storage takes the staged
 // kernel where it applies.
@@ -79,7 +82,7 @@ cudaError_t launch_step(int storage, int closure, const void* fin, const void* g
                         const StepParams<double>& p, cudaStream_t st, const StagedStep* ss = nullptr);
 // In-place (one-buffer) step, phase 0 or 1 of a pair (lks_aa.cuh); f, g are the single buffers.
 cudaError_t launch_step_aa(int storage, int closure, int phase, void* f, void* g, const StepParams<double>& pd,
-                           cudaStream_t st);
+                           cudaStream_t st, const StagedStep* ss = nullptr);
 
 // Initial equilibrium state (deviation form) with the counter-based perturbation.
 cudaError_t launch_init(int storage, void* f, void* g, int nx, int ny, double B0, uint64_t seed, double amp,

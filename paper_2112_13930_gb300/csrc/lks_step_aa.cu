@@ -286,7 +286,9 @@ static cudaError_t launch_aa_phase(int storage, int closure, void* f, void* g, c
 }
 
 cudaError_t launch_step_aa(int storage, int closure, int phase, void* f, void* g, const StepParams<double>& pd,
-                           cudaStream_t st) {
+                           cudaStream_t st, const StagedStep* ss) {
+    if (phase == 0 && ss && staged_step_applies(storage, pd.nx, 1))
+        return launch_step_aa_staged(storage, closure, f, g, convert_params<float>(pd), *ss, st);
     return phase == 0 ? launch_aa_phase<0>(storage, closure, f, g, pd, st)
                       : launch_aa_phase<1>(storage, closure, f, g, pd, st);
 }

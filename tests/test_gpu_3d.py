@@ -207,3 +207,24 @@ def test_staged_pair_path_bitwise_equals_one_node_kernel(l3, storage):
         out.append((f[:, 0, :, 0].copy(), gg[:, :, 0, :, 0].copy()))
         g.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_kernels_agree_bitwise_on_a_tiled_perturbed_state(l3, storage):
+    """nx = 12 runs the one-node kernel, nx = 24 the staged one (two nodes per thread on FP32x2): the
+    wide lattice started from the narrow one's perturbed state tiled twice in x stays that state
+    tiled, bit for bit, with every node carrying its own values."""
+    o, a, _, _ = _pair(l3, 12, 6, 3, (0.3, 2.0), (0.01, 0.04), storage, seed=9)
+    b = l3.Lattice3D(24, 6, 3, 0.8, 0.7, 0.02, 2e-6, storage)
+    b.set_walls(0.3, 2.0, 0.01, 0.04)
+    f, g = a.get_state()
+    b.set_state(np.concatenate([f, f], axis=-1), np.concatenate([g, g], axis=-1))
+    for n in (1, 9):
+        a.step(n)
+        b.step(n)
+        fa, ga = a.get_state()
+        fb, gb = b.get_state()
+        assert np.array_equal(fb, np.concatenate([fa, fa], axis=-1)), n
+        assert np.array_equal(gb, np.concatenate([ga, ga], axis=-1)), n
+    a.close()
+    b.close()

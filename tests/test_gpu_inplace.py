@@ -55,8 +55,11 @@ CASES = [
     # nx, ny: 1D grid with odd nx; nx = 1 (the x-neighbours are the node itself); 2D grid with a
     # ragged last block (300 = 256 + 44); ny = 3, the smallest moment-based channel.  16-bit
     # storage with even nx takes the two-nodes-per-thread kernels: 24 pairs per row on the 1D grid
-    # (warps spanning two rows), 65 pairs on the 2D grid (one active lane in the last warp)
-    (37, 9), (1, 12), (300, 7), (64, 3), (48, 10), (130, 5),
+    # (warps spanning two rows), 65 pairs on the 2D grid (one active lane in the last warp).  16-bit
+    # storage with nx a multiple of 8 and at least 1024 stages rows through shared memory (phase 0
+    # in place, the whole step with two buffers): 1032 (a full and a ragged segment, halos wrapped
+    # across the row edges), 2056 (a middle segment with both halos in one copy)
+    (37, 9), (1, 12), (300, 7), (64, 3), (48, 10), (130, 5), (1032, 5), (2056, 3),
 ]
 
 
