@@ -738,6 +738,41 @@ def bench_validation(args):
     return 0
 
 
+def bench_c2(args):
+    """The timing matrix of the shear-driven 4096 x 4096 channel: moment-based closure, top wall at
+    U_w = 0.05, bottom at rest, tau_f = tau_m = 0.8, Ha in {5, 20, 50} (B0 = Ha 0.1 / 2047.5) and the
+    same c on both walls in {0, 0.01, 1, 100, 1e6}, from rest: 200 warm-up steps, then the median of
+    3 timed runs (FP32: 5000 steps each; FP64, bound by the FP64 pipe: --c2-fp64-steps each)."""
+    import numpy as np
+    import torch
+    from paper_2112_13930_gb300 import build, lks
+    torch.cuda.set_device(0)
+    build.build()
+    lks.load()
+    stream = torch.cuda.current_stream()
+    n, a = 4096, 2047.5
+    rows = []
+    for storage, steps in (("f32", 5000), ("f64", args.c2_fp64_steps)):
+        for ha in (5.0, 20.0, 50.0):
+            lat = lks.Lattice(n, n, 0.8, 0.8, ha * 0.1 / a, 0.0, "moment", storage)
+            for c in (0.0, 0.01, 1.0, 100.0, 1e6):
+                lat.set_walls(c, c, 0.0, 0.05)
+                lat.step(200)
+                t = sorted(_time_steps(lat, steps, stream) for _ in range(3))[1]
+                rows.append({"storage": storage, "Ha": ha, "c": c, "steps": steps,
+                             "mlups": round(n * n * steps / t / 1e6, 1)})
+            lat.close()
+            del lat
+            torch.cuda.empty_cache()
+    out = {"workload": "c2", "config": {"n": n, "closure": "moment", "u_top": 0.05, "tau": 0.8,
+                                        "warmup": 200, "repeats": 3}, "points": rows}
+    for st in ("f32", "f64"):
+        v = [r["mlups"] for r in rows if r["storage"] == st]
+        out[st] = {"min": min(v), "median": float(np.median(v)), "max": max(v)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def bench_c1(args):
     """Body-force Hartmann channel, 4 x 65 nodes, walls at y = +-a with the Shercliff condition
     (link-based closure), B0 from Ha = 10, c = 0.1, tau_f = tau_m = 0.8, FP64, 2e4 steps: GPU wall
@@ -808,6 +843,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--storage", choices=["f32", "f64", "bf16", "f16"], default="f32")
+    ap.add_argument("--c2-fp64-steps", type=int, default=300, help="--workload c2: FP64 steps per timed run")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--inplace", action="store_true",
                     help="time the in-place (one-buffer) step instead of the two-buffer step")
@@ -817,7 +853,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--workload", choices=["main", "c1", "precision", "sweep", "serve", "validation", "d3"],
+    ap.add_argument("--workload", choices=["main", "c1", "c2", "precision", "sweep", "serve", "validation", "d3"],
                     default="main")
     ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 5], default=None,
                     help="preset of the five benchmark configurations: 1 = c1, 2 = main, 3 = precision, "
@@ -849,6 +885,8 @@ def main():
         args.workload = {1: "c1", 2: "main", 3: "precision", 4: "sweep", 5: "serve"}[args.config]
     if args.impl == "reference":
         return bench_reference(args)
+    if args.workload == "c2":
+        return bench_c2(args)
     if args.workload == "c1":
         return bench_c1(args)
     if args.workload == "precision":
