@@ -462,17 +462,19 @@ def bench_precision(args):
                                                "B0": b0, "Fx": fx, "seed": seed, "perturb_amp": amp}}
 
     stream = torch.cuda.current_stream()
-    mlups = {}
-    fields = {}
     steps_err = args.precision_steps
-    for st in ("f64", "f32", "f16", "bf16"):
-        lat = lks.Lattice(n, n, tau, tau, b0, fx, closure, st, seed=seed, perturb_amp=amp)
-        lat.set_walls(c, c)
-        if st == "f64":
-            # parity of the FP64 path on sampled rows against the oracle (2 steps of the full lattice)
-            if not args.skip_cpu:
+
+    def run(cl, b0c, fxc, check_oracle):
+        """MLUPS per storage type and the error of each against the FP64 run after steps_err steps."""
+        mlups, fields = {}, {}
+        for st in ("f64", "f32", "f16", "bf16"):
+            lat = lks.Lattice(n, n, tau, tau, b0c, fxc, cl, st, seed=seed, perturb_amp=amp)
+            lat.set_walls(c, c)
+            if st == "f64" and check_oracle and not args.skip_cpu:
+                # parity of the FP64 path on sampled rows against the oracle (2 steps of the full lattice)
                 import oracle
-                o = oracle.Oracle(n, n, tau, tau, b0, fx, oracle.LINK, c, c, seed=seed, perturb_amp=amp)
+                o = oracle.Oracle(n, n, tau, tau, b0c, fxc, oracle.LINK if cl == "link" else oracle.MOMENT, c, c,
+                                  seed=seed, perturb_amp=amp)
                 o.step(2)
                 lat.step(2)
                 mo = o.moments()
@@ -485,30 +487,40 @@ def bench_precision(args):
                 out["fp64_vs_oracle_2_steps_sampled_rows"] = err
                 del o, mo, mg
                 lat.close()
-                lat = lks.Lattice(n, n, tau, tau, b0, fx, closure, st, seed=seed, perturb_amp=amp)
+                lat = lks.Lattice(n, n, tau, tau, b0c, fxc, cl, st, seed=seed, perturb_amp=amp)
                 lat.set_walls(c, c)
-        k = 50 if st == "f64" else 200
-        lat.step(5)
-        t = _time_steps(lat, k, stream)
-        mlups[st] = round(n * n * k / t / 1e6, 1)
-        lat.step(steps_err - 5 - k)
-        m = torch.empty((5, n, n), dtype=torch.float64, device="cuda")
-        lat.moments_device(m)
-        torch.cuda.synchronize()
-        fields[st] = (m[1].clone(), m[3].clone())
-        del m
-        lat.close()
+            k = 50 if st == "f64" else 200
+            lat.step(5)
+            t = _time_steps(lat, k, stream)
+            mlups[st] = round(n * n * k / t / 1e6, 1)
+            lat.step(steps_err - 5 - k)
+            m = torch.empty((5, n, n), dtype=torch.float64, device="cuda")
+            lat.moments_device(m)
+            torch.cuda.synchronize()
+            fields[st] = (m[1].clone(), m[3].clone())
+            del m
+            lat.close()
+            torch.cuda.empty_cache()
+        errs = {}
+        u64, b64 = fields["f64"]
+        for st in ("f32", "f16", "bf16"):
+            u, b = fields[st]
+            errs[st] = {"u_x_relmax": float((u - u64).abs().max() / u64.abs().max()),
+                        "u_x_rel_rms": float(((u - u64) ** 2).mean().sqrt() / u64.abs().max()),
+                        "B_x_relmax": float((b - b64).abs().max() / b64.abs().max()),
+                        "B_x_rel_rms": float(((b - b64) ** 2).mean().sqrt() / b64.abs().max())}
+        del fields
         torch.cuda.empty_cache()
-    errs = {}
-    u64, b64 = fields["f64"]
-    for st in ("f32", "f16", "bf16"):
-        u, b = fields[st]
-        errs[st] = {"u_x_relmax": float((u - u64).abs().max() / u64.abs().max()),
-                    "u_x_rel_rms": float(((u - u64) ** 2).mean().sqrt() / u64.abs().max()),
-                    "B_x_relmax": float((b - b64).abs().max() / b64.abs().max()),
-                    "B_x_rel_rms": float(((b - b64) ** 2).mean().sqrt() / b64.abs().max())}
-    del fields
-    torch.cuda.empty_cache()
+        return mlups, errs
+
+    mlups, errs = run(closure, b0, fx, True)
+    # the same physics with the moment-based closure (walls on the node rows: a = (n - 1)/2)
+    am = (n - 1) / 2
+    b0m = ha * nu / am
+    fxm = 0.01 * nu / (am * am * ustar0)
+    mlups_m, errs_m = run("moment", b0m, fxm, False)
+    out["moment"] = {"B0": b0m, "Fx": fxm, "mlups": mlups_m,
+                     "error_vs_fp64_after_%d_steps" % steps_err: errs_m}
     # analytic comparison on a 4 x 513 channel of the same physics (Ha, c, tau, u_c = 0.01)
     ny = 513
     a2 = ny / 2
