@@ -46,6 +46,12 @@
  * Errors: every call returns an lks_status; LKS_OK is 0.  After an error,
  * lks_last_error(h) (or lks_last_error(NULL) for handle-less calls) gives a
  * one-line message.  A state that became non-finite gives LKS_EUNSTABLE.
+ *
+ * 16-bit storage with nx a multiple of 8 and nx >= 1024 steps through kernels
+ * that stage rows in shared memory with the bulk-copy engine (the whole step
+ * with two buffers, the first step of each in-place pair).  Their waits are
+ * bounded (1 s); a wait that ran out makes the next synchronising call
+ * (lks_sync, lks_moments, lks_residual, lks_get_state) return LKS_ETIMEOUT.
  */
 #ifndef LKS_H_
 #define LKS_H_
