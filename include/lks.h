@@ -187,12 +187,14 @@ lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int
 
 /* Copy the state out as FP64 absolute populations (deviation + rest
  * equilibrium): host_f 9 x ny x nx, host_g 2 x 5 x ny x nx, layouts as above.
- * Synchronises. */
+ * Converts 2^20 nodes at a time through a staging buffer of 19 x 2^20 doubles
+ * (152 MB; fewer for smaller lattices) that the handle allocates on first use and
+ * keeps until lks_destroy; LKS_ENOMEM if that allocation fails.  Synchronises. */
 lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g);
 
 /* Replace the state by FP64 absolute populations from host memory (same
  * layout as lks_get_state), rounded to the storage type; resets the step
- * counter and the residual snapshot.  Synchronises. */
+ * counter and the residual snapshot.  Same staging buffer.  Synchronises. */
 lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host_g);
 
 /* Block until all work of the handle has finished; reports asynchronous errors. */

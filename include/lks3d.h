@@ -89,11 +89,13 @@ lks_status lks3_run_to_steady(lks3_handle* h, double tol, int64_t check_every, i
                               int64_t* steps_out, double* r_out);
 
 /* State as FP64 absolute populations (deviation + rest): host_f 19 x N, host_g 21 x N.
- * Synchronises; uses a temporary device buffer of 40 N doubles. */
+ * Converts 2^20 nodes at a time through a staging buffer of 40 x 2^20 doubles (335 MB; fewer
+ * for smaller lattices) that the handle allocates on first use and keeps until lks3_destroy;
+ * LKS_ENOMEM if that allocation fails.  Synchronises. */
 lks_status lks3_get_state(lks3_handle* h, double* host_f, double* host_g);
 
 /* Replace the state by FP64 absolute populations (rounded to the storage type); resets the step
- * counter and the residual snapshot.  Synchronises; temporary device buffer as above. */
+ * counter and the residual snapshot.  Synchronises; same staging buffer. */
 lks_status lks3_set_state(lks3_handle* h, const double* host_f, const double* host_g);
 
 lks_status lks3_sync(lks3_handle* h);

@@ -576,12 +576,13 @@ __device__ void node_moments3<double>(const double* f, const double* g, int64_t 
 }
 
 template <typename S>
-__global__ void moments3_kernel(const S* f, const S* g, int64_t N, double B0, double Fx, double* out) {
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+__global__ void moments3_kernel(const S* f, const S* g, int64_t N, int64_t n0, int64_t M, double B0, double Fx,
+                                double* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         double m[7];
-        node_moments3<S>(f, g, N, n, B0, Fx, m);
+        node_moments3<S>(f, g, N, n0 + i, B0, Fx, m);
 #pragma unroll
-        for (int k = 0; k < 7; ++k) out[k * N + n] = m[k];
+        for (int k = 0; k < 7; ++k) out[k * M + i] = m[k];
     }
 }
 
@@ -656,25 +657,28 @@ __global__ void residual3_final(const double* partial, int nb, double* out) {
         for (int c = 0; c < 4; ++c) out[c] = red[c][0];
 }
 
-// Absolute FP64 populations <-> stored deviations.  rest_f: 19 FP64 rest values; g rest is
-// W_a B0 for the y component and 0 otherwise.
+// Absolute FP64 populations <-> stored deviations, for the M nodes n0 .. n0+M-1 of the N-node
+// state; the FP64 side holds 40 planes of M values (19 of f, then 21 of g).  rest_f: 19 FP64 rest
+// values; g rest is W_a B0 for the y component and 0 otherwise.
 template <typename S, typename C>
-__global__ void to_abs3_kernel(const S* f, const S* g, int64_t N, const double* rest_f, double B0, double* of,
-                               double* og) {
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-        for (int a = 0; a < 19; ++a) of[a * N + n] = (double)load_s<S, C>(f + a * N + n) + rest_f[a];
+__global__ void to_abs3_kernel(const S* f, const S* g, int64_t N, int64_t n0, int64_t M, const double* rest_f,
+                               double B0, double* of, double* og) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = n0 + i;
+        for (int a = 0; a < 19; ++a) of[a * M + i] = (double)load_s<S, C>(f + a * N + n) + rest_f[a];
         for (int k = 0; k < 21; ++k)
-            og[k * N + n] = (double)load_s<S, C>(g + k * N + n) + (k / 7 == 1 ? w7(k % 7) * B0 : 0.0);
+            og[k * M + i] = (double)load_s<S, C>(g + k * N + n) + (k / 7 == 1 ? w7(k % 7) * B0 : 0.0);
     }
 }
 
 template <typename S, typename C>
-__global__ void from_abs3_kernel(const double* inf, const double* ing, int64_t N, const double* rest_f, double B0,
-                                 S* f, S* g) {
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-        for (int a = 0; a < 19; ++a) store_s<S, C>(f + a * N + n, (C)(inf[a * N + n] - rest_f[a]));
+__global__ void from_abs3_kernel(const double* inf, const double* ing, int64_t N, int64_t n0, int64_t M,
+                                 const double* rest_f, double B0, S* f, S* g) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = n0 + i;
+        for (int a = 0; a < 19; ++a) store_s<S, C>(f + a * N + n, (C)(inf[a * M + i] - rest_f[a]));
         for (int k = 0; k < 21; ++k)
-            store_s<S, C>(g + k * N + n, (C)(ing[k * N + n] - (k / 7 == 1 ? w7(k % 7) * B0 : 0.0)));
+            store_s<S, C>(g + k * N + n, (C)(ing[k * M + i] - (k / 7 == 1 ? w7(k % 7) * B0 : 0.0)));
     }
 }
 
@@ -744,6 +748,7 @@ struct lks3_handle {
     bool staged = false;       // 16-bit storage with nx % 8 == 0: step3_staged_kernel
     unsigned staged_grid = 0;  // resident blocks of it on the device
     double* host4 = nullptr;  // pinned
+    double* state_stage = nullptr;  // 40 * min(N, 2^20) doubles for state and moment transfers, on first use
     double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
     int64_t steps = 0;
     std::string err;
@@ -948,6 +953,24 @@ lks_status lks3_step(lks3_handle* h, int64_t n) {
 
 int64_t lks3_steps_taken(const lks3_handle* h) { return h ? h->steps : -1; }
 
+// State transfers and per-node host moments convert kStateChunk3 nodes at a time through a staging
+// buffer the handle keeps, so their device memory stays bounded (335 MB) whatever the lattice size.
+constexpr int64_t kStateChunk3 = int64_t(1) << 20;
+
+static lks_status state_stage3(lks3_handle* h, int64_t* chunk) {
+    const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
+    *chunk = N < kStateChunk3 ? N : kStateChunk3;
+    if (!h->state_stage) {
+        cudaError_t e = cudaMalloc((void**)&h->state_stage, 40 * (size_t)*chunk * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->state_stage = nullptr;
+            return fail3(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
+        }
+    }
+    return LKS_OK;
+}
+
 lks_status lks3_moments(lks3_handle* h, int what, double* host_out) {
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_out) return fail3(h, LKS_EINVAL, "host_out is NULL");
@@ -961,19 +984,19 @@ lks_status lks3_moments(lks3_handle* h, int what, double* host_out) {
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(host_out, h->prof, 7 * (size_t)p.ny * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     } else if (what == LKS_MOMENTS_NODES) {
-        double* tmp = nullptr;
-        e = cudaMalloc((void**)&tmp, 7 * (size_t)N * sizeof(double));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail3(h, LKS_ENOMEM, "cudaMalloc of the moment staging buffer failed");
+        int64_t M = 0;
+        if (lks_status s = state_stage3(h, &M)) return s;
+        double* st = h->state_stage;
+        e = cudaSuccess;
+        for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
+            const int64_t m = N - n0 < M ? N - n0 : M;
+            LKS3_DISPATCH(p.storage, (moments3_kernel<S><<<grid_for(m), 256, 0, h->stream>>>(
+                                         (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, n0, m, p.B0, p.Fx, st)));
+            e = cudaGetLastError();
+            for (int k = 0; k < 7 && e == cudaSuccess; ++k)
+                e = cudaMemcpyAsync(host_out + k * N + n0, st + k * m, m * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream);
         }
-        LKS3_DISPATCH(p.storage, (moments3_kernel<S><<<grid_for(N), 256, 0, h->stream>>>(
-                                     (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, p.B0, p.Fx, tmp)));
-        e = cudaGetLastError();
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(host_out, tmp, 7 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        cudaFree(tmp);
     } else {
         return fail3(h, LKS_EINVAL, "bad 'what'");
     }
@@ -1032,21 +1055,22 @@ lks_status lks3_get_state(lks3_handle* h, double* host_f, double* host_g) {
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail3(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
-    double* tmp = nullptr;
-    cudaError_t e = cudaMalloc((void**)&tmp, 40 * (size_t)N * sizeof(double));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail3(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
+    int64_t M = 0;
+    if (lks_status s = state_stage3(h, &M)) return s;
+    double* st = h->state_stage;
+    cudaError_t e = cudaSuccess;
+    for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
+        const int64_t m = N - n0 < M ? N - n0 : M;
+        LKS3_DISPATCH(h->p.storage, (to_abs3_kernel<S, C><<<grid_for(m), 256, 0, h->stream>>>(
+                                        (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, n0, m, h->rest, h->p.B0,
+                                        st, st + 19 * m)));
+        e = cudaGetLastError();
+        for (int a = 0; a < 40 && e == cudaSuccess; ++a) {
+            double* dst = a < 19 ? host_f + a * N + n0 : host_g + (a - 19) * N + n0;
+            e = cudaMemcpyAsync(dst, st + a * m, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        }
     }
-    LKS3_DISPATCH(h->p.storage, (to_abs3_kernel<S, C><<<grid_for(N), 256, 0, h->stream>>>(
-                                    (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, h->rest, h->p.B0, tmp,
-                                    tmp + 19 * N)));
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, 19 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(host_g, tmp + 19 * N, 21 * (size_t)N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(tmp);
     if (e != cudaSuccess) return cuda3(h, e, "lks3_get_state");
     return flag_check3(h, "lks3_get_state");
 }
@@ -1055,23 +1079,25 @@ lks_status lks3_set_state(lks3_handle* h, const double* host_f, const double* ho
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail3(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
-    double* tmp = nullptr;
-    cudaError_t e = cudaMalloc((void**)&tmp, 40 * (size_t)N * sizeof(double));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail3(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
-    }
-    e = cudaMemcpyAsync(tmp, host_f, 19 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(tmp + 19 * N, host_g, 21 * (size_t)N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) {
-        LKS3_DISPATCH(h->p.storage, (from_abs3_kernel<S, C><<<grid_for(N), 256, 0, h->stream>>>(
-                                        tmp, tmp + 19 * N, N, h->rest, h->p.B0, (S*)h->f[h->cur], (S*)h->g[h->cur])));
-        e = cudaGetLastError();
+    int64_t M = 0;
+    if (lks_status s = state_stage3(h, &M)) return s;
+    double* st = h->state_stage;
+    cudaError_t e = cudaSuccess;
+    for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
+        const int64_t m = N - n0 < M ? N - n0 : M;
+        for (int a = 0; a < 40 && e == cudaSuccess; ++a) {
+            const double* src = a < 19 ? host_f + a * N + n0 : host_g + (a - 19) * N + n0;
+            e = cudaMemcpyAsync(st + a * m, src, m * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        }
+        if (e == cudaSuccess) {
+            LKS3_DISPATCH(h->p.storage, (from_abs3_kernel<S, C><<<grid_for(m), 256, 0, h->stream>>>(
+                                            st, st + 19 * m, N, n0, m, h->rest, h->p.B0, (S*)h->f[h->cur],
+                                            (S*)h->g[h->cur])));
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess) e = launch_snapshot3(h);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(tmp);
     if (e != cudaSuccess) return cuda3(h, e, "lks3_set_state");
     h->steps = 0;
     return LKS_OK;
@@ -1087,6 +1113,7 @@ lks_status lks3_sync(lks3_handle* h) {
 lks_status lks3_destroy(lks3_handle* h) {
     if (!h) return LKS_OK;
     if (h->stream || h->base) cudaStreamSynchronize(h->stream);
+    if (h->state_stage) cudaFree(h->state_stage);
     if (h->owns && h->base) cudaFree(h->base);
     if (h->host4) cudaFreeHost(h->host4);
     delete h;

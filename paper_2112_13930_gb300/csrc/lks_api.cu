@@ -172,7 +172,7 @@ struct lks_handle {
     double* partial = nullptr;
     double* dout = nullptr;
     double* prof = nullptr;
-    double* node_stage = nullptr;  // lazily allocated 5*N doubles for per-node host moments
+    double* state_stage = nullptr;  // 19 * min(N, 2^20) doubles for state and moment transfers, on first use
     double* host_small = nullptr;  // pinned 8 doubles
     int* flag = nullptr;
     bool staged = false;              // 16-bit, nx % 8 == 0, nx >= 1024: the staged kernels
@@ -254,6 +254,24 @@ cudaError_t build_graph(lks_handle* h, int start) {
     e = cudaGraphInstantiate(&h->graph[start], graph, 0);
     cudaGraphDestroy(graph);
     return e;
+}
+
+// State transfers and per-node host moments convert kStateChunk nodes at a time through a staging
+// buffer the handle keeps, so their device memory stays bounded (152 MB) whatever the lattice size.
+constexpr int64_t kStateChunk = int64_t(1) << 20;
+
+lks_status state_stage(lks_handle* h, int64_t* chunk) {
+    const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    *chunk = N < kStateChunk ? N : kStateChunk;
+    if (!h->state_stage) {
+        cudaError_t e = cudaMalloc((void**)&h->state_stage, 19 * (size_t)*chunk * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->state_stage = nullptr;
+            return fail(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
+        }
+    }
+    return LKS_OK;
 }
 
 }  // namespace
@@ -390,24 +408,26 @@ lks_status lks_moments(lks_handle* h, int what, double* host_out) {
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_out) return fail(h, LKS_EINVAL, "host_out is NULL");
     if (what != LKS_MOMENTS_NODES && what != LKS_MOMENTS_PROFILES) return fail(h, LKS_EINVAL, "bad 'what'");
-    const size_t N = (size_t)h->p.nx * h->p.ny;
-    double* dst = h->prof;
-    size_t count = 5 * (size_t)h->p.ny;
-    if (what == LKS_MOMENTS_NODES) {
-        if (!h->node_stage) {
-            cudaError_t e = cudaMalloc((void**)&h->node_stage, 5 * N * sizeof(double));
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                h->node_stage = nullptr;
-                return fail(h, LKS_ENOMEM, "cudaMalloc of the per-node moment staging buffer failed");
-            }
+    cudaError_t e = cudaSuccess;
+    if (what == LKS_MOMENTS_PROFILES) {
+        if (lks_status s = lks_moments_device(h, what, h->prof)) return s;
+        e = cudaMemcpyAsync(host_out, h->prof, 5 * (size_t)h->p.ny * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream);
+    } else {
+        const int64_t N = (int64_t)h->p.nx * h->p.ny;
+        int64_t M = 0;
+        if (lks_status s = state_stage(h, &M)) return s;
+        double* st = h->state_stage;
+        const int ilv = lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace);
+        for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
+            const int64_t m = N - n0 < M ? N - n0 : M;
+            e = lks::launch_node_moments(h->p.storage, h->f[h->cur], h->g[h->cur], N, n0, m, h->p.B0, h->p.Fx, st,
+                                         h->stream, h->p.coupling, h->p.tau_m, ilv);
+            for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+                e = cudaMemcpyAsync(host_out + k * N + n0, st + k * m, m * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream);
         }
-        dst = h->node_stage;
-        count = 5 * N;
     }
-    lks_status s = lks_moments_device(h, what, dst);
-    if (s != LKS_OK) return s;
-    cudaError_t e = cudaMemcpyAsync(host_out, dst, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_moments");
     return staged_check(h, "lks_moments");
@@ -466,20 +486,22 @@ lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g) {
     NvtxRange nvtx_range("lks_get_state");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
-    const size_t N = (size_t)h->p.nx * h->p.ny;
-    double* tmp = nullptr;
-    cudaError_t e = cudaMalloc((void**)&tmp, 19 * N * sizeof(double));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
+    const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    int64_t M = 0;
+    if (lks_status s = state_stage(h, &M)) return s;
+    double* st = h->state_stage;
+    const int ilv = lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace);
+    cudaError_t e = cudaSuccess;
+    for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
+        const int64_t m = N - n0 < M ? N - n0 : M;
+        e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], N, n0, m, h->p.B0, st, st + 9 * m,
+                               h->stream, h->p.coupling, ilv);
+        for (int a = 0; a < 19 && e == cudaSuccess; ++a) {
+            double* dst = a < 9 ? host_f + a * N + n0 : host_g + (a - 9) * N + n0;
+            e = cudaMemcpyAsync(dst, st + a * m, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        }
     }
-    e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], (int64_t)N, h->p.B0, tmp, tmp + 9 * N,
-                           h->stream, h->p.coupling, lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace));
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, tmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(host_g, tmp + 9 * N, 10 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_get_state");
     return staged_check(h, "lks_get_state");
 }
@@ -488,25 +510,26 @@ lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host
     NvtxRange nvtx_range("lks_set_state");
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
-    const size_t N = (size_t)h->p.nx * h->p.ny;
-    double* tmp = nullptr;
-    cudaError_t e = cudaMalloc((void**)&tmp, 19 * N * sizeof(double));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(h, LKS_ENOMEM, "cudaMalloc of the FP64 state staging buffer failed");
+    const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    int64_t M = 0;
+    if (lks_status s = state_stage(h, &M)) return s;
+    double* st = h->state_stage;
+    const int ilv = lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace);
+    cudaError_t e = cudaSuccess;
+    for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
+        const int64_t m = N - n0 < M ? N - n0 : M;
+        for (int a = 0; a < 19 && e == cudaSuccess; ++a) {
+            const double* src = a < 9 ? host_f + a * N + n0 : host_g + (a - 9) * N + n0;
+            e = cudaMemcpyAsync(st + a * m, src, m * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        }
+        if (e == cudaSuccess)
+            e = lks::launch_from_abs(h->p.storage, st, st + 9 * m, N, n0, m, h->p.B0, h->f[h->cur], h->g[h->cur],
+                                     h->stream, h->p.coupling, ilv);
     }
-    e = cudaMemcpyAsync(tmp, host_f, 9 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(tmp + 9 * N, host_g, 10 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-        e = lks::launch_from_abs(h->p.storage, tmp, tmp + 9 * N, (int64_t)N, h->p.B0, h->f[h->cur], h->g[h->cur],
-                                 h->stream, h->p.coupling, lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace));
     if (e == cudaSuccess)
         e = lks::launch_snapshot(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0, h->p.Fx,
-                                 h->snap, h->stream, h->p.coupling, h->p.tau_m,
-                                 lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace));
+                                 h->snap, h->stream, h->p.coupling, h->p.tau_m, ilv);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_set_state");
     h->steps = 0;
     return LKS_OK;
@@ -524,7 +547,7 @@ lks_status lks_destroy(lks_handle* h) {
     if (!h) return LKS_OK;
     if (h->stream || h->base) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
-    if (h->node_stage) cudaFree(h->node_stage);
+    if (h->state_stage) cudaFree(h->state_stage);
     if (h->owns && h->base) cudaFree(h->base);
     if (h->host_small) cudaFreeHost(h->host_small);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

@@ -117,14 +117,16 @@ __device__ __forceinline__ void node_moments(const S* f, const S* g, int64_t N, 
     m[4] = by;
 }
 
+// Moments of the M nodes n0 .. n0+M-1 of the N-node state: out[k*M + i] for node n0 + i.
 template <typename S, typename C>
-__global__ void moments_kernel(const S* f, const S* g, int64_t N, MomentModel mm, double* out, int ilv) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+__global__ void moments_kernel(const S* f, const S* g, int64_t N, int64_t n0, int64_t M, MomentModel mm,
+                               double* out, int ilv) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
     double m[5];
-    node_moments<S, C>(f, g, N, slot_of(n, ilv), mm, m);
+    node_moments<S, C>(f, g, N, slot_of(n0 + i, ilv), mm, m);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) out[k * N + n] = m[k];
+    for (int k = 0; k < 5; ++k) out[k * M + i] = m[k];
 }
 
 // Fixed-order block sum of K values per thread (tree in shared memory).
@@ -207,28 +209,30 @@ __global__ void snapshot_kernel(const S* f, const S* g, int64_t N, MomentModel m
 }
 
 template <typename S, typename C>
-__global__ void to_abs_kernel(const S* f, const S* g, int64_t N, double B0, int coupling, double* fa, double* ga,
-                              int ilv) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const int64_t pn = slot_of(n, ilv);
-    for (int a = 0; a < 9; ++a) fa[a * N + n] = (double)load_s<S, C>(f + a * N + pn) + f_rest(a, B0, coupling);
+__global__ void to_abs_kernel(const S* f, const S* g, int64_t N, int64_t n0, int64_t M, double B0, int coupling,
+                              double* fa, double* ga, int ilv) {
+    // nodes n0 .. n0 + M - 1 into planes of stride M
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int64_t pn = slot_of(n0 + i, ilv);
+    for (int a = 0; a < 9; ++a) fa[a * M + i] = (double)load_s<S, C>(f + a * N + pn) + f_rest(a, B0, coupling);
     for (int a = 0; a < 5; ++a) {
-        ga[a * N + n] = (double)load_s<S, C>(g + a * N + pn);
-        ga[(5 + a) * N + n] = (double)load_s<S, C>(g + (5 + a) * N + pn) + w5(a) * B0;
+        ga[a * M + i] = (double)load_s<S, C>(g + a * N + pn);
+        ga[(5 + a) * M + i] = (double)load_s<S, C>(g + (5 + a) * N + pn) + w5(a) * B0;
     }
 }
 
 template <typename S, typename C>
-__global__ void from_abs_kernel(const double* fa, const double* ga, int64_t N, double B0, int coupling, S* f, S* g,
-                                int ilv) {
-    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    const int64_t pn = slot_of(n, ilv);
-    for (int a = 0; a < 9; ++a) store_s<S, C>(f + a * N + pn, (C)(fa[a * N + n] - f_rest(a, B0, coupling)));
+__global__ void from_abs_kernel(const double* fa, const double* ga, int64_t N, int64_t n0, int64_t M, double B0,
+                                int coupling, S* f, S* g, int ilv) {
+    // nodes n0 .. n0 + M - 1 from planes of stride M
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int64_t pn = slot_of(n0 + i, ilv);
+    for (int a = 0; a < 9; ++a) store_s<S, C>(f + a * N + pn, (C)(fa[a * M + i] - f_rest(a, B0, coupling)));
     for (int a = 0; a < 5; ++a) {
-        store_s<S, C>(g + a * N + pn, (C)ga[a * N + n]);
-        store_s<S, C>(g + (5 + a) * N + pn, (C)(ga[(5 + a) * N + n] - w5(a) * B0));
+        store_s<S, C>(g + a * N + pn, (C)ga[a * M + i]);
+        store_s<S, C>(g + (5 + a) * N + pn, (C)(ga[(5 + a) * M + i] - w5(a) * B0));
     }
 }
 
@@ -270,11 +274,20 @@ cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, in
     const MomentModel mm{B0, Fx, tau_m, coupling};
     if (what == 0) {
         LKS_DISPATCH(storage, (moments_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N,
-                                                                                      mm, out, ilv)));
+                                                                                      0, N, mm, out, ilv)));
     } else {
         LKS_DISPATCH(storage, (profiles_kernel<S, C><<<ny, kThreads, 0, st>>>((const S*)f, (const S*)g, nx, ny, mm,
                                                                               out, ilv)));
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_moments(int storage, const void* f, const void* g, int64_t N, int64_t n0, int64_t M,
+                                double B0, double Fx, double* out, cudaStream_t st, int coupling, double tau_m,
+                                int ilv) {
+    const MomentModel mm{B0, Fx, tau_m, coupling};
+    LKS_DISPATCH(storage, (moments_kernel<S, C><<<grid_for(M), kThreads, 0, st>>>((const S*)f, (const S*)g, N, n0,
+                                                                                  M, mm, out, ilv)));
     return cudaGetLastError();
 }
 
@@ -306,16 +319,16 @@ cudaError_t launch_snapshot(int storage, const void* f, const void* g, int nx, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, double B0, double* fabs,
-                          double* gabs, cudaStream_t st, int coupling, int ilv) {
-    LKS_DISPATCH(storage, (to_abs_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>((const S*)f, (const S*)g, N, B0,
-                                                                                 coupling, fabs, gabs, ilv)));
+cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, int64_t n0, int64_t M, double B0,
+                          double* fabs, double* gabs, cudaStream_t st, int coupling, int ilv) {
+    LKS_DISPATCH(storage, (to_abs_kernel<S, C><<<grid_for(M), kThreads, 0, st>>>((const S*)f, (const S*)g, N, n0, M,
+                                                                                 B0, coupling, fabs, gabs, ilv)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, double B0, void* f,
-                            void* g, cudaStream_t st, int coupling, int ilv) {
-    LKS_DISPATCH(storage, (from_abs_kernel<S, C><<<grid_for(N), kThreads, 0, st>>>(fabs, gabs, N, B0, coupling,
+cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, int64_t n0, int64_t M,
+                            double B0, void* f, void* g, cudaStream_t st, int coupling, int ilv) {
+    LKS_DISPATCH(storage, (from_abs_kernel<S, C><<<grid_for(M), kThreads, 0, st>>>(fabs, gabs, N, n0, M, B0, coupling,
                                                                                    (S*)f, (S*)g, ilv)));
     return cudaGetLastError();
 }

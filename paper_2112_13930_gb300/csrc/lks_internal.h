@@ -94,6 +94,11 @@ cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, in
                            int what, double* out, cudaStream_t st, int coupling = 0, double tau_m = 1.0,
                            int ilv = 0);
 
+// Per-node moments of the M nodes n0 .. n0+M-1 of an N-node state: out[m*M + i] for node n0 + i.
+cudaError_t launch_node_moments(int storage, const void* f, const void* g, int64_t N, int64_t n0, int64_t M,
+                                double B0, double Fx, double* out, cudaStream_t st, int coupling = 0,
+                                double tau_m = 1.0, int ilv = 0);
+
 // Residual partial sums: nblk blocks write partial[4*blk + k] = (sum du^2, sum u^2, sum db^2, sum b^2)
 // and refresh the snapshot snap[0..N) = u_x, snap[N..2N) = B_x; then one block reduces in fixed order
 // into out[0..4).
@@ -104,10 +109,11 @@ cudaError_t launch_residual(int storage, const void* f, const void* g, int nx, i
 cudaError_t launch_snapshot(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
                             double* snap, cudaStream_t st, int coupling = 0, double tau_m = 1.0, int ilv = 0);
 
-// FP64 absolute populations <-> stored deviations.
-cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, double B0, double* fabs,
-                          double* gabs, cudaStream_t st, int coupling = 0, int ilv = 0);
-cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, double B0, void* f,
-                            void* g, cudaStream_t st, int coupling = 0, int ilv = 0);
+// FP64 absolute populations <-> stored deviations, for the nodes n0 .. n0 + M - 1 of an N-node lattice;
+// fabs / gabs hold those nodes in planes of stride M (9 and 10 planes).
+cudaError_t launch_to_abs(int storage, const void* f, const void* g, int64_t N, int64_t n0, int64_t M, double B0,
+                          double* fabs, double* gabs, cudaStream_t st, int coupling = 0, int ilv = 0);
+cudaError_t launch_from_abs(int storage, const double* fabs, const double* gabs, int64_t N, int64_t n0, int64_t M,
+                            double B0, void* f, void* g, cudaStream_t st, int coupling = 0, int ilv = 0);
 
 }  // namespace lks
