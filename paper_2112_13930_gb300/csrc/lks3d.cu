@@ -28,6 +28,7 @@
 #include "../../include/lks3d.h"
 #include "lks_device.cuh"
 #include "lks_bulk.cuh"
+#include "lks_internal.h"
 #include "lks_packed.cuh"
 #include "lks_vec.cuh"
 
@@ -664,10 +665,17 @@ template <typename S, typename C>
 __global__ void to_abs3_kernel(const S* f, const S* g, int64_t N, int64_t n0, int64_t M, const double* rest_f,
                                double B0, double* of, double* og) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        // all loads before the first store: the FP64 planes may be host memory behind a link
         const int64_t n = n0 + i;
-        for (int a = 0; a < 19; ++a) of[a * M + i] = (double)load_s<S, C>(f + a * N + n) + rest_f[a];
-        for (int k = 0; k < 21; ++k)
-            og[k * M + i] = (double)load_s<S, C>(g + k * N + n) + (k / 7 == 1 ? w7(k % 7) * B0 : 0.0);
+        C v[40];
+#pragma unroll
+        for (int a = 0; a < 19; ++a) v[a] = load_s<S, C>(f + a * N + n);
+#pragma unroll
+        for (int k = 0; k < 21; ++k) v[19 + k] = load_s<S, C>(g + k * N + n);
+#pragma unroll
+        for (int a = 0; a < 19; ++a) of[a * M + i] = (double)v[a] + rest_f[a];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) og[k * M + i] = (double)v[19 + k] + (k / 7 == 1 ? w7(k % 7) * B0 : 0.0);
     }
 }
 
@@ -675,10 +683,17 @@ template <typename S, typename C>
 __global__ void from_abs3_kernel(const double* inf, const double* ing, int64_t N, int64_t n0, int64_t M,
                                  const double* rest_f, double B0, S* f, S* g) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        // all loads before the first store (see to_abs3_kernel)
         const int64_t n = n0 + i;
-        for (int a = 0; a < 19; ++a) store_s<S, C>(f + a * N + n, (C)(inf[a * M + i] - rest_f[a]));
-        for (int k = 0; k < 21; ++k)
-            store_s<S, C>(g + k * N + n, (C)(ing[k * M + i] - (k / 7 == 1 ? w7(k % 7) * B0 : 0.0)));
+        double v[40];
+#pragma unroll
+        for (int a = 0; a < 19; ++a) v[a] = inf[a * M + i];
+#pragma unroll
+        for (int k = 0; k < 21; ++k) v[19 + k] = ing[k * M + i];
+#pragma unroll
+        for (int a = 0; a < 19; ++a) store_s<S, C>(f + a * N + n, (C)(v[a] - rest_f[a]));
+#pragma unroll
+        for (int k = 0; k < 21; ++k) store_s<S, C>(g + k * N + n, (C)(v[19 + k] - (k / 7 == 1 ? w7(k % 7) * B0 : 0.0)));
     }
 }
 
@@ -749,6 +764,7 @@ struct lks3_handle {
     unsigned staged_grid = 0;  // resident blocks of it on the device
     double* host4 = nullptr;  // pinned
     double* state_stage = nullptr;  // 40 * min(N, 2^20) doubles for state and moment transfers, on first use
+    bool host_direct = false;       // kernels read and write caller host arrays directly (pageable access)
     double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
     int64_t steps = 0;
     std::string err;
@@ -908,6 +924,7 @@ lks_status lks3_create(const lks3_params* p, lks3_handle** out) {
     h->prof = (double*)(h->base + h->L.off_prof);
     h->rest = (double*)(h->base + h->L.off_rest);
     h->flag = (int*)(h->base + h->L.off_flag);
+    h->host_direct = lks::host_access_direct();
     h->staged = (p->storage == LKS_BF16_DEV || p->storage == LKS_F16_DEV) && p->nx % 8 == 0 && p->nx <= kTaskNodes3;
     double rest[19];
     for (int a = 0; a < 19; ++a) rest[a] = f_rest(a, p->B0);
@@ -984,17 +1001,20 @@ lks_status lks3_moments(lks3_handle* h, int what, double* host_out) {
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(host_out, h->prof, 7 * (size_t)p.ny * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     } else if (what == LKS_MOMENTS_NODES) {
-        int64_t M = 0;
-        if (lks_status s = state_stage3(h, &M)) return s;
-        double* st = h->state_stage;
+        // directly into host_out (one chunk of N nodes), or M nodes at a time through the staging buffer
+        int64_t M = N;
+        if (!h->host_direct) {
+            if (lks_status s = state_stage3(h, &M)) return s;
+        }
+        double* out = h->host_direct ? host_out : h->state_stage;
         e = cudaSuccess;
         for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
             const int64_t m = N - n0 < M ? N - n0 : M;
             LKS3_DISPATCH(p.storage, (moments3_kernel<S><<<grid_for(m), 256, 0, h->stream>>>(
-                                         (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, n0, m, p.B0, p.Fx, st)));
+                                         (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, n0, m, p.B0, p.Fx, out)));
             e = cudaGetLastError();
-            for (int k = 0; k < 7 && e == cudaSuccess; ++k)
-                e = cudaMemcpyAsync(host_out + k * N + n0, st + k * m, m * sizeof(double), cudaMemcpyDeviceToHost,
+            for (int k = 0; k < 7 && e == cudaSuccess && !h->host_direct; ++k)
+                e = cudaMemcpyAsync(host_out + k * N + n0, out + k * m, m * sizeof(double), cudaMemcpyDeviceToHost,
                                     h->stream);
         }
     } else {
@@ -1051,23 +1071,29 @@ lks_status lks3_run_to_steady(lks3_handle* h, double tol, int64_t check_every, i
     return LKS_OK;
 }
 
+// State transfers and per-node host moments: with host_direct one chunk of N nodes whose FP64 planes
+// are the caller's arrays themselves; otherwise M nodes at a time through the staging buffer, one copy
+// per plane.
 lks_status lks3_get_state(lks3_handle* h, double* host_f, double* host_g) {
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail3(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
-    int64_t M = 0;
-    if (lks_status s = state_stage3(h, &M)) return s;
-    double* st = h->state_stage;
+    int64_t M = N;
+    if (!h->host_direct) {
+        if (lks_status s = state_stage3(h, &M)) return s;
+    }
     cudaError_t e = cudaSuccess;
     for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
         const int64_t m = N - n0 < M ? N - n0 : M;
+        double* of = h->host_direct ? host_f : h->state_stage;
+        double* og = h->host_direct ? host_g : h->state_stage + 19 * m;
         LKS3_DISPATCH(h->p.storage, (to_abs3_kernel<S, C><<<grid_for(m), 256, 0, h->stream>>>(
                                         (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, n0, m, h->rest, h->p.B0,
-                                        st, st + 19 * m)));
+                                        of, og)));
         e = cudaGetLastError();
-        for (int a = 0; a < 40 && e == cudaSuccess; ++a) {
+        for (int a = 0; a < 40 && e == cudaSuccess && !h->host_direct; ++a) {
             double* dst = a < 19 ? host_f + a * N + n0 : host_g + (a - 19) * N + n0;
-            e = cudaMemcpyAsync(dst, st + a * m, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            e = cudaMemcpyAsync(dst, h->state_stage + a * m, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1079,20 +1105,27 @@ lks_status lks3_set_state(lks3_handle* h, const double* host_f, const double* ho
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail3(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
-    int64_t M = 0;
-    if (lks_status s = state_stage3(h, &M)) return s;
-    double* st = h->state_stage;
+    int64_t M = N;
+    if (!h->host_direct) {
+        if (lks_status s = state_stage3(h, &M)) return s;
+    }
     cudaError_t e = cudaSuccess;
     for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
         const int64_t m = N - n0 < M ? N - n0 : M;
-        for (int a = 0; a < 40 && e == cudaSuccess; ++a) {
-            const double* src = a < 19 ? host_f + a * N + n0 : host_g + (a - 19) * N + n0;
-            e = cudaMemcpyAsync(st + a * m, src, m * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        const double* sf = host_f;
+        const double* sg = host_g;
+        if (!h->host_direct) {
+            for (int a = 0; a < 40 && e == cudaSuccess; ++a) {
+                const double* src = a < 19 ? host_f + a * N + n0 : host_g + (a - 19) * N + n0;
+                e = cudaMemcpyAsync(h->state_stage + a * m, src, m * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream);
+            }
+            sf = h->state_stage;
+            sg = h->state_stage + 19 * m;
         }
         if (e == cudaSuccess) {
             LKS3_DISPATCH(h->p.storage, (from_abs3_kernel<S, C><<<grid_for(m), 256, 0, h->stream>>>(
-                                            st, st + 19 * m, N, n0, m, h->rest, h->p.B0, (S*)h->f[h->cur],
-                                            (S*)h->g[h->cur])));
+                                            sf, sg, N, n0, m, h->rest, h->p.B0, (S*)h->f[h->cur], (S*)h->g[h->cur])));
             e = cudaGetLastError();
         }
     }

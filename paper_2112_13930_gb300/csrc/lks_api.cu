@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -154,8 +155,23 @@ StepParams<double> make_step_params(int nx, int ny, int closure, double tau_f, d
     return s;
 }
 
-}  // namespace lks
+// Whether the conversion kernels of state transfers and per-node host moments may read and write the
+// caller's host arrays themselves: the device must access pageable host memory coherently (true with
+// the host page tables of a Grace CPU over NVLink-C2C, where kernel accesses run at the link's rate).
+// LKS_HOST_STAGING=1 in the environment forces the staged copies.
+bool host_access_direct() {
+    const char* env = getenv("LKS_HOST_STAGING");
+    if (env && env[0] && strcmp(env, "0") != 0) return false;
+    int dev = 0, pageable = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return pageable != 0;
+}
 
+}  // namespace lks
 
 struct lks_handle {
     lks_params p;
@@ -173,6 +189,7 @@ struct lks_handle {
     double* dout = nullptr;
     double* prof = nullptr;
     double* state_stage = nullptr;  // 19 * min(N, 2^20) doubles for state and moment transfers, on first use
+    bool host_direct = false;       // kernels read and write caller host arrays directly (pageable access)
     double* host_small = nullptr;  // pinned 8 doubles
     int* flag = nullptr;
     bool staged = false;              // 16-bit, nx % 8 == 0, nx >= 1024: the staged kernels
@@ -256,8 +273,10 @@ cudaError_t build_graph(lks_handle* h, int start) {
     return e;
 }
 
-// State transfers and per-node host moments convert kStateChunk nodes at a time through a staging
-// buffer the handle keeps, so their device memory stays bounded (152 MB) whatever the lattice size.
+
+// Otherwise state transfers and per-node host moments convert kStateChunk nodes at a time through a
+// staging buffer the handle keeps, so their device memory stays bounded (152 MB) whatever the lattice
+// size.
 constexpr int64_t kStateChunk = int64_t(1) << 20;
 
 lks_status state_stage(lks_handle* h, int64_t* chunk) {
@@ -272,6 +291,60 @@ lks_status state_stage(lks_handle* h, int64_t* chunk) {
         }
     }
     return LKS_OK;
+}
+
+int ilv_of(const lks_handle* h) { return lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace); }
+
+// Stored state -> FP64 host arrays, M nodes per chunk: one conversion kernel into the staging buffer,
+// then one copy per population plane.
+cudaError_t staged_to_host(lks_handle* h, double* host_f, double* host_g, int64_t M) {
+    const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    double* st = h->state_stage;
+    cudaError_t e = cudaSuccess;
+    for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
+        const int64_t m = N - n0 < M ? N - n0 : M;
+        e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], N, n0, m, h->p.B0, st, st + 9 * m,
+                               h->stream, h->p.coupling, ilv_of(h));
+        for (int a = 0; a < 19 && e == cudaSuccess; ++a) {
+            double* dst = a < 9 ? host_f + a * N + n0 : host_g + (a - 9) * N + n0;
+            e = cudaMemcpyAsync(dst, st + a * m, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        }
+    }
+    return e;
+}
+
+// FP64 host arrays -> stored state, M nodes per chunk.
+cudaError_t staged_from_host(lks_handle* h, const double* host_f, const double* host_g, int64_t M) {
+    const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    double* st = h->state_stage;
+    cudaError_t e = cudaSuccess;
+    for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
+        const int64_t m = N - n0 < M ? N - n0 : M;
+        for (int a = 0; a < 19 && e == cudaSuccess; ++a) {
+            const double* src = a < 9 ? host_f + a * N + n0 : host_g + (a - 9) * N + n0;
+            e = cudaMemcpyAsync(st + a * m, src, m * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        }
+        if (e == cudaSuccess)
+            e = lks::launch_from_abs(h->p.storage, st, st + 9 * m, N, n0, m, h->p.B0, h->f[h->cur], h->g[h->cur],
+                                     h->stream, h->p.coupling, ilv_of(h));
+    }
+    return e;
+}
+
+// Per-node moments -> host array (5 planes of N), M nodes per chunk.
+cudaError_t staged_moments_to_host(lks_handle* h, double* host_out, int64_t M) {
+    const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    double* st = h->state_stage;
+    cudaError_t e = cudaSuccess;
+    for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
+        const int64_t m = N - n0 < M ? N - n0 : M;
+        e = lks::launch_node_moments(h->p.storage, h->f[h->cur], h->g[h->cur], N, n0, m, h->p.B0, h->p.Fx, st,
+                                     h->stream, h->p.coupling, h->p.tau_m, ilv_of(h));
+        for (int k = 0; k < 5 && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(host_out + k * N + n0, st + k * m, m * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream);
+    }
+    return e;
 }
 
 }  // namespace
@@ -326,6 +399,7 @@ lks_status lks_create(const lks_params* p, lks_handle** out) {
     e = cudaHostAlloc((void**)&h->host_small, 8 * sizeof(double), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) h->host_direct = lks::host_access_direct();
     if (e == cudaSuccess && lks::staged_step_applies(p->storage, p->nx, p->inplace)) {
         e = lks::prepare_staged_step(p->storage, p->inplace, &h->ss.grid);
         h->ss.err = h->flag;
@@ -408,25 +482,19 @@ lks_status lks_moments(lks_handle* h, int what, double* host_out) {
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_out) return fail(h, LKS_EINVAL, "host_out is NULL");
     if (what != LKS_MOMENTS_NODES && what != LKS_MOMENTS_PROFILES) return fail(h, LKS_EINVAL, "bad 'what'");
-    cudaError_t e = cudaSuccess;
+    cudaError_t e;
     if (what == LKS_MOMENTS_PROFILES) {
         if (lks_status s = lks_moments_device(h, what, h->prof)) return s;
         e = cudaMemcpyAsync(host_out, h->prof, 5 * (size_t)h->p.ny * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream);
-    } else {
+    } else if (h->host_direct) {
         const int64_t N = (int64_t)h->p.nx * h->p.ny;
+        e = lks::launch_node_moments(h->p.storage, h->f[h->cur], h->g[h->cur], N, 0, N, h->p.B0, h->p.Fx, host_out,
+                                     h->stream, h->p.coupling, h->p.tau_m, ilv_of(h));
+    } else {
         int64_t M = 0;
         if (lks_status s = state_stage(h, &M)) return s;
-        double* st = h->state_stage;
-        const int ilv = lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace);
-        for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
-            const int64_t m = N - n0 < M ? N - n0 : M;
-            e = lks::launch_node_moments(h->p.storage, h->f[h->cur], h->g[h->cur], N, n0, m, h->p.B0, h->p.Fx, st,
-                                         h->stream, h->p.coupling, h->p.tau_m, ilv);
-            for (int k = 0; k < 5 && e == cudaSuccess; ++k)
-                e = cudaMemcpyAsync(host_out + k * N + n0, st + k * m, m * sizeof(double), cudaMemcpyDeviceToHost,
-                                    h->stream);
-        }
+        e = staged_moments_to_host(h, host_out, M);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_moments");
@@ -487,19 +555,14 @@ lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g) {
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny;
-    int64_t M = 0;
-    if (lks_status s = state_stage(h, &M)) return s;
-    double* st = h->state_stage;
-    const int ilv = lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace);
-    cudaError_t e = cudaSuccess;
-    for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
-        const int64_t m = N - n0 < M ? N - n0 : M;
-        e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], N, n0, m, h->p.B0, st, st + 9 * m,
-                               h->stream, h->p.coupling, ilv);
-        for (int a = 0; a < 19 && e == cudaSuccess; ++a) {
-            double* dst = a < 9 ? host_f + a * N + n0 : host_g + (a - 9) * N + n0;
-            e = cudaMemcpyAsync(dst, st + a * m, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-        }
+    cudaError_t e;
+    if (h->host_direct) {
+        e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], N, 0, N, h->p.B0, host_f, host_g,
+                               h->stream, h->p.coupling, ilv_of(h));
+    } else {
+        int64_t M = 0;
+        if (lks_status s = state_stage(h, &M)) return s;
+        e = staged_to_host(h, host_f, host_g, M);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_get_state");
@@ -511,24 +574,18 @@ lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny;
-    int64_t M = 0;
-    if (lks_status s = state_stage(h, &M)) return s;
-    double* st = h->state_stage;
-    const int ilv = lks::interleave_row(h->p.storage, h->p.nx, h->p.inplace);
-    cudaError_t e = cudaSuccess;
-    for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
-        const int64_t m = N - n0 < M ? N - n0 : M;
-        for (int a = 0; a < 19 && e == cudaSuccess; ++a) {
-            const double* src = a < 9 ? host_f + a * N + n0 : host_g + (a - 9) * N + n0;
-            e = cudaMemcpyAsync(st + a * m, src, m * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-        }
-        if (e == cudaSuccess)
-            e = lks::launch_from_abs(h->p.storage, st, st + 9 * m, N, n0, m, h->p.B0, h->f[h->cur], h->g[h->cur],
-                                     h->stream, h->p.coupling, ilv);
+    cudaError_t e;
+    if (h->host_direct) {
+        e = lks::launch_from_abs(h->p.storage, host_f, host_g, N, 0, N, h->p.B0, h->f[h->cur], h->g[h->cur],
+                                 h->stream, h->p.coupling, ilv_of(h));
+    } else {
+        int64_t M = 0;
+        if (lks_status s = state_stage(h, &M)) return s;
+        e = staged_from_host(h, host_f, host_g, M);
     }
     if (e == cudaSuccess)
         e = lks::launch_snapshot(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0, h->p.Fx,
-                                 h->snap, h->stream, h->p.coupling, h->p.tau_m, ilv);
+                                 h->snap, h->stream, h->p.coupling, h->p.tau_m, ilv_of(h));
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lks_set_state");
     h->steps = 0;

@@ -214,11 +214,20 @@ __global__ void to_abs_kernel(const S* f, const S* g, int64_t N, int64_t n0, int
     // nodes n0 .. n0 + M - 1 into planes of stride M
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
+    // All loads before the first store: the FP64 planes may be host memory behind a link with
+    // microseconds of latency, and a store the compiler cannot prove disjoint would order the loads.
     const int64_t pn = slot_of(n0 + i, ilv);
-    for (int a = 0; a < 9; ++a) fa[a * M + i] = (double)load_s<S, C>(f + a * N + pn) + f_rest(a, B0, coupling);
+    C v[19];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = load_s<S, C>(f + a * N + pn);
+#pragma unroll
+    for (int a = 0; a < 10; ++a) v[9 + a] = load_s<S, C>(g + a * N + pn);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) fa[a * M + i] = (double)v[a] + f_rest(a, B0, coupling);
+#pragma unroll
     for (int a = 0; a < 5; ++a) {
-        ga[a * M + i] = (double)load_s<S, C>(g + a * N + pn);
-        ga[(5 + a) * M + i] = (double)load_s<S, C>(g + (5 + a) * N + pn) + w5(a) * B0;
+        ga[a * M + i] = (double)v[9 + a];
+        ga[(5 + a) * M + i] = (double)v[14 + a] + w5(a) * B0;
     }
 }
 
@@ -228,11 +237,19 @@ __global__ void from_abs_kernel(const double* fa, const double* ga, int64_t N, i
     // nodes n0 .. n0 + M - 1 from planes of stride M
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
+    // All loads before the first store (see to_abs_kernel).
     const int64_t pn = slot_of(n0 + i, ilv);
-    for (int a = 0; a < 9; ++a) store_s<S, C>(f + a * N + pn, (C)(fa[a * M + i] - f_rest(a, B0, coupling)));
+    double v[19];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = fa[a * M + i];
+#pragma unroll
+    for (int a = 0; a < 10; ++a) v[9 + a] = ga[a * M + i];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) store_s<S, C>(f + a * N + pn, (C)(v[a] - f_rest(a, B0, coupling)));
+#pragma unroll
     for (int a = 0; a < 5; ++a) {
-        store_s<S, C>(g + a * N + pn, (C)ga[a * M + i]);
-        store_s<S, C>(g + (5 + a) * N + pn, (C)(ga[(5 + a) * M + i] - w5(a) * B0));
+        store_s<S, C>(g + a * N + pn, (C)v[9 + a]);
+        store_s<S, C>(g + (5 + a) * N + pn, (C)(v[14 + a] - w5(a) * B0));
     }
 }
 

@@ -164,6 +164,7 @@ class Lattice3D:
     def set_state(self, f, g):
         f = np.ascontiguousarray(f, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.shape == (19, self.nz, self.ny, self.nx) and g.shape == (3, 7, self.nz, self.ny, self.nx)
         _check(lib().lks3_set_state(self._h, _ptr(f), _ptr(g)), self._h)
 
     def sync(self):

@@ -1,8 +1,10 @@
 """State transfers of lattices larger than one conversion chunk (2^20 nodes), on the GPU.
 
 lks_get_state / lks_set_state (and the 3D pair) convert between stored deviations and FP64
-absolute populations 2^20 nodes at a time through a staging buffer.  On lattices of a little more
-than 2^20 nodes (one full chunk and a ragged one) every node must land where it belongs:
+absolute populations either directly in the caller's host arrays (devices with coherent access to
+pageable host memory, such as a GPU attached to a Grace CPU) or, with LKS_HOST_STAGING=1 or
+elsewhere, 2^20 nodes at a time through a staging buffer.  Both ways are run.  On lattices of a
+little more than 2^20 nodes (one full chunk and a ragged one) every node must land where it belongs:
   - FP64 storage: get_state(set_state(x)) equals x to within one rounding of (x - rest) + rest;
   - 16-bit storage (two-buffer and the interleaved in-place layout): each deviation comes back
     within one unit roundoff of the storage type (FP16: plus half its subnormal spacing, 2^-25),
@@ -79,8 +81,15 @@ def _check_roundtrip(lat, rest_f, rest_g, storage, seed):
         assert np.array_equal(f2, f1) and np.array_equal(g2, g1)
 
 
+@pytest.fixture(params=["direct", "staged"])
+def host_mode(request, monkeypatch):
+    """The handle reads LKS_HOST_STAGING when it is created."""
+    monkeypatch.setenv("LKS_HOST_STAGING", "1" if request.param == "staged" else "0")
+    return request.param
+
+
 @pytest.mark.parametrize("storage,inplace", [("f64", False), ("bf16", False), ("f16", True)])
-def test_2d_state_roundtrip_over_two_chunks(mods, storage, inplace):
+def test_2d_state_roundtrip_over_two_chunks(mods, host_mode, storage, inplace):
     lks, _ = mods
     nx, ny = 1032, 1023  # 1,055,736 nodes = 2^20 + 7160
     lat = lks.Lattice(nx, ny, 0.8, 0.8, 0.03, 0.0, "link", storage, inplace=inplace)
@@ -95,7 +104,7 @@ def test_2d_state_roundtrip_over_two_chunks(mods, storage, inplace):
 
 
 @pytest.mark.parametrize("storage", ["f64", "bf16"])
-def test_3d_state_roundtrip_over_two_chunks(mods, storage):
+def test_3d_state_roundtrip_over_two_chunks(mods, host_mode, storage):
     _, l3 = mods
     nx, ny, nz = 128, 91, 91  # 1,059,968 nodes = 2^20 + 11392
     lat = l3.Lattice3D(nx, ny, nz, 0.8, 0.7, 0.02, 0.0, storage)
