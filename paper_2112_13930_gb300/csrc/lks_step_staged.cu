@@ -11,15 +11,16 @@
 // x: wrapped copies at the row ends), completing on the stage's `full` mbarrier.  Sixteen consumer
 // warps take two x-adjacent nodes per thread as one float2 (packed FP32x2 arithmetic): 19 words of
 // the staged rows (byte_perm for the x shift), the wall closure, the collision, 19 packed words
-// stored; each warp then arrives on the stage's `empty` mbarrier, which the producer waits for
-// before it refills the stage.  Every wait is bounded (kWaitNs); one that runs out sets *err and
+// stored; each warp arrives on the stage's `empty` mbarrier (FP16: once its words are in registers;
+// BF16: after its stores), which the producer waits for before it refills the stage.  Every wait is bounded (kWaitNs); one that runs out sets *err and
 // ends that warp's loop, and the producer waits, within the same limit, for its last copies to each
 // stage before it returns.
 //
 // One block of 16 consumer warps per SM with 1024-node tasks (2 KB copies) beat two blocks of 8
 // warps with 512-node tasks at 4096^2: 76-80 against 71-72 GLUPS (the copies per byte halve).  Rows
 // without a wall run a compile-time path without the closure code (BF16, moment closure: 79.8
-// against 76.1 GLUPS).
+// against 76.1 GLUPS).  A launch of a whole producer warpgroup that moved registers to the consumers
+// with setmaxnreg (32 producer, 112 consumer) ran slower for both 16-bit types (73.4 GLUPS).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -181,7 +182,11 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
         return;
     }
 
-    // consumers: thread tid holds nodes x0 + 2 tid and x0 + 2 tid + 1 of the task's row
+    // consumers: thread tid holds nodes x0 + 2 tid and x0 + 2 tid + 1 of the task's row.  With FP16
+    // a warp hands its stage back as soon as its 19 words are in registers (4096^2: 78.8 against
+    // 74.6 GLUPS); with BF16 after the collision and the stores, since the early release costs
+    // registers beyond the 96 a thread of this block has and was measured slower (78.0 against 79.5).
+    constexpr bool kEarlyRelease = std::is_same<S, __half>::value;
     typedef Packed<S> P;
     const int xw = kHaloW + tid;
     for (int64_t it = 0; it < nmine; ++it) {
@@ -193,27 +198,38 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
         const int64_t t = t0 + it * G;
         const int y = (int)(t / nseg), x0 = (int)(t % nseg) * kSegX;
         const int T = min(kSegX, nx - x0);
-        if (2 * tid < T) {
+        const bool active = 2 * tid < T;
+        {
             const bool bottom = (y == 0), top = (y == ny - 1);
             const uint32_t* st = stage0 + s * kStageW;
             // rows without a wall (all but two) take a path with no closure code
             auto body = [&](auto walls) {
                 constexpr bool W = decltype(walls)::value;
+                uint32_t u[kSlots];
+                if (active) {
+#pragma unroll
+                    for (int k = 0; k < kSlots; ++k) {
+                        const int a = dir_of(k), ex = ex9(a), ey = ey9(a);
+                        const bool wall = W && ((ey == 1 && bottom) || (ey == -1 && top));
+                        const uint32_t* row = st + k * kSlotW;
+                        if (wall || ex == 0)
+                            u[k] = row[xw];
+                        else if (ex == 1)  // x <- x - 1 (high half of the word before), x + 1 <- x
+                            u[k] = __byte_perm(row[xw - 1], row[xw], 0x5432);
+                        else  // x <- x + 1, x + 1 <- x + 2 (low half of the word after)
+                            u[k] = __byte_perm(row[xw], row[xw + 1], 0x5432);
+                    }
+                }
+                if constexpr (kEarlyRelease) {
+                    // the warp's words are in registers (still packed): the stage goes back to the
+                    // producer before the collision and the stores
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                }
+                if (!active) return;
                 float2 v[kSlots];
 #pragma unroll
-                for (int k = 0; k < kSlots; ++k) {
-                    const int a = dir_of(k), ex = ex9(a), ey = ey9(a);
-                    const bool wall = W && ((ey == 1 && bottom) || (ey == -1 && top));
-                    const uint32_t* row = st + k * kSlotW;
-                    uint32_t w;
-                    if (wall || ex == 0)
-                        w = row[xw];
-                    else if (ex == 1)  // x <- x - 1 (high half of the word before), x + 1 <- x
-                        w = __byte_perm(row[xw - 1], row[xw], 0x5432);
-                    else  // x <- x + 1, x + 1 <- x + 2 (low half of the word after)
-                        w = __byte_perm(row[xw], row[xw + 1], 0x5432);
-                    v[k] = make_float2(P::lo(w), P::hi(w));
-                }
+                for (int k = 0; k < kSlots; ++k) v[k] = make_float2(P::lo(u[k]), P::hi(u[k]));
                 float2 f[9], gx[5], gy[5];
 #pragma unroll
                 for (int a = 0; a < 9; ++a) f[a] = v[a];
@@ -257,8 +273,10 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
             else
                 body(std::false_type{});
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
+        if constexpr (!kEarlyRelease) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
     }
 }
 
