@@ -162,8 +162,9 @@ enum {
 /* Moments of the current state: rho = sum f, rho u = sum f e - F/2 (the
  * post-collision form of rho u = sum f e + F/2 of Sec. V), B = sum g
  * (Eq. zerothmomentofg), accumulated in FP64.  host_out is caller-allocated
- * host memory; per-node moments are written into it by the moment kernel or
- * through the staging buffer, as lks_get_state writes.  Synchronises the stream. */
+ * host memory; per-node moments are written into it by the moment kernel when
+ * it is page-locked, else through the staging buffer, as lks_get_state writes.
+ * Synchronises the stream. */
 lks_status lks_moments(lks_handle* h, int what, double* host_out);
 
 /* Same as lks_moments but writes into caller-allocated device memory
@@ -188,19 +189,20 @@ lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int
 
 /* Copy the state out as FP64 absolute populations (deviation + rest
  * equilibrium): host_f 9 x ny x nx, host_g 2 x 5 x ny x nx, layouts as above.
- * Where the device accesses pageable host memory coherently (a GPU attached to a
- * Grace CPU over NVLink-C2C) and LKS_HOST_STAGING is unset or "0" when the handle is
- * created, one conversion kernel writes host_f and host_g itself; they may be pinned
- * or pageable.  Otherwise it converts 2^20 nodes at a time through a staging buffer
- * of 19 x 2^20 doubles (152 MB; fewer for smaller lattices) that the handle
- * allocates on first use and keeps until lks_destroy; LKS_ENOMEM if that allocation
- * fails.  Either way the arrays must hold the full sizes above.  Synchronises. */
+ * If host_f and host_g are page-locked (cudaHostAlloc, cudaHostRegister) and
+ * LKS_HOST_STAGING is unset or "0", one conversion kernel writes them through
+ * their mapped device addresses.  Otherwise the state is converted 2^20 nodes at a
+ * time into a staging buffer of 19 x 2^20 doubles (152 MB; fewer for smaller
+ * lattices) and copied out plane by plane; the handle allocates that buffer on
+ * first use and keeps it until lks_destroy (LKS_ENOMEM if the allocation fails).
+ * Either way the arrays must hold the full sizes above.  Synchronises. */
 lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g);
 
 /* Replace the state by FP64 absolute populations from host memory (same
  * layout as lks_get_state), rounded to the storage type; resets the step
- * counter and the residual snapshot.  Read directly or through the staging buffer
- * as lks_get_state writes.  Synchronises. */
+ * counter and the residual snapshot.  Page-locked arrays are read by the
+ * conversion kernel, pageable ones through the staging buffer, as lks_get_state
+ * writes them.  Synchronises. */
 lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host_g);
 
 /* Block until all work of the handle has finished; reports asynchronous errors. */

@@ -89,11 +89,11 @@ lks_status lks3_run_to_steady(lks3_handle* h, double tol, int64_t check_every, i
                               int64_t* steps_out, double* r_out);
 
 /* State as FP64 absolute populations (deviation + rest): host_f 19 x N, host_g 21 x N.
- * Host arrays are written by the conversion kernel itself where the device accesses pageable
- * host memory coherently (LKS_HOST_STAGING unset or "0" at creation), else through a staging
- * buffer of 40 x 2^20 doubles (335 MB; fewer for smaller lattices), 2^20 nodes at a time, that
- * the handle allocates on first use and keeps until lks3_destroy (LKS_ENOMEM if that fails).
- * lks3_moments with LKS_MOMENTS_NODES works the same way.  Synchronises. */
+ * Page-locked host arrays are written by the conversion kernel itself (LKS_HOST_STAGING unset or
+ * "0"); pageable ones through a staging buffer of 40 x 2^20 doubles (335 MB; fewer for smaller
+ * lattices), 2^20 nodes at a time, that the handle allocates on first use and keeps until
+ * lks3_destroy (LKS_ENOMEM if that fails).  lks3_moments with LKS_MOMENTS_NODES works the same
+ * way.  Synchronises. */
 lks_status lks3_get_state(lks3_handle* h, double* host_f, double* host_g);
 
 /* Replace the state by FP64 absolute populations (rounded to the storage type); resets the step

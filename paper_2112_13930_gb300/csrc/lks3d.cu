@@ -764,7 +764,6 @@ struct lks3_handle {
     unsigned staged_grid = 0;  // resident blocks of it on the device
     double* host4 = nullptr;  // pinned
     double* state_stage = nullptr;  // 40 * min(N, 2^20) doubles for state and moment transfers, on first use
-    bool host_direct = false;       // kernels read and write caller host arrays directly (pageable access)
     double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
     int64_t steps = 0;
     std::string err;
@@ -924,7 +923,6 @@ lks_status lks3_create(const lks3_params* p, lks3_handle** out) {
     h->prof = (double*)(h->base + h->L.off_prof);
     h->rest = (double*)(h->base + h->L.off_rest);
     h->flag = (int*)(h->base + h->L.off_flag);
-    h->host_direct = lks::host_access_direct();
     h->staged = (p->storage == LKS_BF16_DEV || p->storage == LKS_F16_DEV) && p->nx % 8 == 0 && p->nx <= kTaskNodes3;
     double rest[19];
     for (int a = 0; a < 19; ++a) rest[a] = f_rest(a, p->B0);
@@ -1001,19 +999,21 @@ lks_status lks3_moments(lks3_handle* h, int what, double* host_out) {
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(host_out, h->prof, 7 * (size_t)p.ny * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     } else if (what == LKS_MOMENTS_NODES) {
-        // directly into host_out (one chunk of N nodes), or M nodes at a time through the staging buffer
+        // page-locked host_out: written by the kernel (one chunk of N nodes); else M nodes at a time
+        // through the staging buffer
+        double* direct = (double*)lks::host_direct_ptr(host_out);
         int64_t M = N;
-        if (!h->host_direct) {
+        if (!direct) {
             if (lks_status s = state_stage3(h, &M)) return s;
         }
-        double* out = h->host_direct ? host_out : h->state_stage;
+        double* out = direct ? direct : h->state_stage;
         e = cudaSuccess;
         for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
             const int64_t m = N - n0 < M ? N - n0 : M;
             LKS3_DISPATCH(p.storage, (moments3_kernel<S><<<grid_for(m), 256, 0, h->stream>>>(
                                          (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, n0, m, p.B0, p.Fx, out)));
             e = cudaGetLastError();
-            for (int k = 0; k < 7 && e == cudaSuccess && !h->host_direct; ++k)
+            for (int k = 0; k < 7 && e == cudaSuccess && !direct; ++k)
                 e = cudaMemcpyAsync(host_out + k * N + n0, out + k * m, m * sizeof(double), cudaMemcpyDeviceToHost,
                                     h->stream);
         }
@@ -1071,27 +1071,30 @@ lks_status lks3_run_to_steady(lks3_handle* h, double tol, int64_t check_every, i
     return LKS_OK;
 }
 
-// State transfers and per-node host moments: with host_direct one chunk of N nodes whose FP64 planes
-// are the caller's arrays themselves; otherwise M nodes at a time through the staging buffer, one copy
-// per plane.
+// State transfers and per-node host moments: for page-locked host arrays one chunk of N nodes whose
+// FP64 planes are the caller's arrays themselves; otherwise M nodes at a time through the staging
+// buffer, one copy per plane.
 lks_status lks3_get_state(lks3_handle* h, double* host_f, double* host_g) {
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail3(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
+    double* df = (double*)lks::host_direct_ptr(host_f);
+    double* dg = (double*)lks::host_direct_ptr(host_g);
+    const bool direct = df && dg;
     int64_t M = N;
-    if (!h->host_direct) {
+    if (!direct) {
         if (lks_status s = state_stage3(h, &M)) return s;
     }
     cudaError_t e = cudaSuccess;
     for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
         const int64_t m = N - n0 < M ? N - n0 : M;
-        double* of = h->host_direct ? host_f : h->state_stage;
-        double* og = h->host_direct ? host_g : h->state_stage + 19 * m;
+        double* of = direct ? df : h->state_stage;
+        double* og = direct ? dg : h->state_stage + 19 * m;
         LKS3_DISPATCH(h->p.storage, (to_abs3_kernel<S, C><<<grid_for(m), 256, 0, h->stream>>>(
                                         (const S*)h->f[h->cur], (const S*)h->g[h->cur], N, n0, m, h->rest, h->p.B0,
                                         of, og)));
         e = cudaGetLastError();
-        for (int a = 0; a < 40 && e == cudaSuccess && !h->host_direct; ++a) {
+        for (int a = 0; a < 40 && e == cudaSuccess && !direct; ++a) {
             double* dst = a < 19 ? host_f + a * N + n0 : host_g + (a - 19) * N + n0;
             e = cudaMemcpyAsync(dst, h->state_stage + a * m, m * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
         }
@@ -1105,16 +1108,19 @@ lks_status lks3_set_state(lks3_handle* h, const double* host_f, const double* ho
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail3(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny * h->p.nz;
+    const double* df = (const double*)lks::host_direct_ptr(host_f);
+    const double* dg = (const double*)lks::host_direct_ptr(host_g);
+    const bool direct = df && dg;
     int64_t M = N;
-    if (!h->host_direct) {
+    if (!direct) {
         if (lks_status s = state_stage3(h, &M)) return s;
     }
     cudaError_t e = cudaSuccess;
     for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += M) {
         const int64_t m = N - n0 < M ? N - n0 : M;
-        const double* sf = host_f;
-        const double* sg = host_g;
-        if (!h->host_direct) {
+        const double* sf = df;
+        const double* sg = dg;
+        if (!direct) {
             for (int a = 0; a < 40 && e == cudaSuccess; ++a) {
                 const double* src = a < 19 ? host_f + a * N + n0 : host_g + (a - 19) * N + n0;
                 e = cudaMemcpyAsync(h->state_stage + a * m, src, m * sizeof(double), cudaMemcpyHostToDevice,

@@ -155,20 +155,21 @@ StepParams<double> make_step_params(int nx, int ny, int closure, double tau_f, d
     return s;
 }
 
-// Whether the conversion kernels of state transfers and per-node host moments may read and write the
-// caller's host arrays themselves: the device must access pageable host memory coherently (true with
-// the host page tables of a Grace CPU over NVLink-C2C, where kernel accesses run at the link's rate).
-// LKS_HOST_STAGING=1 in the environment forces the staged copies.
-bool host_access_direct() {
+// The device address through which a kernel may read or write the host array at p directly:
+// page-locked memory (cudaHostAlloc, cudaHostRegister) is mapped into the device's address space,
+// and kernels stream it at the rate of the host link (NVLink-C2C on a Grace host: 211 GB/s in,
+// 194 GB/s out, as fast as the copy engine).  nullptr for pageable memory, whose pages the copy
+// engine handles far better (a kernel's first touch of a fresh pageable page faults it in through
+// the host page tables one page at a time), and when LKS_HOST_STAGING=1 forces the staged copies.
+void* host_direct_ptr(const void* p) {
     const char* env = getenv("LKS_HOST_STAGING");
-    if (env && env[0] && strcmp(env, "0") != 0) return false;
-    int dev = 0, pageable = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) {
+    if (!p || (env && env[0] && strcmp(env, "0") != 0)) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return nullptr;
     }
-    return pageable != 0;
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 }  // namespace lks
@@ -189,7 +190,6 @@ struct lks_handle {
     double* dout = nullptr;
     double* prof = nullptr;
     double* state_stage = nullptr;  // 19 * min(N, 2^20) doubles for state and moment transfers, on first use
-    bool host_direct = false;       // kernels read and write caller host arrays directly (pageable access)
     double* host_small = nullptr;  // pinned 8 doubles
     int* flag = nullptr;
     bool staged = false;              // 16-bit, nx % 8 == 0, nx >= 1024: the staged kernels
@@ -274,9 +274,9 @@ cudaError_t build_graph(lks_handle* h, int start) {
 }
 
 
-// Otherwise state transfers and per-node host moments convert kStateChunk nodes at a time through a
-// staging buffer the handle keeps, so their device memory stays bounded (152 MB) whatever the lattice
-// size.
+// Otherwise (pageable host arrays) state transfers and per-node host moments convert kStateChunk nodes
+// at a time through a staging buffer the handle keeps, so their device memory stays bounded (152 MB)
+// whatever the lattice size.
 constexpr int64_t kStateChunk = int64_t(1) << 20;
 
 lks_status state_stage(lks_handle* h, int64_t* chunk) {
@@ -399,7 +399,6 @@ lks_status lks_create(const lks_params* p, lks_handle** out) {
     e = cudaHostAlloc((void**)&h->host_small, 8 * sizeof(double), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream);
-    if (e == cudaSuccess) h->host_direct = lks::host_access_direct();
     if (e == cudaSuccess && lks::staged_step_applies(p->storage, p->nx, p->inplace)) {
         e = lks::prepare_staged_step(p->storage, p->inplace, &h->ss.grid);
         h->ss.err = h->flag;
@@ -487,9 +486,9 @@ lks_status lks_moments(lks_handle* h, int what, double* host_out) {
         if (lks_status s = lks_moments_device(h, what, h->prof)) return s;
         e = cudaMemcpyAsync(host_out, h->prof, 5 * (size_t)h->p.ny * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream);
-    } else if (h->host_direct) {
+    } else if (double* dout = (double*)lks::host_direct_ptr(host_out)) {  // page-locked: written by the kernel
         const int64_t N = (int64_t)h->p.nx * h->p.ny;
-        e = lks::launch_node_moments(h->p.storage, h->f[h->cur], h->g[h->cur], N, 0, N, h->p.B0, h->p.Fx, host_out,
+        e = lks::launch_node_moments(h->p.storage, h->f[h->cur], h->g[h->cur], N, 0, N, h->p.B0, h->p.Fx, dout,
                                      h->stream, h->p.coupling, h->p.tau_m, ilv_of(h));
     } else {
         int64_t M = 0;
@@ -555,10 +554,12 @@ lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g) {
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    double* df = (double*)lks::host_direct_ptr(host_f);
+    double* dg = (double*)lks::host_direct_ptr(host_g);
     cudaError_t e;
-    if (h->host_direct) {
-        e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], N, 0, N, h->p.B0, host_f, host_g,
-                               h->stream, h->p.coupling, ilv_of(h));
+    if (df && dg) {  // page-locked: one kernel writes the arrays
+        e = lks::launch_to_abs(h->p.storage, h->f[h->cur], h->g[h->cur], N, 0, N, h->p.B0, df, dg, h->stream,
+                               h->p.coupling, ilv_of(h));
     } else {
         int64_t M = 0;
         if (lks_status s = state_stage(h, &M)) return s;
@@ -574,10 +575,12 @@ lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!host_f || !host_g) return fail(h, LKS_EINVAL, "host_f/host_g is NULL");
     const int64_t N = (int64_t)h->p.nx * h->p.ny;
+    const double* df = (const double*)lks::host_direct_ptr(host_f);
+    const double* dg = (const double*)lks::host_direct_ptr(host_g);
     cudaError_t e;
-    if (h->host_direct) {
-        e = lks::launch_from_abs(h->p.storage, host_f, host_g, N, 0, N, h->p.B0, h->f[h->cur], h->g[h->cur],
-                                 h->stream, h->p.coupling, ilv_of(h));
+    if (df && dg) {  // page-locked: one kernel reads the arrays
+        e = lks::launch_from_abs(h->p.storage, df, dg, N, 0, N, h->p.B0, h->f[h->cur], h->g[h->cur], h->stream,
+                                 h->p.coupling, ilv_of(h));
     } else {
         int64_t M = 0;
         if (lks_status s = state_stage(h, &M)) return s;

@@ -94,9 +94,9 @@ cudaError_t launch_moments(int storage, const void* f, const void* g, int nx, in
                            int what, double* out, cudaStream_t st, int coupling = 0, double tau_m = 1.0,
                            int ilv = 0);
 
-// Whether conversion kernels may read and write caller host arrays directly: the current device accesses
-// pageable host memory coherently and LKS_HOST_STAGING is unset or "0".
-bool host_access_direct();
+// The device address of the host array at p if conversion kernels may access it directly (page-locked
+// memory, LKS_HOST_STAGING unset or "0"); nullptr otherwise.
+void* host_direct_ptr(const void* p);
 
 // Per-node moments of the M nodes n0 .. n0+M-1 of an N-node state: out[m*M + i] for node n0 + i.
 cudaError_t launch_node_moments(int storage, const void* f, const void* g, int64_t N, int64_t n0, int64_t M,

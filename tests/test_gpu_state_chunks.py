@@ -1,10 +1,11 @@
 """State transfers of lattices larger than one conversion chunk (2^20 nodes), on the GPU.
 
 lks_get_state / lks_set_state (and the 3D pair) convert between stored deviations and FP64
-absolute populations either directly in the caller's host arrays (devices with coherent access to
-pageable host memory, such as a GPU attached to a Grace CPU) or, with LKS_HOST_STAGING=1 or
-elsewhere, 2^20 nodes at a time through a staging buffer.  Both ways are run.  On lattices of a
-little more than 2^20 nodes (one full chunk and a ragged one) every node must land where it belongs:
+absolute populations either directly in the caller's host arrays when they are page-locked (one
+kernel over the mapped memory) or, for pageable arrays and with LKS_HOST_STAGING=1, 2^20 nodes at a
+time through a staging buffer.  All three are run: page-locked, pageable, and page-locked with the
+staging forced.  On lattices of a little more than 2^20 nodes (one full chunk and a ragged one)
+every node must land where it belongs:
   - FP64 storage: get_state(set_state(x)) equals x to within one rounding of (x - rest) + rest;
   - 16-bit storage (two-buffer and the interleaved in-place layout): each deviation comes back
     within one unit roundoff of the storage type (FP16: plus half its subnormal spacing, 2^-25),
@@ -56,6 +57,49 @@ def _check_moments(mg, mo):
         assert float(np.max(np.abs(mg[k] - mo[k]))) <= 1e-13, k
 
 
+class Host:
+    """get/set_state and per-node moments through the C ABI into host arrays of one kind."""
+
+    def __init__(self, mods, lat, mode):
+        import torch
+        self.pinned = mode != "pageable"
+        self.lat = lat
+        lks, l3 = mods
+        if isinstance(lat, l3.Lattice3D):
+            lib, self.ptr, self.check = l3.lib(), l3._ptr, l3._check
+            self.get, self.set, self.mom = lib.lks3_get_state, lib.lks3_set_state, lib.lks3_moments
+            n = (lat.nz, lat.ny, lat.nx)
+            self.shapes = ((19,) + n, (3, 7) + n, (7,) + n)
+        else:
+            lib, self.ptr, self.check = lks.load(), lks._dptr, lks._check
+            self.get, self.set, self.mom = lib.lks_get_state, lib.lks_set_state, lib.lks_moments
+            n = (lat.ny, lat.nx)
+            self.shapes = ((9,) + n, (2, 5) + n, (5,) + n)
+        self.nodes_what = lks.MOMENTS_NODES
+        self.torch = torch
+
+    def empty(self, shape):
+        if self.pinned:
+            return self.torch.empty(shape, dtype=self.torch.float64, pin_memory=True).numpy()
+        return np.empty(shape)
+
+    def get_state(self):
+        f, g = self.empty(self.shapes[0]), self.empty(self.shapes[1])
+        self.check(self.get(self.lat._h, self.ptr(f), self.ptr(g)), self.lat._h)
+        return f, g
+
+    def set_state(self, f, g):
+        hf, hg = self.empty(self.shapes[0]), self.empty(self.shapes[1])
+        hf[...] = f
+        hg[...] = g
+        self.check(self.set(self.lat._h, self.ptr(hf), self.ptr(hg)), self.lat._h)
+
+    def moments(self):
+        m = self.empty(self.shapes[2])
+        self.check(self.mom(self.lat._h, self.nodes_what, self.ptr(m)), self.lat._h)
+        return m
+
+
 def _perturbed(rest_f, rest_g, seed):
     rng = np.random.default_rng(seed)
     f = rest_f + 1e-3 * rng.uniform(-1, 1, rest_f.shape) * np.abs(rest_f)
@@ -63,10 +107,10 @@ def _perturbed(rest_f, rest_g, seed):
     return f, g
 
 
-def _check_roundtrip(lat, rest_f, rest_g, storage, seed):
+def _check_roundtrip(host, rest_f, rest_g, storage, seed):
     f, g = _perturbed(rest_f, rest_g, seed)
-    lat.set_state(f, g)
-    f1, g1 = lat.get_state()
+    host.set_state(f, g)
+    f1, g1 = host.get_state()
     u = U_S[storage]
     for x, y, r in ((f, f1, rest_f), (g, g1, rest_g)):
         d = x - r
@@ -76,15 +120,15 @@ def _check_roundtrip(lat, rest_f, rest_g, storage, seed):
             # one rounding to FP32, then one to the 16-bit type
             assert np.max(np.abs((y - r) - d) - 1.01 * u * np.abs(d) - ABS[storage]) <= 0.0
     if storage != "f64":
-        lat.set_state(f1, g1)
-        f2, g2 = lat.get_state()
+        host.set_state(f1, g1)
+        f2, g2 = host.get_state()
         assert np.array_equal(f2, f1) and np.array_equal(g2, g1)
 
 
-@pytest.fixture(params=["direct", "staged"])
+@pytest.fixture(params=["pinned", "pageable", "pinned-staged"])
 def host_mode(request, monkeypatch):
-    """The handle reads LKS_HOST_STAGING when it is created."""
-    monkeypatch.setenv("LKS_HOST_STAGING", "1" if request.param == "staged" else "0")
+    """LKS_HOST_STAGING is read by every transfer."""
+    monkeypatch.setenv("LKS_HOST_STAGING", "1" if request.param == "pinned-staged" else "0")
     return request.param
 
 
@@ -94,11 +138,12 @@ def test_2d_state_roundtrip_over_two_chunks(mods, host_mode, storage, inplace):
     nx, ny = 1032, 1023  # 1,055,736 nodes = 2^20 + 7160
     lat = lks.Lattice(nx, ny, 0.8, 0.8, 0.03, 0.0, "link", storage, inplace=inplace)
     try:
-        rest_f, rest_g = lat.get_state()
-        _check_roundtrip(lat, rest_f, rest_g, storage, seed=11)
+        host = Host(mods, lat, host_mode)
+        rest_f, rest_g = host.get_state()
+        _check_roundtrip(host, rest_f, rest_g, storage, seed=11)
         if storage == "f64":
-            f, g = lat.get_state()
-            _check_moments(lat.moments(), _sum_moments(f, g, E2, 2))
+            f, g = host.get_state()
+            _check_moments(host.moments(), _sum_moments(f, g, E2, 2))
     finally:
         lat.close()
 
@@ -109,10 +154,11 @@ def test_3d_state_roundtrip_over_two_chunks(mods, host_mode, storage):
     nx, ny, nz = 128, 91, 91  # 1,059,968 nodes = 2^20 + 11392
     lat = l3.Lattice3D(nx, ny, nz, 0.8, 0.7, 0.02, 0.0, storage)
     try:
-        rest_f, rest_g = lat.get_state()
-        _check_roundtrip(lat, rest_f, rest_g, storage, seed=12)
+        host = Host(mods, lat, host_mode)
+        rest_f, rest_g = host.get_state()
+        _check_roundtrip(host, rest_f, rest_g, storage, seed=12)
         if storage == "f64":
-            f, g = lat.get_state()
-            _check_moments(lat.moments(), _sum_moments(f, g, E3, 3))
+            f, g = host.get_state()
+            _check_moments(host.moments(), _sum_moments(f, g, E3, 3))
     finally:
         lat.close()
