@@ -206,6 +206,14 @@ lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g);
 lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host_g);
 
 /* Block until all work of the handle has finished; reports asynchronous errors. */
+/* Self-test of the bounded device waits (failure detection without a GPU fault): enqueue on the
+ * handle's stream one warp that waits, with the staged kernels' bounded wait, on a shared-memory
+ * barrier nothing completes, gives up after limit_s seconds (0 < limit_s <= 1) and records the
+ * timeout as a staged step's wait would.  The next synchronising call returns LKS_ETIMEOUT and the
+ * handle stays in that error state (destroy it; the CUDA context remains usable).  LKS_EINVAL for a
+ * handle that runs no staged kernel or a limit out of range. */
+lks_status lks_selftest_wait_timeout(lks_handle* h, double limit_s);
+
 lks_status lks_sync(lks_handle* h);
 
 /* Release the handle and the memory it owns.  Safe on NULL. */

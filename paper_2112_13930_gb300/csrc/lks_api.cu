@@ -595,6 +595,15 @@ lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host
     return LKS_OK;
 }
 
+lks_status lks_selftest_wait_timeout(lks_handle* h, double limit_s) {
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!h->staged) return fail(h, LKS_EINVAL, "lks_selftest_wait_timeout: the handle runs no staged kernel");
+    if (!(limit_s > 0.0 && limit_s <= 1.0)) return fail(h, LKS_EINVAL, "lks_selftest_wait_timeout: limit not in (0, 1] s");
+    cudaError_t e = lks::launch_wait_timeout_probe(h->flag, (uint64_t)(limit_s * 1e9), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lks_selftest_wait_timeout");
+    return LKS_OK;
+}
+
 lks_status lks_sync(lks_handle* h) {
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     cudaError_t e = cudaStreamSynchronize(h->stream);

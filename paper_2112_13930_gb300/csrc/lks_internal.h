@@ -71,6 +71,10 @@ bool staged_step_applies(int storage, int nx, int inplace);
 // Opt the storage type's staged kernels (two-buffer or in-place) into their shared memory (before any
 // graph capture) and return the grid that keeps one wave of blocks resident.
 cudaError_t prepare_staged_step(int storage, int inplace, unsigned* grid);
+// One warp that waits at most limit_ns on an mbarrier nothing completes, then sets *err (self-test of
+// the bounded waits of the staged kernels).
+cudaError_t launch_wait_timeout_probe(int* err, uint64_t limit_ns, cudaStream_t st);
+
 cudaError_t launch_step_staged(int storage, int closure, const void* fin, const void* gin, void* fout, void* gout,
                                const StepParams<float>& p, const StagedStep& ss, cudaStream_t st);
 cudaError_t launch_step_aa_staged(int storage, int closure, void* f, void* g, const StepParams<float>& p,

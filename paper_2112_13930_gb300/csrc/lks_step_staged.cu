@@ -481,6 +481,20 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_aa_staged(S* __restri
     }
 }
 
+// Failure detection without a GPU fault: one warp waits, with the staged kernels' bounded wait, on
+// a freshly initialised mbarrier that nothing arrives on (its first phase never completes), gives
+// up after limit_ns and records the timeout in *err as a staged step's wait would.  No copy is in
+// flight to that barrier, so returning is safe.
+__global__ void wait_timeout_probe_kernel(int* err, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit_ns)) atomicExch(err, 1);
+}
+
 template <typename K>
 cudaError_t prepare_kernel(K kernel, int* blocks) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
@@ -561,6 +575,11 @@ cudaError_t prepare_staged_step(int storage, int inplace, unsigned* grid) {
         e = storage == 2 ? prepare_typed<__nv_bfloat16>(inplace, &blocks) : prepare_typed<__half>(inplace, &blocks);
     *grid = (unsigned)(sms * blocks);
     return e;
+}
+
+cudaError_t launch_wait_timeout_probe(int* err, uint64_t limit_ns, cudaStream_t st) {
+    wait_timeout_probe_kernel<<<1, 32, 0, st>>>(err, limit_ns);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step_aa_staged(int storage, int closure, void* f, void* g, const StepParams<float>& p,

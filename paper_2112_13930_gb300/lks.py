@@ -68,6 +68,7 @@ SIGNATURES = {
     "lks_get_state": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     "lks_set_state": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     "lks_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "lks_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "lks_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "lks_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "lks_status_string": (ctypes.c_char_p, [ctypes.c_int]),
