@@ -246,13 +246,15 @@ def test_full_size_perturbed_fp64_sampled_rows(lks):
     g.close()
 
 
-def test_full_size_fp32_timed_configuration_one_step(lks):
-    """The benchmark's timed configuration itself (4096 x 4096, moment-based closure, FP32 storage,
-    c = 1 on both walls, top wall moving) from a seeded perturbation: one step against the FP64
-    oracle over the whole lattice, every population of rows at both walls and in the interior
-    within the one-step bound 8 u_s max|d| derived above."""
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_full_size_timed_configuration_one_step(lks, storage):
+    """The benchmark's timed configuration itself (4096 x 4096, moment-based closure, c = 1 on both
+    walls, top wall moving) in its FP32 storage and the 16-bit extras' (staged kernel, ~108 tasks
+    per persistent block), from a seeded perturbation: one step against the FP64 oracle over the
+    whole lattice, every population of rows at both walls and in the interior within the one-step
+    bound 8 u_s max|d| derived above."""
     n = 4096
-    o, g = _pair(lks, n, n, "moment", "f32", B0=0.001, Fx=1e-6, c=(1.0, 1.0), u=(0.0, 0.05), seed=20211228,
+    o, g = _pair(lks, n, n, "moment", storage, B0=0.001, Fx=1e-6, c=(1.0, 1.0), u=(0.0, 0.05), seed=20211228,
                  amp=1e-3)
     rest = oracle.Oracle(4, 4, 0.8, 0.8, 0.001, 1e-6, oracle.MOMENT, seed=0, perturb_amp=0.0)
     f_rest = rest.f[:, :1, :1]            # the rest state is the same at every node
@@ -264,8 +266,8 @@ def test_full_size_fp32_timed_configuration_one_step(lks):
     rows = [0, 1, 2, 1000, 2047, 4093, 4094, 4095]
     df = np.max(np.abs(o.f - f_rest))
     dg = np.max(np.abs(o.g - g_rest))
-    assert np.max(np.abs(fg[:, rows] - o.f[:, rows])) <= 8 * ONE_STEP["f32"] * df
-    assert np.max(np.abs(gg[:, :, rows] - o.g[:, :, rows])) <= 8 * ONE_STEP["f32"] * dg
+    assert np.max(np.abs(fg[:, rows] - o.f[:, rows])) <= 8 * ONE_STEP[storage] * df
+    assert np.max(np.abs(gg[:, :, rows] - o.g[:, :, rows])) <= 8 * ONE_STEP[storage] * dg
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
