@@ -228,3 +228,22 @@ def test_kernels_agree_bitwise_on_a_tiled_perturbed_state(l3, storage):
         assert np.array_equal(gb, np.concatenate([ga, ga], axis=-1)), n
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_full_size_one_step(l3, storage):
+    """The 3D benchmark size (256^3; FP32: the one-node kernel, BF16: the staged kernel with ~100
+    tasks per persistent block) with both walls at c = 1 and the top one moving, from a perturbed
+    state: one step against the FP64 oracle over the whole lattice, every population of the planes
+    y = 0, 1, 127, 254, 255 within 8 u_s of the largest deviation from rest."""
+    n = 256
+    o, gpu, f_rest, g_rest = _pair(l3, n, n, n, (1.0, 1.0), (0.0, 0.05), storage, seed=6)
+    o.step(1)
+    gpu.step(1)
+    fg, gg = gpu.get_state()
+    gpu.close()
+    ys = [0, 1, 127, 254, 255]
+    df = float(np.max(np.abs(o.f - f_rest)))
+    dg = float(np.max(np.abs(o.g - g_rest)))
+    assert np.max(np.abs(fg[:, :, ys] - o.f[:, :, ys])) <= 8 * ONE_STEP[storage] * df
+    assert np.max(np.abs(gg[:, :, :, ys] - o.g[:, :, :, ys])) <= 8 * ONE_STEP[storage] * dg
