@@ -100,6 +100,12 @@ lks_status lks3_get_state(lks3_handle* h, double* host_f, double* host_g);
  * counter and the residual snapshot.  Synchronises; same staging buffer. */
 lks_status lks3_set_state(lks3_handle* h, const double* host_f, const double* host_g);
 
+/* Self-test of the staged kernel's bounded waits, as lks_selftest_wait_timeout: the next
+ * synchronising call returns LKS_ETIMEOUT and the handle stays in that error state; LKS_EINVAL for a
+ * handle that runs no staged kernel (FP32/FP64, or nx not a multiple of 8 or above 512) or a limit
+ * outside (0, 1] s. */
+lks_status lks3_selftest_wait_timeout(lks3_handle* h, double limit_s);
+
 lks_status lks3_sync(lks3_handle* h);
 lks_status lks3_destroy(lks3_handle* h);
 

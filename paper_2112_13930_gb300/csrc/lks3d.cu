@@ -1142,6 +1142,16 @@ lks_status lks3_set_state(lks3_handle* h, const double* host_f, const double* ho
     return LKS_OK;
 }
 
+lks_status lks3_selftest_wait_timeout(lks3_handle* h, double limit_s) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!h->staged) return fail3(h, LKS_EINVAL, "lks3_selftest_wait_timeout: the handle runs no staged kernel");
+    if (!(limit_s > 0.0 && limit_s <= 1.0))
+        return fail3(h, LKS_EINVAL, "lks3_selftest_wait_timeout: limit not in (0, 1] s");
+    cudaError_t e = lks::launch_wait_timeout_probe(h->flag, (uint64_t)(limit_s * 1e9), h->stream);
+    if (e != cudaSuccess) return cuda3(h, e, "lks3_selftest_wait_timeout");
+    return LKS_OK;
+}
+
 lks_status lks3_sync(lks3_handle* h) {
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     cudaError_t e = cudaStreamSynchronize(h->stream);

@@ -44,6 +44,7 @@ SIGNATURES = {
     "lks3_get_state": (_status, [_VP, _dp, _dp]),
     "lks3_set_state": (_status, [_VP, _dp, _dp]),
     "lks3_sync": (_status, [_VP]),
+    "lks3_selftest_wait_timeout": (_status, [_VP, ctypes.c_double]),
     "lks3_destroy": (_status, [_VP]),
     "lks3_last_error": (ctypes.c_char_p, [_VP]),
 }

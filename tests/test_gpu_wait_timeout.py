@@ -27,6 +27,12 @@ def lks():
     return mod
 
 
+@pytest.fixture(scope="module")
+def l3(lks):
+    from paper_2112_13930_gb300 import lks3d
+    return lks3d
+
+
 def _staged(lks):
     # BF16, nx a multiple of 8 and >= 1024: the staged two-buffer step
     return lks.Lattice(1032, 8, 0.8, 0.8, 0.02, 1e-6, "moment", "bf16", seed=3, perturb_amp=1e-3)
@@ -68,3 +74,25 @@ def test_selftest_rejects_unstaged_handles_and_bad_limits(lks):
         assert L.lks_selftest_wait_timeout(lat._h, bad) == lks.LKS_EINVAL
     lat.sync()  # nothing was enqueued: still healthy
     lat.close()
+
+
+def test_3d_wait_that_runs_out_reports_etimeout(lks, l3):
+    L = l3.lib()
+    lat = l3.Lattice3D(24, 8, 4, 0.8, 0.7, 0.02, 1e-6, "bf16")  # staged: BF16, nx % 8 == 0, nx <= 512
+    lat.step(3)
+    lat.sync()
+    limit = 0.05
+    t0 = time.perf_counter()
+    assert L.lks3_selftest_wait_timeout(lat._h, limit) == lks.LKS_OK
+    st = L.lks3_sync(lat._h)
+    dt = time.perf_counter() - t0
+    assert st == lks.LKS_ETIMEOUT
+    assert b"wait ran out" in L.lks3_last_error(lat._h)
+    assert limit <= dt < 5.0
+    lat.close()
+    f32 = l3.Lattice3D(24, 8, 4, 0.8, 0.7, 0.02, 1e-6, "f32")
+    assert L.lks3_selftest_wait_timeout(f32._h, limit) == lks.LKS_EINVAL
+    f32.step(3)
+    f32.sync()
+    assert np.all(np.isfinite(f32.moments()))
+    f32.close()
