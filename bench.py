@@ -323,6 +323,19 @@ def bench_ours(args):
                "d2h_bytes_per_step": int(round(5 * 8 * nodes / args.steps)),
                "timed": "lks_set_state (FP64 host->device + conversion) + lks_step(K) + lks_moments (nodes, "
                         "device->host), pinned host buffers"}
+        # the two host transfers of that region, each timed alone afterwards (best of 3, wall clock)
+        t_set, t_mom = [], []
+        for _ in range(3):
+            t1 = time.perf_counter()
+            lat.set_state(f_host, g_host)
+            t2 = time.perf_counter()
+            lks._check(lks.load().lks_moments(lat._h, lks.MOMENTS_NODES, lks._dptr(m_host)), lat._h)
+            t3 = time.perf_counter()
+            t_set.append(t2 - t1)
+            t_mom.append(t3 - t2)
+        e2e["breakdown_ms"] = {"lks_set_state": round(min(t_set) * 1e3, 2),
+                               "lks_moments_nodes": round(min(t_mom) * 1e3, 2),
+                               "steps_at_device_rate": round(per_launch * args.steps * 1e3, 2)}
         del f_host, g_host, m_host
     lat.close()
     del lat
