@@ -6,21 +6,26 @@
 // A task is a row segment of up to kSegX nodes (x0 .. x0 + T - 1 of row y).  For each of the 19
 // population slots (f_0..8, g_x0..4, g_y0..4) a producer warp copies, one slot per lane, the segment
 // of the row the slot pulls from (y - e_y; a link-closure wall row takes its own row of the opposite
-// plane; a moment-closure wall row fetches nothing for the slots it reconstructs) into one of
-// kStages shared-memory stages, with a 16-byte halo on each side for the x-shifted slots (periodic in
-// x: wrapped copies at the row ends), completing on the stage's `full` mbarrier.  Sixteen consumer
+// plane; a moment-closure wall row fetches nothing for the slots it reconstructs) into one of the
+// shared-memory stages, with a 16-byte halo on each side for the x-shifted slots (periodic in x:
+// wrapped copies at the row ends), completing on the stage's `full` mbarrier.  Sixteen consumer
 // warps take two x-adjacent nodes per thread as one float2 (packed FP32x2 arithmetic): 19 words of
 // the staged rows (byte_perm for the x shift), the wall closure, the collision, 19 packed words
-// stored; each warp arrives on the stage's `empty` mbarrier (FP16: once its words are in registers;
-// BF16: after its stores), which the producer waits for before it refills the stage.  Every wait is bounded (kWaitNs); one that runs out sets *err and
+// stored.  In the two-buffer kernel each lane first copies its 19 words into its column of the
+// warp's private scratch and the warp arrives on the stage's `empty` mbarrier at once, so the
+// producer refills the stage while the warp computes from the scratch; the in-place kernel arrives
+// after its stores.  Every wait is bounded (kWaitNs); one that runs out sets *err and
 // ends that warp's loop, and the producer waits, within the same limit, for its last copies to each
 // stage before it returns.
 //
 // One block of 16 consumer warps per SM with 1024-node tasks (2 KB copies) beat two blocks of 8
 // warps with 512-node tasks at 4096^2: 76-80 against 71-72 GLUPS (the copies per byte halve).  Rows
 // without a wall run a compile-time path without the closure code (BF16, moment closure: 79.8
-// against 76.1 GLUPS).  A launch of a whole producer warpgroup that moved registers to the consumers
-// with setmaxnreg (32 producer, 112 consumer) ran slower for both 16-bit types (73.4 GLUPS).
+// against 76.1 GLUPS).  Releasing the stage as soon as the words are read, through the per-warp
+// scratch (four stages instead of five): BF16 82.8, FP16 80.0 GLUPS against 79.4 and 78.8 with the
+// release after the stores.  Holding the words in registers across the release instead spilled at
+// the 96 registers a thread of this block has (BF16 78.0, FP16 78.7); a whole producer warpgroup
+// that moved registers to the consumers with setmaxnreg (32 / 112) ran at 73.4.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +49,12 @@ constexpr int kConsumerWarps = kSegX / 64;
 constexpr int kThreads = kSegX / 2 + 32;         // consumers + the producer warp
 constexpr uint64_t kWaitNs = 1000000000ull;      // 1 s
 constexpr size_t kSmem = 128 + (size_t)kStages * kStageW * 4;
+// The two-buffer kernel: four stages, and behind them a private scratch area per consumer warp into
+// which each lane copies its 19 staged words, so that the warp can hand its stage back at once.
+constexpr int kStagesTB = 4;
+constexpr int kScratchW = kSlots * 32;  // words per consumer warp
+constexpr size_t kSmemTB = 128 + (size_t)kStagesTB * kStageW * 4 + (size_t)kConsumerWarps * kScratchW * 4;
+static_assert(kSmemTB <= 227 * 1024, "shared memory per block");
 
 // D2Q9 (f) and D2Q5 (g) directions of slot k: k < 9 is f_k, 9..13 is g_x,k-9, 14..18 is g_y,k-14.
 __host__ __device__ constexpr int dir_of(int k) { return k < 9 ? k : (k < 14 ? k - 9 : k - 14); }
@@ -103,7 +114,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
                                                                    const StepParams<float> p, int* err) {
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(sm);
-    uint64_t* empty = full + kStages;
+    uint64_t* empty = full + kStagesTB;
     uint32_t* stage0 = reinterpret_cast<uint32_t*>(sm + 128);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nx = p.nx, ny = p.ny;
@@ -113,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
     const int64_t G = gridDim.x, t0 = blockIdx.x;
     const int64_t nmine = t0 < ntask ? (ntask - 1 - t0) / G + 1 : 0;  // tasks t0, t0 + G, ...
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kStagesTB; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumerWarps);
         }
@@ -129,8 +140,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
         const S* bw = base + (int64_t)plane_of(k, opp9(a)) * N;  // the opposite one (link walls)
         int64_t it = 0;
         for (; it < nmine; ++it) {
-            const int s = (int)(it % kStages);
-            const int64_t u = it / kStages;
+            const int s = (int)(it % kStagesTB);
+            const int64_t u = it / kStagesTB;
             if (u > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)(u - 1) & 1u, kWaitNs)) {
                 if (lane == 0) atomicExch(err, 1);
                 break;
@@ -174,24 +185,21 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
         }
         // no copy may be left in flight into this block's shared memory: wait for the last phase
         // issued to each stage (already complete unless a consumer gave up)
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kStagesTB; ++s) {
             if (it <= s) continue;
-            const int64_t u_last = (it - 1 - s) / kStages;
+            const int64_t u_last = (it - 1 - s) / kStagesTB;
             if (!mbar_wait_bounded(&full[s], (uint32_t)u_last & 1u, kWaitNs) && lane == 0) atomicExch(err, 1);
         }
         return;
     }
 
-    // consumers: thread tid holds nodes x0 + 2 tid and x0 + 2 tid + 1 of the task's row.  With FP16
-    // a warp hands its stage back as soon as its 19 words are in registers (4096^2: 78.8 against
-    // 74.6 GLUPS); with BF16 after the collision and the stores, since the early release costs
-    // registers beyond the 96 a thread of this block has and was measured slower (78.0 against 79.5).
-    constexpr bool kEarlyRelease = std::is_same<S, __half>::value;
+    // consumers: thread tid holds nodes x0 + 2 tid and x0 + 2 tid + 1 of the task's row
+    uint32_t* scr = stage0 + kStagesTB * kStageW + warp * kScratchW;
     typedef Packed<S> P;
     const int xw = kHaloW + tid;
     for (int64_t it = 0; it < nmine; ++it) {
-        const int s = (int)(it % kStages);
-        if (!mbar_wait_bounded(&full[s], (uint32_t)(it / kStages) & 1u, kWaitNs)) {
+        const int s = (int)(it % kStagesTB);
+        if (!mbar_wait_bounded(&full[s], (uint32_t)(it / kStagesTB) & 1u, kWaitNs)) {
             atomicExch(err, 1);
             break;
         }
@@ -205,31 +213,33 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
             // rows without a wall (all but two) take a path with no closure code
             auto body = [&](auto walls) {
                 constexpr bool W = decltype(walls)::value;
-                uint32_t u[kSlots];
                 if (active) {
 #pragma unroll
                     for (int k = 0; k < kSlots; ++k) {
                         const int a = dir_of(k), ex = ex9(a), ey = ey9(a);
                         const bool wall = W && ((ey == 1 && bottom) || (ey == -1 && top));
                         const uint32_t* row = st + k * kSlotW;
+                        uint32_t w;
                         if (wall || ex == 0)
-                            u[k] = row[xw];
+                            w = row[xw];
                         else if (ex == 1)  // x <- x - 1 (high half of the word before), x + 1 <- x
-                            u[k] = __byte_perm(row[xw - 1], row[xw], 0x5432);
+                            w = __byte_perm(row[xw - 1], row[xw], 0x5432);
                         else  // x <- x + 1, x + 1 <- x + 2 (low half of the word after)
-                            u[k] = __byte_perm(row[xw], row[xw + 1], 0x5432);
+                            w = __byte_perm(row[xw], row[xw + 1], 0x5432);
+                        scr[k * 32 + lane] = w;  // this lane's column of the warp's scratch
                     }
                 }
-                if constexpr (kEarlyRelease) {
-                    // the warp's words are in registers (still packed): the stage goes back to the
-                    // producer before the collision and the stores
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&empty[s]);
-                }
+                // the warp's words are in its scratch: the stage goes back to the producer before the
+                // collision and the stores
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
                 if (!active) return;
                 float2 v[kSlots];
 #pragma unroll
-                for (int k = 0; k < kSlots; ++k) v[k] = make_float2(P::lo(u[k]), P::hi(u[k]));
+                for (int k = 0; k < kSlots; ++k) {
+                    const uint32_t w = scr[k * 32 + lane];
+                    v[k] = make_float2(P::lo(w), P::hi(w));
+                }
                 float2 f[9], gx[5], gy[5];
 #pragma unroll
                 for (int a = 0; a < 9; ++a) f[a] = v[a];
@@ -272,10 +282,6 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
                 body(std::true_type{});
             else
                 body(std::false_type{});
-        }
-        if constexpr (!kEarlyRelease) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
         }
     }
 }
@@ -496,10 +502,10 @@ __global__ void wait_timeout_probe_kernel(int* err, uint64_t limit_ns) {
 }
 
 template <typename K>
-cudaError_t prepare_kernel(K kernel, int* blocks) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+cudaError_t prepare_kernel(K kernel, int* blocks, size_t smem = kSmem) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, kSmem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem);
     if (e == cudaSuccess && occ < 1) e = cudaErrorInvalidConfiguration;
     *blocks = occ;
     return e;
@@ -517,10 +523,10 @@ cudaError_t prepare_typed(int inplace, int* blocks) {
         if (e == cudaSuccess) e = prepare_kernel(step_kernel_aa_staged<S, 0, 1>, &b[2]);
         if (e == cudaSuccess) e = prepare_kernel(step_kernel_aa_staged<S, 1, 1>, &b[3]);
     } else {
-        e = prepare_kernel(step_kernel_staged<S, 0, 0>, &b[0]);
-        if (e == cudaSuccess) e = prepare_kernel(step_kernel_staged<S, 1, 0>, &b[1]);
-        if (e == cudaSuccess) e = prepare_kernel(step_kernel_staged<S, 0, 1>, &b[2]);
-        if (e == cudaSuccess) e = prepare_kernel(step_kernel_staged<S, 1, 1>, &b[3]);
+        e = prepare_kernel(step_kernel_staged<S, 0, 0>, &b[0], kSmemTB);
+        if (e == cudaSuccess) e = prepare_kernel(step_kernel_staged<S, 1, 0>, &b[1], kSmemTB);
+        if (e == cudaSuccess) e = prepare_kernel(step_kernel_staged<S, 0, 1>, &b[2], kSmemTB);
+        if (e == cudaSuccess) e = prepare_kernel(step_kernel_staged<S, 1, 1>, &b[3], kSmemTB);
     }
     *blocks = std::min(std::min(b[0], b[1]), std::min(b[2], b[3]));
     return e;
@@ -552,11 +558,11 @@ void launch_typed_staged(const void* fin, const void* gin, void* fout, void* gou
     S* fo = (S*)fout;
     S* go = (S*)gout;
     if (p.coupling == 0) {
-        if (closure == 0) step_kernel_staged<S, 0, 0><<<grid, kThreads, kSmem, st>>>(fi, gi, fo, go, p, ss.err);
-        else step_kernel_staged<S, 1, 0><<<grid, kThreads, kSmem, st>>>(fi, gi, fo, go, p, ss.err);
+        if (closure == 0) step_kernel_staged<S, 0, 0><<<grid, kThreads, kSmemTB, st>>>(fi, gi, fo, go, p, ss.err);
+        else step_kernel_staged<S, 1, 0><<<grid, kThreads, kSmemTB, st>>>(fi, gi, fo, go, p, ss.err);
     } else {
-        if (closure == 0) step_kernel_staged<S, 0, 1><<<grid, kThreads, kSmem, st>>>(fi, gi, fo, go, p, ss.err);
-        else step_kernel_staged<S, 1, 1><<<grid, kThreads, kSmem, st>>>(fi, gi, fo, go, p, ss.err);
+        if (closure == 0) step_kernel_staged<S, 0, 1><<<grid, kThreads, kSmemTB, st>>>(fi, gi, fo, go, p, ss.err);
+        else step_kernel_staged<S, 1, 1><<<grid, kThreads, kSmemTB, st>>>(fi, gi, fo, go, p, ss.err);
     }
 }
 
