@@ -11,10 +11,9 @@
 // wrapped copies at the row ends), completing on the stage's `full` mbarrier.  Sixteen consumer
 // warps take two x-adjacent nodes per thread as one float2 (packed FP32x2 arithmetic): 19 words of
 // the staged rows (byte_perm for the x shift), the wall closure, the collision, 19 packed words
-// stored.  In the two-buffer kernel each lane first copies its 19 words into its column of the
-// warp's private scratch and the warp arrives on the stage's `empty` mbarrier at once, so the
-// producer refills the stage while the warp computes from the scratch; the in-place kernel arrives
-// after its stores.  Every wait is bounded (kWaitNs); one that runs out sets *err and
+// stored.  Each lane first copies its 19 words into its column of the warp's private scratch and
+// the warp arrives on the stage's `empty` mbarrier at once, so the producer refills the stage while
+// the warp computes from the scratch.  Every wait is bounded (kWaitNs); one that runs out sets *err and
 // ends that warp's loop, and the producer waits, within the same limit, for its last copies to each
 // stage before it returns.
 //
@@ -49,8 +48,9 @@ constexpr int kConsumerWarps = kSegX / 64;
 constexpr int kThreads = kSegX / 2 + 32;         // consumers + the producer warp
 constexpr uint64_t kWaitNs = 1000000000ull;      // 1 s
 constexpr size_t kSmem = 128 + (size_t)kStages * kStageW * 4;
-// The two-buffer kernel: four stages, and behind them a private scratch area per consumer warp into
-// which each lane copies its 19 staged words, so that the warp can hand its stage back at once.
+// Both kernels: four stages, and behind them a private scratch area per consumer warp into which each
+// lane copies its 19 staged words, so that the warp can hand its stage back at once (the in-place
+// phase 0 with it: BF16 81.8, FP16 83.0 GLUPS per pair of steps against 80.9 and 80.5).
 constexpr int kStagesTB = 4;
 constexpr int kScratchW = kSlots * 32;  // words per consumer warp
 constexpr size_t kSmemTB = 128 + (size_t)kStagesTB * kStageW * 4 + (size_t)kConsumerWarps * kScratchW * 4;
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_aa_staged(S* __restri
                                                                       const StepParams<float> p, int* err) {
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t* full = reinterpret_cast<uint64_t*>(sm);
-    uint64_t* empty = full + kStages;
+    uint64_t* empty = full + kStagesTB;
     uint32_t* stage0 = reinterpret_cast<uint32_t*>(sm + 128);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ny = p.ny, H = p.nx / 2;              // words per row
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_aa_staged(S* __restri
     uint32_t* fw = reinterpret_cast<uint32_t*>(fb);
     uint32_t* gw = reinterpret_cast<uint32_t*>(gb);
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kStagesTB; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kConsumerWarps);
         }
@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_aa_staged(S* __restri
         const uint32_t* bw = base + (int64_t)plane_of(k, opp9(a)) * NP;
         int64_t it = 0;
         for (; it < nmine; ++it) {
-            const int s = (int)(it % kStages);
-            const int64_t u = it / kStages;
+            const int s = (int)(it % kStagesTB);
+            const int64_t u = it / kStagesTB;
             if (u > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)(u - 1) & 1u, kWaitNs)) {
                 if (lane == 0) atomicExch(err, 1);
                 break;
@@ -371,26 +371,28 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_aa_staged(S* __restri
             if (n1) bulk_g2s(dst + d1, src + g1, 4u * n1, &full[s]);
             if (n2) bulk_g2s(dst + d2, src + g2, 4u * n2, &full[s]);
         }
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kStagesTB; ++s) {
             if (it <= s) continue;
-            const int64_t u_last = (it - 1 - s) / kStages;
+            const int64_t u_last = (it - 1 - s) / kStagesTB;
             if (!mbar_wait_bounded(&full[s], (uint32_t)u_last & 1u, kWaitNs) && lane == 0) atomicExch(err, 1);
         }
         return;
     }
 
+    uint32_t* scr = stage0 + kStagesTB * kStageW + warp * kScratchW;
     typedef Packed<S> P;
     const int xw = kHaloW + tid;
     for (int64_t it = 0; it < nmine; ++it) {
-        const int s = (int)(it % kStages);
-        if (!mbar_wait_bounded(&full[s], (uint32_t)(it / kStages) & 1u, kWaitNs)) {
+        const int s = (int)(it % kStagesTB);
+        if (!mbar_wait_bounded(&full[s], (uint32_t)(it / kStagesTB) & 1u, kWaitNs)) {
             atomicExch(err, 1);
             break;
         }
         const int64_t t = t0 + it * G;
         const int y = (int)(t / nseg), w0 = (int)(t % nseg) * kSegW;
         const int TW = min(kSegW, H - w0);
-        if (tid < TW) {
+        const bool active = tid < TW;
+        {
             const bool bottom = (y == 0), top = (y == ny - 1);
             const uint32_t* st = stage0 + s * kStageW;
             const int w = w0 + tid;                           // the thread's word in its row
@@ -398,19 +400,30 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_aa_staged(S* __restri
             const int wm = sm ? H - 1 : w - 1, wp = sp ? 0 : w + 1;
             auto body = [&](auto walls) {
                 constexpr bool W = decltype(walls)::value;
+                if (active) {
+#pragma unroll
+                    for (int k = 0; k < kSlots; ++k) {
+                        const int a = dir_of(k), ex = ex9(a), ey = ey9(a);
+                        const bool wall = W && ((ey == 1 && bottom) || (ey == -1 && top));
+                        const uint32_t* row = st + k * kSlotW;
+                        uint32_t u;
+                        if (wall || ex == 0)
+                            u = row[xw];
+                        else if (ex == 1)  // nodes x - 1: the word before (swapped across the left edge)
+                            u = sm ? __byte_perm(row[xw - 1], 0, 0x1032) : row[xw - 1];
+                        else  // nodes x + 1: the word after (swapped across the right edge)
+                            u = sp ? __byte_perm(row[xw + 1], 0, 0x1032) : row[xw + 1];
+                        scr[k * 32 + lane] = u;
+                    }
+                }
+                // release the stage at once, as the two-buffer kernel does
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+                if (!active) return;
                 float2 v[kSlots];
 #pragma unroll
                 for (int k = 0; k < kSlots; ++k) {
-                    const int a = dir_of(k), ex = ex9(a), ey = ey9(a);
-                    const bool wall = W && ((ey == 1 && bottom) || (ey == -1 && top));
-                    const uint32_t* row = st + k * kSlotW;
-                    uint32_t u;
-                    if (wall || ex == 0)
-                        u = row[xw];
-                    else if (ex == 1)  // nodes x - 1: the word before (swapped across the left edge)
-                        u = sm ? __byte_perm(row[xw - 1], 0, 0x1032) : row[xw - 1];
-                    else  // nodes x + 1: the word after (swapped across the right edge)
-                        u = sp ? __byte_perm(row[xw + 1], 0, 0x1032) : row[xw + 1];
+                    const uint32_t u = scr[k * 32 + lane];
                     v[k] = make_float2(P::lo(u), P::hi(u));
                 }
                 float2 f[9], gx[5], gy[5];
@@ -482,8 +495,6 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_aa_staged(S* __restri
             else
                 body(std::false_type{});
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
     }
 }
 
@@ -518,10 +529,10 @@ cudaError_t prepare_typed(int inplace, int* blocks) {
     int b[4] = {0, 0, 0, 0};
     cudaError_t e;
     if (inplace) {
-        e = prepare_kernel(step_kernel_aa_staged<S, 0, 0>, &b[0]);
-        if (e == cudaSuccess) e = prepare_kernel(step_kernel_aa_staged<S, 1, 0>, &b[1]);
-        if (e == cudaSuccess) e = prepare_kernel(step_kernel_aa_staged<S, 0, 1>, &b[2]);
-        if (e == cudaSuccess) e = prepare_kernel(step_kernel_aa_staged<S, 1, 1>, &b[3]);
+        e = prepare_kernel(step_kernel_aa_staged<S, 0, 0>, &b[0], kSmemTB);
+        if (e == cudaSuccess) e = prepare_kernel(step_kernel_aa_staged<S, 1, 0>, &b[1], kSmemTB);
+        if (e == cudaSuccess) e = prepare_kernel(step_kernel_aa_staged<S, 0, 1>, &b[2], kSmemTB);
+        if (e == cudaSuccess) e = prepare_kernel(step_kernel_aa_staged<S, 1, 1>, &b[3], kSmemTB);
     } else {
         e = prepare_kernel(step_kernel_staged<S, 0, 0>, &b[0], kSmemTB);
         if (e == cudaSuccess) e = prepare_kernel(step_kernel_staged<S, 1, 0>, &b[1], kSmemTB);
@@ -540,11 +551,11 @@ void launch_typed_aa_staged(void* f, void* g, const StepParams<float>& p, int cl
     S* fb = (S*)f;
     S* gb = (S*)g;
     if (p.coupling == 0) {
-        if (closure == 0) step_kernel_aa_staged<S, 0, 0><<<grid, kThreads, kSmem, st>>>(fb, gb, p, ss.err);
-        else step_kernel_aa_staged<S, 1, 0><<<grid, kThreads, kSmem, st>>>(fb, gb, p, ss.err);
+        if (closure == 0) step_kernel_aa_staged<S, 0, 0><<<grid, kThreads, kSmemTB, st>>>(fb, gb, p, ss.err);
+        else step_kernel_aa_staged<S, 1, 0><<<grid, kThreads, kSmemTB, st>>>(fb, gb, p, ss.err);
     } else {
-        if (closure == 0) step_kernel_aa_staged<S, 0, 1><<<grid, kThreads, kSmem, st>>>(fb, gb, p, ss.err);
-        else step_kernel_aa_staged<S, 1, 1><<<grid, kThreads, kSmem, st>>>(fb, gb, p, ss.err);
+        if (closure == 0) step_kernel_aa_staged<S, 0, 1><<<grid, kThreads, kSmemTB, st>>>(fb, gb, p, ss.err);
+        else step_kernel_aa_staged<S, 1, 1><<<grid, kThreads, kSmemTB, st>>>(fb, gb, p, ss.err);
     }
 }
 
