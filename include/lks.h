@@ -71,7 +71,10 @@ typedef enum {
     LKS_EUNSTABLE = 4,       /* the state became non-finite */
     LKS_ETIMEOUT = 5,        /* a bounded device wait gave up */
     LKS_ENOTCONVERGED = 6,   /* max_steps reached before the residual tolerance */
-    LKS_EBUSY = 7            /* no free slot / memory budget (batched and served solves) */
+    LKS_EBUSY = 7,           /* no free slot / memory budget (batched and served solves) */
+    LKS_ESTALLED = 8         /* lks_run_to_steady: the state stopped changing or the residual
+                                stopped decreasing at the storage's rounding floor before reaching
+                                the tolerance (see lks_run_to_steady) */
 } lks_status;
 
 typedef enum { LKS_LINK = 0, LKS_MOMENT = 1 } lks_closure;
@@ -89,7 +92,10 @@ typedef enum { LKS_LINK = 0, LKS_MOMENT = 1 } lks_closure;
  *                  non-equilibrium part of the post-collision g). */
 typedef enum { LKS_MAXWELL = 0, LKS_LORENTZ = 1 } lks_coupling;
 
-/* Storage type of the populations; arithmetic is FP64 for LKS_F64 and FP32 otherwise. */
+/* Storage type of the populations; arithmetic is FP64 for LKS_F64 and FP32 otherwise.  Every type
+ * stores deviations from the rest equilibrium; LKS_F16_DEV stores each deviation times 2^14 (an exact
+ * power-of-two scale that keeps deviations down to 3.7e-9 in FP16's normal range; deviations of
+ * magnitude 4 or more overflow, which the residual reports as LKS_EUNSTABLE).  BF16 is unscaled. */
 typedef enum { LKS_F64 = 0, LKS_F32 = 1, LKS_BF16_DEV = 2, LKS_F16_DEV = 3 } lks_storage;
 
 typedef struct lks_params {
@@ -176,14 +182,26 @@ lks_status lks_moments_device(lks_handle* h, int what, double* dev_out);
  * nodes, FP64, fixed reduction order, where ' is the snapshot taken by the
  * previous lks_residual call (or at creation); the snapshot is then replaced.
  * A term whose denominator is <= 1e-30 is reported as 0.  Returns
- * LKS_EUNSTABLE if any moment is non-finite.  Synchronises the stream. */
+ * LKS_EUNSTABLE if any moment is non-finite.  Synchronises the stream.
+ * A value of exactly 0 on a channel driven by a body force or a moving wall
+ * with FP32 or 16-bit storage means that u_x and B_x did not change by one bit
+ * since the snapshot: the state stagnated (its per-step increments fell below
+ * the resolution of the stored deviations), which is not convergence;
+ * lks_run_to_steady reports it as LKS_ESTALLED. */
 lks_status lks_residual(lks_handle* h, double* r_u, double* r_b);
 
 /* Repeat { lks_step(h, check_every); lks_residual } until max(r_u, r_b) < tol
  * or max_steps steps have been taken.  *steps_out (nullable) gets the steps
  * taken by this call and *r_out (nullable) the last residual.  Returns
- * LKS_ENOTCONVERGED at max_steps.  For an in-place handle check_every and
- * max_steps must be even (LKS_EINVAL).  Synchronises. */
+ * LKS_ENOTCONVERGED at max_steps, and LKS_ESTALLED (the state is left as it
+ * is) when
+ *   - the residual is exactly 0 on a driven channel (body force or moving
+ *     wall) with FP32 or 16-bit storage: the state stopped changing; or
+ *   - the residual has not reached a new minimum for 1000 checks in a row
+ *     while its best value is below the storage's rounding floor (1e-12 FP64,
+ *     1e-4 FP32, 1e-2 16-bit): it jitters at that floor above tol.
+ * For an in-place handle check_every and max_steps must be even (LKS_EINVAL).
+ * Synchronises. */
 lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int64_t max_steps,
                              int64_t* steps_out, double* r_out);
 
@@ -229,22 +247,27 @@ const char* lks_last_error(const lks_handle* h);
  * their own pools, latency-critical loops where cudaMalloc/cudaFree may synchronise the device,
  * plugin hosts that forbid allocation calls.)
  *   f, g      device pointers to one lattice's populations in the layout above (deviation form,
- *             storage type `storage`), nx x ny nodes; read only.
+ *             storage type `storage`, node order), nx x ny nodes; read only.
+ *   B0, Fx    the lattice's applied field and body force (needed for B_y and u_x).
+ *   coupling  lks_coupling of the state: LKS_MAXWELL, or LKS_LORENTZ, whose u_x includes the half
+ *             J x B force recovered from the stored g and so needs the state's tau_m (> 1/2,
+ *             |tau_m - 1| >= 0.05, as lks_create requires; tau_m is ignored for LKS_MAXWELL).
  *   snap      device pointer to 2*nx*ny doubles: u_x then B_x per node of the previous call; the
  *             residual compares against it and overwrites it with the current values.
  *   out       host pointer to 2 doubles: r_u, r_b as defined for lks_residual.
- *   B0, Fx    the lattice's applied field and body force (needed for B_y and u_x).
- *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream); synchronised on return.
+ *   cuda_stream  cudaStream_t to run on (NULL = legacy default stream).  The call synchronises it
+ *             before returning, so it must not be a stream under capture (LKS_EINVAL).
  * The partial sums live in a file-scope device array of 4*1216 + 8 doubles (38.9 KB) that every
  * GPU which loads the library keeps until the process exits.  Lattices above 2^30 nodes are
  * rejected with LKS_EINVAL and a message naming the limit.  The first call on each device looks
- * up the array's device address (with that device current); make that first call before any
- * stream capture.  All calls share the one array: calls that overlap on the GPU (other streams,
- * other threads) race on it and must be serialised by the caller.  Nothing from a previous call
- * needs clearing: each call writes every slot it reads.  Errors: LKS_EINVAL, LKS_ECUDA,
- * LKS_EUNSTABLE (non-finite moments); lks_last_error(NULL) gives the message. */
+ * up the array's device address (with that device current).  All calls share the one array: calls
+ * that overlap on the GPU (other streams, other threads) race on it and must be serialised by the
+ * caller.  Nothing from a previous call needs clearing: each call writes every slot it reads.
+ * Errors: LKS_EINVAL, LKS_ECUDA, LKS_EUNSTABLE (non-finite moments); lks_last_error(NULL) gives the
+ * message. */
 lks_status lks_residual_noalloc(const void* f, const void* g, int32_t storage, int32_t nx, int32_t ny, double B0,
-                                double Fx, double* snap, double* out, void* cuda_stream);
+                                double Fx, int32_t coupling, double tau_m, double* snap, double* out,
+                                void* cuda_stream);
 
 /* Static name of a status code. */
 const char* lks_status_string(lks_status s);

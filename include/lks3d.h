@@ -84,7 +84,9 @@ lks_status lks3_moments(lks3_handle* h, int what, double* host_out);
 lks_status lks3_residual(lks3_handle* h, double* r_u, double* r_b);
 
 /* Repeat { lks3_step(check_every); lks3_residual } until max(r_u, r_b) < tol or max_steps;
- * LKS_ENOTCONVERGED at max_steps.  Synchronises. */
+ * LKS_ENOTCONVERGED at max_steps; LKS_ESTALLED under the same two conditions as lks_run_to_steady
+ * (an exactly zero residual on a driven channel with FP32 or 16-bit storage, or 1000 checks without
+ * a new minimum below the storage's rounding floor).  Synchronises. */
 lks_status lks3_run_to_steady(lks3_handle* h, double tol, int64_t check_every, int64_t max_steps,
                               int64_t* steps_out, double* r_out);
 

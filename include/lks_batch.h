@@ -29,7 +29,9 @@
  * against the snapshot of the previous check (a term with a denominator below 1e-30 counts 0).
  * An instance is CONVERGED when r < tol, STALLED when r is below the storage type's rounding floor
  * (1e-12 FP64, 1e-4 FP32, 1e-2 16-bit) and has not reached a new minimum for 1000 checks in a row,
- * UNSTABLE when r is not finite, MAX_STEPS at max_steps.
+ * or when r is exactly 0 on a channel driven by a body force or a moving wall with FP32 or 16-bit
+ * storage (the state stopped changing: its increments fell below the storage's resolution, which
+ * is not convergence), UNSTABLE when r is not finite, MAX_STEPS at max_steps.
  *
  * Threading: a batch handle is not thread-safe.
  */

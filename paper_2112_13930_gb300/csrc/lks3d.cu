@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __r
                         w = __byte_perm(row[xwm], row[xw], 0x5432);
                     else  // x <- x + 1, x + 1 <- x + 2 (low half of the word after)
                         w = __byte_perm(row[xw], row[xwp], 0x5432);
-                    const float2 v = make_float2(P::lo(w), P::hi(w));
+                    const float2 v = P::pair(w);
                     return W ? wall_in3<float2, float>(p, bottom, top, k, v) : v;
                 };
                 collide3<float2, float>(p, in, [&](int k, float2 v) {
@@ -590,7 +590,7 @@ __global__ void moments3_kernel(const S* f, const S* g, int64_t N, int64_t n0, i
 // x-z averages per row y: one block per row, fixed-order block reduction.
 template <typename S>
 __global__ void profiles3_kernel(const S* f, const S* g, int nx, int ny, int nz, double B0, double Fx, double* out) {
-    __shared__ double red[7][256];
+    __shared__ double red[7 * 32];
     const int y = blockIdx.x;
     const int64_t N = (int64_t)nx * ny * nz;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -601,17 +601,9 @@ __global__ void profiles3_kernel(const S* f, const S* g, int nx, int ny, int nz,
 #pragma unroll
         for (int c = 0; c < 7; ++c) acc[c] += m[c];
     }
-#pragma unroll
-    for (int c = 0; c < 7; ++c) red[c][threadIdx.x] = acc[c];
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h)
-#pragma unroll
-            for (int c = 0; c < 7; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
-        __syncthreads();
-    }
+    lks::block_sum<7>(acc, red);
     if (threadIdx.x == 0)
-        for (int c = 0; c < 7; ++c) out[c * ny + y] = red[c][0] / ((double)nx * nz);
+        for (int c = 0; c < 7; ++c) out[c * ny + y] = acc[c] / ((double)nx * nz);
 }
 
 // Residual partial sums (du^2, u^2, db^2, b^2 of u_x, B_x against the snapshot), one per block;
@@ -619,7 +611,7 @@ __global__ void profiles3_kernel(const S* f, const S* g, int nx, int ny, int nz,
 template <typename S>
 __global__ void residual3_partial(const S* f, const S* g, int64_t N, double B0, double Fx, double* snap,
                                   double* partial) {
-    __shared__ double red[4][256];
+    __shared__ double red[4 * 32];
     double acc[4] = {0, 0, 0, 0};
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
         double m[7];
@@ -632,30 +624,18 @@ __global__ void residual3_partial(const S* f, const S* g, int64_t N, double B0, 
         snap[n] = m[1];
         snap[N + n] = m[4];
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = acc[c];
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
-        __syncthreads();
-    }
+    lks::block_sum<4>(acc, red);
     if (threadIdx.x == 0)
-        for (int c = 0; c < 4; ++c) partial[c * gridDim.x + blockIdx.x] = red[c][0];
+        for (int c = 0; c < 4; ++c) partial[c * gridDim.x + blockIdx.x] = acc[c];
 }
 
 __global__ void residual3_final(const double* partial, int nb, double* out) {
-    __shared__ double red[4][1024];
-    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = (int)threadIdx.x < nb ? partial[c * nb + threadIdx.x] : 0.0;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h)
-            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + h];
-        __syncthreads();
-    }
+    __shared__ double red[4 * 32];
+    double acc[4];
+    for (int c = 0; c < 4; ++c) acc[c] = (int)threadIdx.x < nb ? partial[c * nb + threadIdx.x] : 0.0;
+    lks::block_sum<4>(acc, red);
     if (threadIdx.x == 0)
-        for (int c = 0; c < 4; ++c) out[c] = red[c][0];
+        for (int c = 0; c < 4; ++c) out[c] = acc[c];
 }
 
 // Absolute FP64 populations <-> stored deviations, for the M nodes n0 .. n0+M-1 of the N-node
@@ -1051,7 +1031,10 @@ lks_status lks3_run_to_steady(lks3_handle* h, double tol, int64_t check_every, i
     if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
     if (check_every < 1 || max_steps < 0 || !(tol > 0.0)) return fail3(h, LKS_EINVAL, "bad run_to_steady arguments");
     int64_t taken = 0;
-    double r = INFINITY;
+    double r = INFINITY, best = INFINITY;
+    int since_best = 0;
+    bool stalled = false;
+    const bool zero_stalls = lks::zero_residual_is_stall(h->p.storage, h->p.Fx, h->u_bot, h->u_top);
     lks_status s = LKS_OK;
     while (taken < max_steps) {
         const int64_t n = (max_steps - taken < check_every) ? max_steps - taken : check_every;
@@ -1062,11 +1045,26 @@ lks_status lks3_run_to_steady(lks3_handle* h, double tol, int64_t check_every, i
         s = lks3_residual(h, &ru, &rb);
         if (s != LKS_OK) break;
         r = ru > rb ? ru : rb;
+        if (r == 0.0 && zero_stalls) {
+            stalled = true;
+            break;
+        }
         if (r < tol) break;
+        if (r < best) {
+            best = r;
+            since_best = 0;
+        } else if (++since_best >= lks::kStallChecks && best < lks::stall_floor(h->p.storage)) {
+            stalled = true;
+            break;
+        }
     }
     if (steps_out) *steps_out = taken;
     if (r_out) *r_out = r;
     if (s != LKS_OK) return s;
+    if (stalled)
+        return fail3(h, LKS_ESTALLED,
+                     r == 0.0 ? "the state stopped changing (per-step increments below the storage resolution)"
+                              : "the residual stopped decreasing at the storage's rounding floor");
     if (!(r < tol)) return fail3(h, LKS_ENOTCONVERGED, "max_steps reached before the residual tolerance");
     return LKS_OK;
 }

@@ -529,7 +529,10 @@ lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int
     if (h->p.inplace && ((check_every & 1) || (max_steps & 1)))
         return fail(h, LKS_EINVAL, "an in-place handle steps in pairs: check_every and max_steps must be even");
     int64_t taken = 0;
-    double r = INFINITY;
+    double r = INFINITY, best = INFINITY;
+    int since_best = 0;
+    bool stalled = false;
+    const bool zero_stalls = lks::zero_residual_is_stall(h->p.storage, h->p.Fx, h->u_bot, h->u_top);
     lks_status s = LKS_OK;
     while (taken < max_steps) {
         const int64_t n = (max_steps - taken < check_every) ? max_steps - taken : check_every;
@@ -540,11 +543,26 @@ lks_status lks_run_to_steady(lks_handle* h, double tol, int64_t check_every, int
         s = lks_residual(h, &ru, &rb);
         if (s != LKS_OK) break;
         r = ru > rb ? ru : rb;
+        if (r == 0.0 && zero_stalls) {
+            stalled = true;
+            break;
+        }
         if (r < tol) break;
+        if (r < best) {
+            best = r;
+            since_best = 0;
+        } else if (++since_best >= lks::kStallChecks && best < lks::stall_floor(h->p.storage)) {
+            stalled = true;
+            break;
+        }
     }
     if (steps_out) *steps_out = taken;
     if (r_out) *r_out = r;
     if (s != LKS_OK) return s;
+    if (stalled)
+        return fail(h, LKS_ESTALLED,
+                    r == 0.0 ? "the state stopped changing (per-step increments below the storage resolution)"
+                             : "the residual stopped decreasing at the storage's rounding floor");
     if (!(r < tol)) return fail(h, LKS_ENOTCONVERGED, "max_steps reached before the residual tolerance");
     return LKS_OK;
 }
@@ -636,6 +654,7 @@ const char* lks_status_string(lks_status s) {
         case LKS_ETIMEOUT: return "LKS_ETIMEOUT";
         case LKS_ENOTCONVERGED: return "LKS_ENOTCONVERGED";
         case LKS_EBUSY: return "LKS_EBUSY";
+        case LKS_ESTALLED: return "LKS_ESTALLED";
     }
     return "LKS_UNKNOWN";
 }
@@ -655,8 +674,9 @@ const char* lks_status_string(lks_status s) {
 // kNoallocMaxBlocks blocks, so any lattice up to the 2^30-node limit fits; larger ones are rejected.
 namespace {
 
-constexpr int kNoallocMaxBlocks = 1216;                // the largest value residual_blocks() returns
+constexpr int kNoallocMaxBlocks = lks::kResidualMaxBlocks;  // the largest value residual_blocks() returns
 constexpr int kNoallocScratch = 4 * kNoallocMaxBlocks + 8;
+static_assert(4 * kNoallocMaxBlocks + 4 <= kNoallocScratch, "partials and totals must fit the static scratch");
 constexpr int kNoallocMaxDevices = 64;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocScratch];
 std::mutex g_noalloc_mu;
@@ -683,10 +703,16 @@ cudaError_t noalloc_scratch(double** out) {
 }  // namespace
 
 extern "C" lks_status lks_residual_noalloc(const void* f, const void* g, int32_t storage, int32_t nx, int32_t ny,
-                                           double B0, double Fx, double* snap, double* out, void* cuda_stream) {
+                                           double B0, double Fx, int32_t coupling, double tau_m, double* snap,
+                                           double* out, void* cuda_stream) {
     if (!f || !g || !snap || !out) return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: NULL pointer argument");
     if (storage < LKS_F64 || storage > LKS_F16_DEV) return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: bad storage");
     if (nx < 1 || ny < 1) return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: nx and ny must be >= 1");
+    if (coupling != LKS_MAXWELL && coupling != LKS_LORENTZ)
+        return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: coupling must be LKS_MAXWELL or LKS_LORENTZ");
+    if (coupling == LKS_LORENTZ && !(tau_m > 0.5 && isfinite(tau_m) && fabs(tau_m - 1.0) >= 0.05))
+        return fail(nullptr, LKS_EINVAL,
+                    "lks_residual_noalloc: the Lorentz-force coupling needs tau_m > 1/2 and |tau_m - 1| >= 0.05");
     const int64_t N = (int64_t)nx * (int64_t)ny;
     if (N > ((int64_t)1 << 30))
         return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: nx*ny exceeds the maximum of 2^30 nodes");
@@ -696,11 +722,18 @@ extern "C" lks_status lks_residual_noalloc(const void* f, const void* g, int32_t
     cudaError_t e = noalloc_scratch(&scratch);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "lks_residual_noalloc: cudaGetSymbolAddress");
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    // The call ends by synchronising the stream, which a stream under capture does not allow.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lks_residual_noalloc: cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(nullptr, LKS_EINVAL, "lks_residual_noalloc: the stream is being captured (the call synchronises it)");
     // Every partial and total slot the reduction reads is written earlier in the same call, so
     // nothing left over from a previous call needs clearing.
     double* partial = scratch;
     double* totals = scratch + 4 * kNoallocMaxBlocks;
-    e = lks::launch_residual(storage, f, g, nx, ny, B0, Fx, snap, partial, totals, st);
+    e = lks::launch_residual(storage, f, g, nx, ny, B0, Fx, snap, partial, totals, st, coupling,
+                             coupling == LKS_LORENTZ ? tau_m : 1.0);
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(s, totals, sizeof(s), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -129,28 +129,10 @@ __global__ void moments_kernel(const S* f, const S* g, int64_t N, int64_t n0, in
     for (int k = 0; k < 5; ++k) out[k * M + i] = m[k];
 }
 
-// Fixed-order block sum of K values per thread (tree in shared memory).
-template <int K>
-__device__ __forceinline__ void block_sum(double v[K], double* sh) {
-    const int t = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < K; ++k) sh[k * kThreads + t] = v[k];
-    __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if (t < s) {
-#pragma unroll
-            for (int k = 0; k < K; ++k) sh[k * kThreads + t] += sh[k * kThreads + t + s];
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = sh[k * kThreads];
-}
-
 template <typename S, typename C>
 __global__ void __launch_bounds__(kThreads) profiles_kernel(const S* f, const S* g, int nx, int ny, MomentModel mm,
                                                            double* out, int ilv) {
-    __shared__ double sh[5 * kThreads];
+    __shared__ double sh[5 * 32];
     const int j = blockIdx.x;
     const int64_t N = (int64_t)nx * ny;
     double acc[5] = {0, 0, 0, 0, 0};
@@ -169,7 +151,7 @@ template <typename S, typename C>
 __global__ void __launch_bounds__(kThreads) residual_partial_kernel(const S* f, const S* g, int64_t N,
                                                                    MomentModel mm, double* snap, double* partial,
                                                                    int ilv) {
-    __shared__ double sh[4 * kThreads];
+    __shared__ double sh[4 * 32];
     double acc[4] = {0, 0, 0, 0};
     for (int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x; n < N; n += (int64_t)gridDim.x * kThreads) {
         double m[5];
@@ -189,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) residual_partial_kernel(const S* f, 
 }
 
 __global__ void __launch_bounds__(kThreads) residual_final_kernel(const double* partial, int nblk, double* out) {
-    __shared__ double sh[4 * kThreads];
+    __shared__ double sh[4 * 32];
     double acc[4] = {0, 0, 0, 0};
     for (int b = threadIdx.x; b < nblk; b += kThreads)
         for (int k = 0; k < 4; ++k) acc[k] += partial[4 * b + k];
@@ -311,7 +293,7 @@ cudaError_t launch_node_moments(int storage, const void* f, const void* g, int64
 int residual_blocks(int64_t N) {
     int64_t b = (N + 2047) / 2048;
     if (b < 1) b = 1;
-    if (b > 1216) b = 1216;  // 8 per SM on 152 SMs
+    if (b > kResidualMaxBlocks) b = kResidualMaxBlocks;
     return (int)b;
 }
 

@@ -31,11 +31,11 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kMaxGroups = 15;  // named barriers 1..15 (0 is __syncthreads)
 // An instance is declared STALLED when its residual has not reached a new minimum for kStallChecks
-// checks in a row while already below the rounding floor of the storage type (stall_below: 1e-12
-// FP64, 1e-4 FP32, 1e-2 16-bit).  A long window keeps slowly converging instances (diffusive times
-// of 1e6+ steps, residual falling by well under 1 % per check and jittering) from being stopped early.
-constexpr int kStallChecks = 1000;
-inline double stall_floor(int storage) { return storage == 0 ? 1e-12 : (storage == 1 ? 1e-4 : 1e-2); }
+// checks in a row while already below the rounding floor of the storage type (lks::stall_floor), or
+// when the residual is exactly 0 on a driven channel stored in FP32 or 16 bits
+// (lks::zero_residual_is_stall): the state stopped changing, it did not converge.
+using lks::kStallChecks;
+using lks::stall_floor;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(512) batch_kernel(InstDev* tab, const int32_t*
     __shared__ int32_t flag[16];
     const int gid = threadIdx.x / T;
     const int lt = threadIdx.x - gid * T;
-    double* rd = red + (size_t)gid * 4 * T;
+    double* rd = red + (size_t)gid * 4 * (T >> 5);  // 4 sums per warp of the group
     const int nwork = ctl->nwork;
     const int64_t quantum = ctl->quantum;
     for (;;) {
@@ -199,22 +199,30 @@ __global__ void __launch_bounds__(512) batch_kernel(InstDev* tab, const int32_t*
                     snap[n] = ux;
                     snap[N + n] = bx;
                 }
+                // fixed-order reduction: shuffle tree within each warp, then lane 0 of the group
+                // adds the T/32 warp sums in warp order
+                lks::warp_sum<4>(acc);
+                const int W = T >> 5;
+                if ((lt & 31) == 0)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) rd[k * T + lt] = acc[k];
+                    for (int k = 0; k < 4; ++k) rd[k * W + (lt >> 5)] = acc[k];
                 group_sync(gid, T);
-                for (int h = T / 2; h > 0; h >>= 1) {
-                    if (lt < h)
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) rd[k * T + lt] += rd[k * T + lt + h];
-                    group_sync(gid, T);
-                }
                 if (lt == 0) {
-                    const double ru = rd[T * 1] > 1e-60 ? sqrt(rd[0] / rd[T * 1]) : 0.0;
-                    const double rb = rd[T * 3] > 1e-60 ? sqrt(rd[T * 2] / rd[T * 3]) : 0.0;
+                    double t[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        t[k] = rd[k * W];
+                        for (int q = 1; q < W; ++q) t[k] += rd[k * W + q];
+                    }
+                    const double ru = t[1] > 1e-60 ? sqrt(t[0] / t[1]) : 0.0;
+                    const double rb = t[3] > 1e-60 ? sqrt(t[2] / t[3]) : 0.0;
                     r = ru > rb ? ru : rb;
                     int st = LKS_INST_RUNNING;
-                    if (!isfinite(r) || !isfinite(rd[T * 1]) || !isfinite(rd[T * 3])) {
+                    if (!isfinite(r) || !isfinite(t[1]) || !isfinite(t[3])) {
                         st = LKS_INST_UNSTABLE;
+                    } else if (r == 0.0 && sizeof(S) < 8 &&
+                               (I->pd.Fx != 0.0 || I->pd.bot.U != 0.0 || I->pd.top.U != 0.0)) {
+                        st = LKS_INST_STALLED;  // a driven channel that stopped changing (zero_residual_is_stall)
                     } else if (r < I->tol) {
                         st = LKS_INST_CONVERGED;
                     } else {
@@ -265,7 +273,8 @@ template <> struct CgLoader<__nv_bfloat16, float> {
 };
 template <> struct CgLoader<__half, float> {
     static __device__ __forceinline__ float ld(const __half* p) {
-        return __half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p))));
+        return __fmul_rn(__half2float(__ushort_as_half(__ldcg(reinterpret_cast<const unsigned short*>(p)))),
+                         lks::kHalfUnscale);  // FP16 storage holds deviations times kHalfScale
     }
 };
 
@@ -365,17 +374,18 @@ __global__ void __launch_bounds__(512) batch_cluster_kernel(InstDev* tab, const 
                     snap[n] = ux;
                     snap[N + n] = bx;
                 }
+                lks::warp_sum<4>(acc);
+                const int W = T >> 5;
+                if ((lt & 31) == 0)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) red[k * T + lt] = acc[k];
+                    for (int k = 0; k < 4; ++k) red[k * W + (lt >> 5)] = acc[k];
                 __syncthreads();
-                for (int h = T / 2; h > 0; h >>= 1) {
-                    if (lt < h)
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) red[k * T + lt] += red[k * T + lt + h];
-                    __syncthreads();
-                }
                 if (lt == 0)
-                    for (int k = 0; k < 4; ++k) cpart0[4 * rank + k] = red[k * T];
+                    for (int k = 0; k < 4; ++k) {
+                        double t = red[k * W];
+                        for (int q = 1; q < W; ++q) t += red[k * W + q];
+                        cpart0[4 * rank + k] = t;
+                    }
                 cl.sync();
                 if (rank == 0 && lt == 0) {
                     double t[4] = {0.0, 0.0, 0.0, 0.0};
@@ -387,6 +397,9 @@ __global__ void __launch_bounds__(512) batch_cluster_kernel(InstDev* tab, const 
                     int st = LKS_INST_RUNNING;
                     if (!isfinite(r) || !isfinite(t[1]) || !isfinite(t[3])) {
                         st = LKS_INST_UNSTABLE;
+                    } else if (r == 0.0 && sizeof(S) < 8 &&
+                               (I->pd.Fx != 0.0 || I->pd.bot.U != 0.0 || I->pd.top.U != 0.0)) {
+                        st = LKS_INST_STALLED;  // a driven channel that stopped changing (zero_residual_is_stall)
                     } else if (r < I->tol) {
                         st = LKS_INST_CONVERGED;
                     } else {
@@ -576,14 +589,14 @@ void pool_free(lks_batch* b, size_t off, size_t bytes) {
 
 int blocks_per_sm(lks_batch* b, int T, int G) {
     int nb = 0;
-    const size_t smem = (size_t)G * 4 * T * sizeof(double);
+    const size_t smem = (size_t)G * 4 * (T / 32) * sizeof(double);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(b->cfg), T * G, smem);
     return nb > 0 ? nb : 1;
 }
 
 cudaError_t enqueue_launch(lks_batch* b, cudaStream_t st) {
     const int T = b->T, G = b->G, CS = b->CS;
-    const size_t smem = (size_t)G * 4 * T * sizeof(double);
+    const size_t smem = (size_t)G * 4 * (T / 32) * sizeof(double);
     cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     if (CS == 1) {
@@ -623,7 +636,7 @@ cudaError_t ensure_graph(lks_batch* b) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
-    const size_t smem = (size_t)b->G * 4 * b->T * sizeof(double);
+    const size_t smem = (size_t)b->G * 4 * (b->T / 32) * sizeof(double);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel_for(b->cfg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

@@ -46,6 +46,17 @@ struct StepParams {
     WallCoef<C> bot, top;
 };
 
+// FP16 storage holds each deviation times kHalfScale = 2^14.  The deviations of these flows span
+// roughly 1e-9 .. 1e-1 (the induced field of a weakly perturbed channel sits at W B_x ~ 1e-7);
+// unscaled, everything below 2^-14 = 6.1e-5 would fall into FP16's subnormals and lose its relative
+// precision.  Scaled, values down to 2^-28 = 3.7e-9 keep the full 11-bit significand, and because the
+// scale is a power of two the multiplications are exact: the only rounding is the store's, as before.
+// |deviation| >= 4 overflows to inf, which the residual reports as non-finite (the populations of a
+// stable run deviate from the rest state by well under 1).  BF16 keeps FP32's exponent range and is
+// stored unscaled.
+constexpr float kHalfScale = 16384.0f;
+constexpr float kHalfUnscale = 1.0f / 16384.0f;
+
 // Storage conversions (round to nearest even on the way down).  RO = true loads through the
 // read-only (non-coherent) path, valid only when the buffer is not written during the kernel;
 // RO = false is a plain coherent load for kernels that write and re-read buffers across steps.
@@ -60,7 +71,9 @@ template <bool RO> struct Loader<__nv_bfloat16, float, RO> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(RO ? __ldg(p) : *p); }
 };
 template <bool RO> struct Loader<__half, float, RO> {
-    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(RO ? __ldg(p) : *p); }
+    static __device__ __forceinline__ float ld(const __half* p) {
+        return __fmul_rn(__half2float(RO ? __ldg(p) : *p), kHalfUnscale);
+    }
 };
 template <typename S, typename C> __device__ __forceinline__ C load_s(const S* p) { return Loader<S, C, true>::ld(p); }
 
@@ -70,7 +83,9 @@ template <> __device__ __forceinline__ void store_s<float, float>(float* p, floa
 template <> __device__ __forceinline__ void store_s<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
     *p = __float2bfloat16_rn(v);
 }
-template <> __device__ __forceinline__ void store_s<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
+template <> __device__ __forceinline__ void store_s<__half, float>(__half* p, float v) {
+    *p = __float2half_rn(__fmul_rn(v, kHalfScale));
+}
 
 // Pinned floating-point operations.  Every product in the collision and the closures is written
 // as an explicit fused multiply-add (ffma) or a separately rounded multiply (fmul); no plain '*'
@@ -435,6 +450,41 @@ template <typename S, typename C, int CLOSURE, bool RO, int COUPLING = 0>
 __device__ __forceinline__ void step_node(const S* fin, const S* gin, S* fout, S* gout, const StepParams<C>& p,
                                           int64_t n, int i, int j) {
     step_node_with<S, C, CLOSURE, Loader<S, C, RO>, COUPLING>(fin, gin, fout, gout, p, n, i, j);
+}
+
+// Fixed-order sum of K FP64 values over the 32 lanes of a warp: a shuffle tree with offsets 16, 8,
+// 4, 2, 1, after which lane 0 holds the totals.  Every call combines the lanes in the same order, so
+// the sums are bitwise reproducible.  All 32 lanes must take part.
+template <int K>
+__device__ __forceinline__ void warp_sum(double v[K]) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+}
+
+// Fixed-order sum of K values per thread over a block of up to 1024 threads (a multiple of 32):
+// each warp sums its lanes with warp_sum, lane 0 of every warp parks the warp's K sums in
+// sh[k * 32 + warp], and thread 0 adds the warps' sums in warp order.  The totals end up in
+// thread 0's v (the other threads' v hold partial sums).  sh holds 32 K doubles.  The order depends
+// only on the thread index, so the result is bitwise reproducible.
+template <int K>
+__device__ __forceinline__ void block_sum(double v[K], double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_sum<K>(v);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[k * 32 + warp] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = sh[k * 32];
+            for (int w = 1; w < nw; ++w) t += sh[k * 32 + w];
+            v[k] = t;
+        }
+    }
 }
 
 // Walks a thread's nodes n = first, first + stride, ... of an nx-wide lattice keeping (i, j) up

@@ -109,8 +109,26 @@ cudaError_t launch_node_moments(int storage, const void* f, const void* g, int64
 
 // Residual partial sums: nblk blocks write partial[4*blk + k] = (sum du^2, sum u^2, sum db^2, sum b^2)
 // and refresh the snapshot snap[0..N) = u_x, snap[N..2N) = B_x; then one block reduces in fixed order
-// into out[0..4).
+// into out[0..4).  residual_blocks(N) never exceeds kResidualMaxBlocks (8 blocks per SM on 152 SMs).
+constexpr int kResidualMaxBlocks = 1216;
 int residual_blocks(int64_t N);
+
+// Steady-state bookkeeping shared by lks_run_to_steady, lks3_run_to_steady and the batch engine.
+// A run is STALLED when its residual has not reached a new minimum for kStallChecks checks in a row
+// while already below the rounding floor of the storage type (1e-12 FP64, 1e-4 FP32, 1e-2 16-bit);
+// the long window keeps slowly converging runs (residual falling by well under 1 % per check and
+// jittering) from being stopped early.
+constexpr int kStallChecks = 1000;
+inline double stall_floor(int storage) { return storage == 0 ? 1e-12 : (storage == 1 ? 1e-4 : 1e-2); }
+// A residual of exactly 0 means that u_x and B_x did not change by one bit over a whole check
+// interval.  On a channel driven by a body force or a moving wall, with FP32 or 16-bit storage, that
+// is the state stagnating because the per-step increments fell below the resolution of the stored
+// deviations -- not convergence: the profile can be far from the steady solution.  It is reported as
+// a stall.  (FP64's resolution is far below any tolerance a caller can ask for, and an undriven
+// channel has no increment to lose.)
+inline bool zero_residual_is_stall(int storage, double Fx, double u_bot, double u_top) {
+    return storage != 0 && (Fx != 0.0 || u_bot != 0.0 || u_top != 0.0);
+}
 cudaError_t launch_residual(int storage, const void* f, const void* g, int nx, int ny, double B0, double Fx,
                             double* snap, double* partial, double* out, cudaStream_t st, int coupling = 0,
                             double tau_m = 1.0, int ilv = 0);

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
 #pragma unroll
                 for (int k = 0; k < kSlots; ++k) {
                     const uint32_t w = scr[k * 32 + lane];
-                    v[k] = make_float2(P::lo(w), P::hi(w));
+                    v[k] = P::pair(w);
                 }
                 float2 f[9], gx[5], gy[5];
 #pragma unroll
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_aa_staged(S* __restri
 #pragma unroll
                 for (int k = 0; k < kSlots; ++k) {
                     const uint32_t u = scr[k * 32 + lane];
-                    v[k] = make_float2(P::lo(u), P::hi(u));
+                    v[k] = P::pair(u);
                 }
                 float2 f[9], gx[5], gy[5];
 #pragma unroll

@@ -14,7 +14,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblks.so")
 
-LKS_OK, LKS_EINVAL, LKS_ENOMEM, LKS_ECUDA, LKS_EUNSTABLE, LKS_ETIMEOUT, LKS_ENOTCONVERGED, LKS_EBUSY = range(8)
+(LKS_OK, LKS_EINVAL, LKS_ENOMEM, LKS_ECUDA, LKS_EUNSTABLE, LKS_ETIMEOUT, LKS_ENOTCONVERGED, LKS_EBUSY,
+ LKS_ESTALLED) = range(9)
 LINK, MOMENT = 0, 1
 F64, F32, BF16_DEV, F16_DEV = 0, 1, 2, 3
 MOMENTS_NODES, MOMENTS_PROFILES = 0, 1
@@ -25,6 +26,8 @@ COUPLINGS = {"maxwell": MAXWELL, "lorentz": LORENTZ, MAXWELL: MAXWELL, LORENTZ: 
 STORAGES = {"f64": F64, "f32": F32, "bf16": BF16_DEV, "f16": F16_DEV,
             F64: F64, F32: F32, BF16_DEV: BF16_DEV, F16_DEV: F16_DEV}
 STORAGE_BYTES = {F64: 8, F32: 4, BF16_DEV: 2, F16_DEV: 2}
+# FP16 deviation storage holds each deviation times this power of two (include/lks.h, lks_storage)
+F16_SCALE = 2.0 ** 14
 
 # Every entry point declared in include/lks.h, with (restype, argtypes).
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -73,8 +76,8 @@ SIGNATURES = {
     "lks_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "lks_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lks_residual_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-                                            ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
-                                            _dp, ctypes.c_void_p]),
+                                            ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                            ctypes.c_double, ctypes.c_void_p, _dp, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -88,7 +91,7 @@ class LksError(RuntimeError):
 
 def _status_name(s):
     names = ["LKS_OK", "LKS_EINVAL", "LKS_ENOMEM", "LKS_ECUDA", "LKS_EUNSTABLE", "LKS_ETIMEOUT",
-             "LKS_ENOTCONVERGED", "LKS_EBUSY"]
+             "LKS_ENOTCONVERGED", "LKS_EBUSY", "LKS_ESTALLED"]
     return names[s] if 0 <= s < len(names) else "LKS_%d" % s
 
 

@@ -127,7 +127,7 @@ class Server:
             u, b = lat.profiles()
         finally:
             lat.close()
-        state = {_lks.LKS_OK: "converged", _lks.LKS_ENOTCONVERGED: "max_steps",
+        state = {_lks.LKS_OK: "converged", _lks.LKS_ENOTCONVERGED: "max_steps", _lks.LKS_ESTALLED: "stalled",
                  _lks.LKS_EUNSTABLE: "unstable"}.get(status, "error")
         return {"state": state, "steps": int(steps), "residual": r, "u": u, "b": b}
 
@@ -230,7 +230,7 @@ def serve_one_at_a_time(trace, storage="f64", tol=1e-9, check_every=100, max_ste
         lat.close()
         torch.cuda.synchronize()
         t_done = time.perf_counter() - t0
-        state = {_lks.LKS_OK: "converged", _lks.LKS_ENOTCONVERGED: "max_steps",
+        state = {_lks.LKS_OK: "converged", _lks.LKS_ENOTCONVERGED: "max_steps", _lks.LKS_ESTALLED: "stalled",
                  _lks.LKS_EUNSTABLE: "unstable"}.get(status, "error")
         out.append({"req": req, "t_arrival": req["t_arrival"], "t_done": t_done, "latency": t_done - req["t_arrival"],
                     "steps": int(steps), "residual": r, "status": int(status), "state": state, "u": u, "b": b})
