@@ -60,6 +60,10 @@ class Oracle3DParams(ctypes.Structure):
         ("c_top", ctypes.c_double),
         ("u_bot", ctypes.c_double),
         ("u_top", ctypes.c_double),
+        ("side", ctypes.c_int32),
+        ("pad2", ctypes.c_int32),
+        ("c_back", ctypes.c_double),
+        ("c_front", ctypes.c_double),
     ]
 
 
@@ -224,9 +228,13 @@ class Oracle3D:
     may be set directly (e.g. to a perturbed state) before stepping.
     """
 
-    def __init__(self, nx, ny, nz, tau_f, tau_m, B0, Fx=0.0, c_bot=0.0, c_top=0.0, u_bot=0.0, u_top=0.0):
+    def __init__(self, nx, ny, nz, tau_f, tau_m, B0, Fx=0.0, c_bot=0.0, c_top=0.0, u_bot=0.0, u_top=0.0,
+                 side=False, c_back=0.0, c_front=0.0):
+        """side=True closes the channel into a duct: walls at the z planes (half-way outside planes 0
+        and nz-1) with conductance ratios c_back (z = -b) and c_front (z = +b), relative to a."""
         self.p = Oracle3DParams(nx=nx, ny=ny, nz=nz, pad=0, tau_f=tau_f, tau_m=tau_m, B0=B0, Fx=Fx, c_bot=c_bot,
-                                c_top=c_top, u_bot=u_bot, u_top=u_top)
+                                c_top=c_top, u_bot=u_bot, u_top=u_top, side=int(bool(side)), pad2=0,
+                                c_back=c_back, c_front=c_front)
         self.nx, self.ny, self.nz = nx, ny, nz
         self.f = np.zeros((19, nz, ny, nx))
         self.g = np.zeros((3, 7, nz, ny, nx))
@@ -241,6 +249,10 @@ class Oracle3D:
     def y(self):
         """Wall-normal node coordinates y_j = -a + j + 1/2."""
         return -self.a + np.arange(self.ny, dtype=np.float64) + 0.5
+
+    def z(self):
+        """Side-wall-normal node coordinates z_k = -b + k + 1/2, b = nz/2 (duct)."""
+        return -0.5 * self.nz + np.arange(self.nz, dtype=np.float64) + 0.5
 
     def step(self, n=1):
         if lib().o3_run(ctypes.byref(self.p), _ptr(self.f), _ptr(self.g), int(n)) != 0:

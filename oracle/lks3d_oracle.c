@@ -24,6 +24,20 @@
  *     g_in = -g~_out + 2 W B0 (Eq. magneticfieldanditsgradientrelation1 with B_y(x_b) = B0).
  *     f takes half-way bounce-back with Ladd's moving-wall term 2 w_a rho0 e_a.U / c_s^2 (App. B.1).
  *
+ * Duct (side = 1): two more walls, the planes z = -b (below plane 0) and z = +b (above plane nz-1),
+ * b = nz/2, parallel to the applied field -- the side walls of a rectangular duct whose axis is x
+ * (flows with side layers, named by the paper as the next case for its closures, end of Sec. VII and
+ * Sec. IX).  Each cut link is closed on its own, by the rule of the wall it crosses (no corner
+ * reconstruction: D3Q7 has no diagonal links, and a D3Q19 link crossing both a y and a z wall has
+ * e_x = 0, so half-way bounce-back applies to it with no moving-wall term whichever wall closes it):
+ *   - f: half-way bounce-back (the side walls are at rest);
+ *   - B_x and B_y are tangential there: the weighted (anti-)bounce-back of Eq. linkbasedBCschemefinal
+ *     with theta_s = c_s a/(tau_m - 1/2), c_s the wall's conductance ratio relative to the same length
+ *     a as the Hartmann walls (so c_s a = sigma_w t_w/sigma, the Shercliff condition
+ *     b + c_s a db/dn = 0 of Eq. ShercliffBClocalcoordinate for the induced part b); for B_y the
+ *     anti-bounce-back half restores the applied value, g_in = r g~_out + (1 - r) W B0;
+ *   - B_z is normal to them: anti-bounce-back to B_z = 0, g_in = -g~_out.
+ *
  * State: absolute post-collision populations, f[19][nz][ny][nx], g[3][7][nz][ny][nx] (component
  * index first), node n = (z*ny + y)*nx + x.
  */
@@ -36,6 +50,8 @@ typedef struct {
     int32_t nx, ny, nz, pad;
     double tau_f, tau_m, B0, Fx;
     double c_bot, c_top, u_bot, u_top;
+    int32_t side, pad2;     /* 1: walls at the z planes (duct); 0: periodic in z */
+    double c_back, c_front; /* conductance ratios of the walls z = -b and z = +b (relative to a) */
 } o3_params;
 
 /* D3Q19: rest, 6 faces, 12 edges; opposite of a >= 1 is a + 1 (a odd) or a - 1 (a even). */
@@ -105,9 +121,11 @@ int o3_init(const o3_params* p, double* f, double* g) {
 int o3_step(const o3_params* p, const double* fi, const double* gi, double* fo, double* go) {
     const int nx = p->nx, ny = p->ny, nz = p->nz;
     const int64_t N = (int64_t)nx * ny * nz;
-    double rb, kb, rt, kt;
+    double rb, kb, rt, kt, rk, kk, rf, kf;
     link_coef(p, p->c_bot, &rb, &kb);
     link_coef(p, p->c_top, &rt, &kt);
+    link_coef(p, p->c_back, &rk, &kk);
+    link_coef(p, p->c_front, &rf, &kf);
     const double om_f = 1.0 / p->tau_f, om_m = 1.0 / p->tau_m;
 #pragma omp parallel for collapse(2) schedule(static) if (N >= 16384)
     for (int z = 0; z < nz; ++z) {
@@ -116,22 +134,36 @@ int o3_step(const o3_params* p, const double* fi, const double* gi, double* fo, 
                 const int64_t n = ((int64_t)z * ny + y) * nx + x;
                 double fp[19], gp[3][7];
                 for (int a = 0; a < 19; ++a) {
-                    const int sy = y - E19[a][1];
-                    if (sy >= 0 && sy < ny) {
-                        const int sx = (x - E19[a][0] + nx) % nx, sz = (z - E19[a][2] + nz) % nz;
+                    const int sy = y - E19[a][1], szr = z - E19[a][2];
+                    const int cut_z = p->side && (szr < 0 || szr >= nz);
+                    if (sy >= 0 && sy < ny && !cut_z) {
+                        const int sx = (x - E19[a][0] + nx) % nx, sz = (szr + nz) % nz;
                         fp[a] = fi[a * N + ((int64_t)sz * ny + sy) * nx + sx];
-                    } else {
+                    } else if (sy < 0 || sy >= ny) {
                         /* the link crosses a wall: half-way bounce-back of the node's own outgoing
                          * population, with the moving-wall term (App. B.1) */
                         const double U = sy < 0 ? p->u_bot : p->u_top;
                         fp[a] = fi[opp(a) * N + n] + 6.0 * w19(a) * E19[a][0] * U;
+                    } else {
+                        fp[a] = fi[opp(a) * N + n]; /* side wall at rest: half-way bounce-back */
                     }
                 }
                 for (int i = 0; i < 3; ++i) {
                     for (int a = 0; a < 7; ++a) {
-                        const int sy = y - E7[a][1];
-                        if (sy >= 0 && sy < ny) {
-                            const int sx = (x - E7[a][0] + nx) % nx, sz = (z - E7[a][2] + nz) % nz;
+                        const int sy = y - E7[a][1], szr = z - E7[a][2];
+                        const int cut_z = p->side && (szr < 0 || szr >= nz);
+                        if (cut_z) {
+                            /* side wall (parallel to B0): B_x, B_y tangential, B_z normal */
+                            const double go_out = gi[(i * 7 + opp(a)) * N + n];
+                            const double r = szr < 0 ? rk : rf;
+                            if (i == 2)
+                                gp[i][a] = -go_out;
+                            else if (i == 0)
+                                gp[i][a] = r * go_out;
+                            else
+                                gp[i][a] = r * go_out + (1.0 - r) * w7(a) * p->B0;
+                        } else if (sy >= 0 && sy < ny) {
+                            const int sx = (x - E7[a][0] + nx) % nx, sz = (szr + nz) % nz;
                             gp[i][a] = gi[(i * 7 + a) * N + ((int64_t)sz * ny + sy) * nx + sx];
                         } else {
                             const double go_out = gi[(i * 7 + opp(a)) * N + n];

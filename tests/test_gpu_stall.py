@@ -2,10 +2,11 @@
 
 The 4 x 513 body-force Hartmann channel (Ha = 30, c = 0.5, tau = 0.8, centreline speed 0.01) gains
 about 1e-9 of velocity per step from the body force, far below one unit in the last place of its
-16-bit deviations (~1e-6): after a few thousand steps the stored state is a fixed point of the
-rounded update, u_x and B_x no longer change by a single bit, and the steady-state residual is
-exactly 0 while the profiles are still far from the steady solution.  lks_run_to_steady must return
-LKS_ESTALLED there (not LKS_OK), and the batched engine must end such an instance STALLED."""
+BF16 deviations (8-bit significand, ~1e-5 here): after a few thousand steps the stored state is a
+fixed point of the rounded update, u_x and B_x no longer change by a single bit, and the
+steady-state residual is exactly 0 while the profiles are still far from the steady solution.
+lks_run_to_steady must return LKS_ESTALLED there (not LKS_OK), and the batched engine must end such
+an instance STALLED."""
 import math
 
 import numpy as np
@@ -36,7 +37,7 @@ def _channel():
     return a, b0, fx
 
 
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("storage", ["bf16"])
 def test_single_lattice_reports_stall(mods, storage):
     lks, _ = mods
     a, b0, fx = _channel()
@@ -64,7 +65,7 @@ def test_fp32_same_channel_is_not_reported_as_stalled_early(mods):
     lat.close()
 
 
-@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("storage", ["bf16"])
 def test_batch_reports_stall(mods, storage):
     lks, batch = mods
     a, b0, fx = _channel()
