@@ -67,6 +67,22 @@ lks_status lks3_create(const lks3_params* p, lks3_handle** out);
  * the bottom (below row 0) and top (above row ny-1) walls; for steps enqueued afterwards. */
 lks_status lks3_set_walls(lks3_handle* h, double c_bottom, double c_top, double u_bottom, double u_top);
 
+/* Close the channel into a rectangular duct (enable = 1) or reopen it (enable = 0, periodic in z):
+ * two more walls, the planes z = -b (below plane 0) and z = +b (above plane nz-1), b = nz/2,
+ * parallel to the applied field -- the side walls of a duct whose axis is x, which carry the side
+ * (Shercliff) layers the paper names as the next case for its closures (end of Sec. VII, Sec. IX).
+ * They are at rest and carry the Shercliff thin-wall condition of Eq. ShercliffBClocalcoordinate for
+ * the tangential induced field, with conductance ratios c_back (z = -b) and c_front (z = +b), >= 0,
+ * INFINITY allowed, relative to the same half-width a = ny/2 as the Hartmann walls (c a = sigma_w
+ * t_w / sigma).  Each cut link is closed by the wall it crosses, with no corner reconstruction: f by
+ * half-way bounce-back; B_x and B_y, tangential there, by the weighted (anti-)bounce-back of
+ * Eq. linkbasedBCschemefinal with theta = c a/(tau_m - 1/2), B_y around its applied value B0; B_z,
+ * normal there, by anti-bounce-back to 0.  A link crossing a y wall and a z wall (D3Q19 only,
+ * e_x = 0) is closed by the y wall.  Takes effect for steps enqueued afterwards; a duct handle steps
+ * with a one-node-per-thread kernel over the flattened node index for every storage type (fully
+ * developed flow: nx = 1).  LKS_EINVAL for nz < 2 when enabling, a negative or NaN ratio. */
+lks_status lks3_set_side_walls(lks3_handle* h, int32_t enable, double c_back, double c_front);
+
 /* Enqueue n >= 0 fused steps (asynchronous). */
 lks_status lks3_step(lks3_handle* h, int64_t n);
 

@@ -217,3 +217,11 @@ def fd_on_lattice(ny_lat, nz_lat, B0, nu, eta, F, c_bot, c_top, c_back, c_front,
     iy = (2 * np.arange(ny_lat) + 1) * refine
     iz = (2 * np.arange(nz_lat) + 1) * refine
     return u[np.ix_(iy, iz)], B[np.ix_(iy, iz)]
+
+
+def fd_on_lattice_extrapolated(ny_lat, nz_lat, B0, nu, eta, F, c_bot, c_top, c_back, c_front, refine=1):
+    """Richardson extrapolation of fd_on_lattice from spacings h = 1/(2 refine) and h/2:
+    (4 fine - coarse)/3 removes the O(h^2) term of the second-order solution."""
+    uc, Bc = fd_on_lattice(ny_lat, nz_lat, B0, nu, eta, F, c_bot, c_top, c_back, c_front, refine=refine)
+    uf, Bf = fd_on_lattice(ny_lat, nz_lat, B0, nu, eta, F, c_bot, c_top, c_back, c_front, refine=2 * refine)
+    return (4.0 * uf - uc) / 3.0, (4.0 * Bf - Bc) / 3.0

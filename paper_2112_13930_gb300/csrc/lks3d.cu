@@ -80,10 +80,12 @@ struct Params3 {
     C cB[3];                   // 4.5 w (-1) 2 B0 for |e|^2 = 0, 1, 2 (Maxwell stress, e_y = +1)
     C omW0, omW1, omW1x4;      // w_m W_0, w_m W, 4 w_m W (D3Q7)
     Wall3<C> bot, top;
+    C rs_back, rs_front;       // duct: tangential-component ratios of the side walls z = -b, z = +b
 };
 
 template <typename C>
-Params3<C> make_params3(const lks3_params& p, double c_bot, double c_top, double u_bot, double u_top) {
+Params3<C> make_params3(const lks3_params& p, double c_bot, double c_top, double u_bot, double u_top,
+                        double c_back = 0.0, double c_front = 0.0) {
     Params3<C> q;
     q.nx = p.nx;
     q.ny = p.ny;
@@ -127,6 +129,10 @@ Params3<C> make_params3(const lks3_params& p, double c_bot, double c_top, double
     };
     q.bot = wall(c_bot, u_bot, +1.0);
     q.top = wall(c_top, u_top, -1.0);
+    // side walls (at rest): the same theta = c a/(tau_m - 1/2), with c relative to the Hartmann
+    // half-width a
+    q.rs_back = wall(c_back, 0.0, 0.0).r;
+    q.rs_front = wall(c_front, 0.0, 0.0).r;
     return q;
 }
 
@@ -160,6 +166,21 @@ __device__ __forceinline__ V wall_in3(const Params3<C>& p, bool bottom, bool top
         if (k == 26 + 4) return vneg(v);
         if (k == 33 + 4) return vmul(K::set(w.r), v);
     }
+    return v;
+}
+
+// Side walls of a duct (the planes z = -b below plane 0 and z = +b above plane nz-1, parallel to
+// B0; at rest).  A slot entering through one holds the node's own stored population of the
+// opposite direction.  f: half-way bounce-back (unchanged); B_x and B_y are tangential there: the
+// weighted (anti-)bounce-back with the side wall's ratio r (for B_y around its applied value B0,
+// which the deviation form absorbs: dg_in = r dg_out); B_z is normal: anti-bounce-back to 0 (-v).
+template <typename V, typename C>
+__device__ __forceinline__ V side_in3(const Params3<C>& p, bool back, int k, V v) {
+    using namespace lks;
+    typedef VecOf<V> K;
+    const C r = back ? p.rs_back : p.rs_front;
+    if (k >= 19 && k < 33) return vmul(K::set(r), v);
+    if (k >= 33) return vneg(v);
     return v;
 }
 
@@ -309,13 +330,14 @@ __device__ __forceinline__ void collide3(const Params3<C>& p, In F, Out out) {
     comp(2, bz);
 }
 
-// The fused step of one node per thread.  S: storage type, C: compute type.
-template <typename S, typename C>
-__global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
-                                                    S* __restrict__ fout, S* __restrict__ gout, const Params3<C> p) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= p.nx) return;
+// The fused step of node (x, y, z).  S: storage type, C: compute type.  SIDE: the duct's walls at the
+// z planes take the place of the periodic wrap in z.  Each cut link is closed on its own by the
+// wall it crosses (no corner reconstruction); a link through both a y and a z wall (e_x = 0, f only)
+// is closed by the y wall, whose bounce-back adds no moving-wall term when e_x = 0.
+template <typename S, typename C, bool SIDE>
+__device__ __forceinline__ void step3_node(const S* __restrict__ fin, const S* __restrict__ gin,
+                                           S* __restrict__ fout, S* __restrict__ gout, const Params3<C>& p, int x,
+                                           int y, int z) {
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int64_t N = p.N;
     const int64_t n = ((int64_t)z * ny + y) * nx + x;
@@ -326,17 +348,23 @@ __global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, c
     auto src = [&](int ex, int ey, int ez) -> int64_t {
         return ((int64_t)zs[1 - ez] * ny + (y - ey)) * nx + xs[1 - ex];
     };
+    const bool back = SIDE && z == 0, front = SIDE && z == nz - 1;
+    // does the pull along direction a cross a wall?
+    auto cut = [&](int a) {
+        const int ey = EYa(a), ez = EZa(a);
+        return (ey == 1 && bottom) || (ey == -1 && top) || (SIDE && ((ez == 1 && back) || (ez == -1 && front)));
+    };
     C v[40];
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
         const int ey = EYa(a);
-        if ((ey == 1 && bottom) || (ey == -1 && top)) continue;  // filled below
+        if (cut(a)) continue;  // filled below
         v[a] = load_s<S, C>(fin + a * N + src(EXa(a), ey, EZa(a)));
     }
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
         const int ey = EYa(a);
-        if ((ey == 1 && bottom) || (ey == -1 && top)) continue;
+        if (cut(a)) continue;
         const int64_t s = src(EXa(a), ey, EZa(a));
         v[19 + a] = load_s<S, C>(gin + a * N + s);
         v[26 + a] = load_s<S, C>(gin + (7 + a) * N + s);
@@ -359,8 +387,41 @@ __global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, c
             v[k] = wall_in3<C, C>(p, false, true, k, load_s<S, C>((k < 19 ? fin : gin) + slot_plane3(k, opp(a)) * N + n));
         }
     }
+    if (SIDE && (back || front)) {  // entering along e_z = +1 at z = 0, e_z = -1 at z = nz-1
+#pragma unroll
+        for (int k = 0; k < 40; ++k) {
+            const int a = slot_dir3(k), ey = EYa(a), ez = EZa(a);
+            if (!((ez == 1 && back) || (ez == -1 && front))) continue;
+            if ((ey == 1 && bottom) || (ey == -1 && top)) continue;  // closed by the y wall above
+            v[k] = side_in3<C, C>(p, ez == 1, k, load_s<S, C>((k < 19 ? fin : gin) + slot_plane3(k, opp(a)) * N + n));
+        }
+    }
     collide3<C, C>(p, [&](int k) -> C { return v[k]; },
                 [&](int k, C val) { store_s<S, C>((k < 19 ? fout : gout) + slot_plane3(k, slot_dir3(k)) * N + n, val); });
+}
+
+// One node per thread, x fastest (grid: x blocks, y, z).
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) step3_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
+                                                    S* __restrict__ fout, S* __restrict__ gout, const Params3<C> p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    step3_node<S, C, false>(fin, gin, fout, gout, p, x, blockIdx.y, blockIdx.z);
+}
+
+// The duct: one node per thread over the flattened node index n = (z ny + y) nx + x, so that a warp
+// covers consecutive nodes (coalesced) whatever nx is -- a fully developed duct flow has nx = 1.
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) step3_duct_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
+                                                         S* __restrict__ fout, S* __restrict__ gout,
+                                                         const Params3<C> p) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const int64_t t = n / p.nx;
+    const int x = (int)(n - t * p.nx);
+    const int z = (int)(t / p.ny);
+    const int y = (int)(t - (int64_t)z * p.ny);
+    step3_node<S, C, true>(fin, gin, fout, gout, p, x, y, z);
 }
 
 // 16-bit storage staged through shared memory by the bulk-copy engine.  A task is R whole rows
@@ -745,6 +806,8 @@ struct lks3_handle {
     double* host4 = nullptr;  // pinned
     double* state_stage = nullptr;  // 40 * min(N, 2^20) doubles for state and moment transfers, on first use
     double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
+    bool side = false;                 // duct: walls at the z planes (lks3_set_side_walls)
+    double c_back = 0.0, c_front = 0.0;
     int64_t steps = 0;
     std::string err;
 };
@@ -836,6 +899,15 @@ cudaError_t launch_step3(lks3_handle* h) {
     const lks3_params& p = h->p;
     const dim3 grid((p.nx + 255) / 256, p.ny, p.nz);
     const int src = h->cur;
+    if (h->side) {
+        const int64_t N = (int64_t)p.nx * p.ny * p.nz;
+        LKS3_DISPATCH(p.storage, {
+            const Params3<C> q = make_params3<C>(p, h->c_bot, h->c_top, h->u_bot, h->u_top, h->c_back, h->c_front);
+            step3_duct_kernel<S, C><<<(unsigned)((N + 255) / 256), 256, 0, h->stream>>>(
+                (const S*)h->f[src], (const S*)h->g[src], (S*)h->f[src ^ 1], (S*)h->g[src ^ 1], q);
+        });
+        return cudaGetLastError();
+    }
     if (h->staged) {
         if (p.storage == LKS_BF16_DEV)
             launch_staged3<__nv_bfloat16>(h, src);
@@ -931,6 +1003,17 @@ lks_status lks3_set_walls(lks3_handle* h, double c_bottom, double c_top, double 
     h->c_top = c_top;
     h->u_bot = u_bottom;
     h->u_top = u_top;
+    return LKS_OK;
+}
+
+lks_status lks3_set_side_walls(lks3_handle* h, int32_t enable, double c_back, double c_front) {
+    if (!h) return fail3(nullptr, LKS_EINVAL, "handle is NULL");
+    if (enable != 0 && enable != 1) return fail3(h, LKS_EINVAL, "enable must be 0 or 1");
+    if (!(c_back >= 0.0) || !(c_front >= 0.0)) return fail3(h, LKS_EINVAL, "side-wall conductance ratios must be >= 0");
+    if (enable && h->p.nz < 2) return fail3(h, LKS_EINVAL, "a duct needs nz >= 2");
+    h->side = enable != 0;
+    h->c_back = c_back;
+    h->c_front = c_front;
     return LKS_OK;
 }
 

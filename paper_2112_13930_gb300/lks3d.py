@@ -36,6 +36,7 @@ SIGNATURES = {
     "lks3_footprint_bytes": (ctypes.c_size_t, [_PP]),
     "lks3_create": (_status, [_PP, ctypes.POINTER(_VP)]),
     "lks3_set_walls": (_status, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "lks3_set_side_walls": (_status, [_VP, ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
     "lks3_step": (_status, [_VP, ctypes.c_int64]),
     "lks3_steps_taken": (ctypes.c_int64, [_VP]),
     "lks3_moments": (_status, [_VP, ctypes.c_int, _dp]),
@@ -123,6 +124,15 @@ class Lattice3D:
 
     def set_walls(self, c_bottom, c_top, u_bottom=0.0, u_top=0.0):
         _check(lib().lks3_set_walls(self._h, c_bottom, c_top, u_bottom, u_top), self._h)
+
+    def set_side_walls(self, c_back, c_front, enable=True):
+        """Close the channel into a duct: walls at the z planes with conductance ratios c_back
+        (z = -b) and c_front (z = +b), relative to the Hartmann half-width a."""
+        _check(lib().lks3_set_side_walls(self._h, int(bool(enable)), c_back, c_front), self._h)
+
+    def z(self):
+        """Side-wall-normal node coordinates z_k = -b + k + 1/2, b = nz/2 (duct)."""
+        return -0.5 * self.nz + np.arange(self.nz, dtype=np.float64) + 0.5
 
     def step(self, n=1):
         _check(lib().lks3_step(self._h, int(n)), self._h)

@@ -183,3 +183,17 @@ def test_duct_mutant_is_caught(tmp_path, name):
     _compile3.unmutated = _compile3(tmp_path, "none", text)
     L = _compile3(tmp_path, name, text.replace(old, new))
     assert _defect(L, name) > 1e-3
+
+
+@pytest.mark.parametrize("ha,c", [(5.0, 0.5), (8.0, math.inf)])
+def test_extrapolated_fd_matches_series(ha, c):
+    """The Richardson-extrapolated finite-difference solution on the lattice nodes of a 32^2 duct with
+    insulating side walls agrees with the series to well below the scheme's own error there (~1e-3)."""
+    n, nu, eta, F = 32, 0.1, 0.075, 1e-6
+    a = n / 2
+    B0 = ha * math.sqrt(nu * eta) / a
+    y = -a + np.arange(n) + 0.5
+    us, bs = duct.hunt_series(y[:, None], y[None, :], a, a, B0, nu, eta, F, c, nterms=2000)
+    ue, be = duct.fd_on_lattice_extrapolated(n, n, B0, nu, eta, F, c, c, 0.0, 0.0, refine=2)
+    assert np.max(np.abs(ue - us)) < 6e-5 * np.max(np.abs(us))
+    assert np.max(np.abs(be - bs)) < 6e-5 * np.max(np.abs(bs))
