@@ -565,9 +565,15 @@ def bench_precision(args):
 def bench_sweep(args):
     """Batched sweep: a seeded sample of the 4096-instance parameter-sweep set (nx = 4, ny in
     33..1025, Ha log-uniform in [1, 200], c log-uniform in [1e-3, 1e3] plus 5% each of 0 and inf,
-    half body-force/link-based, half shear/moment-based), FP32, residual tolerance 1e-10, solved by
-    persistent launches of the batched engine; the one-at-a-time FP64 baseline solves the first
-    instances of the same sample through the single-lattice API."""
+    half body-force/link-based, half shear/moment-based), residual tolerance 1e-10.
+
+    Arms: (1) the mixed-precision lane -- FP32 batch to a hand-off residual of 1e-5 (or its rounding
+    floor), then each instance continued in an FP64 batch to 1e-10 -- the headline; (2) FP32 alone
+    (stalls at its floor); (3) FP64 through the batched engine on the first instances; and, on the
+    same first --sweep-baseline instances, (4) the mixed lane run on just those and (5) one-at-a-time
+    FP64 solving through the single-lattice API, with p50/p99 time-to-steady of both arms and the
+    accuracy gates (rel. L2 <= 1e-4 against the FP64 solve on the same grid, and against the closed
+    form where the FP64 solve itself meets it)."""
     import numpy as np
     import torch
     from paper_2112_13930_gb300 import build, lks, sweep, workloads
@@ -578,71 +584,107 @@ def bench_sweep(args):
     sample = specs[: args.sweep_sample]
     cands = [(64, 8, 1), (128, 4, 1), (256, 2, 1), (512, 1, 1), (256, 1, 2), (512, 1, 2), (256, 1, 4),
              (512, 1, 4), (128, 1, 8), (256, 1, 8)]
+
+    def pct(x, q):
+        x = [v for v in x if v is not None]
+        return float(np.percentile(x, q)) if x else None
+
+    def rel(a, b):
+        return max(float(np.sqrt(np.mean((a["u"] - b["u"]) ** 2)) / max(1e-300, np.max(np.abs(b["u"])))),
+                   float(np.sqrt(np.mean((a["b"] - b["b"]) ** 2)) / max(1e-300, np.max(np.abs(b["b"])))))
+
+    def states_of(recs):
+        out = {}
+        for r in recs:
+            out[r["state"]] = out.get(r["state"], 0) + 1
+        return out
+
+    # (1) mixed lane on the whole sample
+    mix = sweep.run_mixed(sample, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=args.sweep_quantum,
+                          max_steps=args.sweep_max_steps, shape=(128, 1, 1), time_budget=args.sweep_time)
+    mrecs = mix["records"]
+    mconv = [r for r in mrecs if r["state"] == "converged"]
+    mnodes = sum(r["nodes"] * (r["steps_fp32"] + r["steps_fp64"]) for r in mrecs)
+    # (2) FP32 alone
     res = sweep.run_batched(sample, "f32", tol=1e-10, check_every=100, quantum=args.sweep_quantum,
                             max_steps=args.sweep_max_steps, tune_candidates=cands, time_budget=args.sweep_time)
     recs = res["records"]
     done = [r for r in recs if r["t_done"] is not None]
-    t_done = np.array([r["t_done"] for r in done]) if done else np.array([np.nan])
     node_updates = sum(r["nodes"] * r["steps"] for r in recs)
-    states = {}
-    for r in recs:
-        states[r["state"]] = states.get(r["state"], 0) + 1
-    resolved = [r for r in recs if r["state"] in ("converged", "stalled") and r["ny"] / 2 / r["ha"] >= 3.0]
-    gate = [max(r["l2_u"], r["l2_b"]) for r in resolved]
-    # FP64 through the batched engine on the first instances: the same answers as one-at-a-time FP64
-    # (identical per-node arithmetic), so its speedup over the baseline is like for like.
+    # (3) FP64 through the batched engine on the first instances
     nb64 = max(args.sweep_baseline, args.sweep_fp64_sample)
     res64 = sweep.run_batched(sample[:nb64], "f64", tol=1e-10, check_every=100, quantum=args.sweep_quantum,
-                              max_steps=args.sweep_max_steps, tune_candidates=cands,
-                              time_budget=args.sweep_time)
-    base = sweep.run_one_at_a_time(sample[: args.sweep_baseline], "f64", tol=1e-10, check_every=100,
-                                   max_steps=args.sweep_max_steps)
-    brecs = base["records"]
-    blat = np.array([r["t_done"] for r in brecs])
-    same = [r for r in recs[: len(brecs)]]
-    # FP32 batched result against the FP64 solve of the same instance on the same grid
-    vs64 = []
-    for r32, r64 in zip(same, brecs):
-        if r32["state"] == "unstable" or r64["status"] == 4:
-            continue
-        eu = float(np.sqrt(np.mean((r32["u"] - r64["u"]) ** 2)) / max(1e-300, np.max(np.abs(r64["u"]))))
-        eb = float(np.sqrt(np.mean((r32["b"] - r64["b"]) ** 2)) / max(1e-300, np.max(np.abs(r64["b"]))))
-        vs64.append(max(eu, eb))
+                              max_steps=args.sweep_max_steps, tune_candidates=cands, time_budget=args.sweep_time)
     r64 = res64["records"]
-    same64 = []
-    for a, c in zip(r64, brecs):
-        if a["state"] == "unstable":
+    # (4), (5) the same first K instances, both arms
+    K = args.sweep_baseline
+    mixK = sweep.run_mixed(sample[:K], handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=args.sweep_quantum,
+                           max_steps=args.sweep_max_steps, shape=(128, 1, 1))
+    base = sweep.run_one_at_a_time(sample[:K], "f64", tol=1e-10, check_every=100, max_steps=args.sweep_max_steps)
+    brecs = base["records"]
+    gate = {"instances": K, "fp64_one_at_a_time_unstable": 0, "fp64_one_at_a_time_converged": 0,
+            "mixed_vs_fp64_same_grid_le_1e-4": 0, "fp32_vs_fp64_same_grid_le_1e-4": 0,
+            "fp64_meets_analytic_le_1e-4": 0, "mixed_meets_analytic_where_fp64_does": 0,
+            "mixed_vs_fp64_same_grid_rel_l2": [], "fp32_vs_fp64_same_grid_rel_l2": [],
+            "fp64_vs_analytic_rel_l2": []}
+    for m, f32r, bb in zip(mixK["records"], recs[:K], brecs):
+        if bb["status"] == lks.LKS_EUNSTABLE:
+            gate["fp64_one_at_a_time_unstable"] += 1
+            gate["mixed_vs_fp64_same_grid_rel_l2"].append(None)
+            gate["fp32_vs_fp64_same_grid_rel_l2"].append(None)
+            gate["fp64_vs_analytic_rel_l2"].append(None)
             continue
-        same64.append(max(float(np.max(np.abs(a["u"] - c["u"])) / max(1e-300, np.max(np.abs(c["u"])))),
-                          float(np.max(np.abs(a["b"] - c["b"])) / max(1e-300, np.max(np.abs(c["b"]))))))
-    t64 = np.array([r["t_done"] for r in r64 if r["t_done"] is not None])
-    fp64_batched = {"instances": len(r64), "wall_s": round(res64["wall"], 3),
-                    "solves_per_s": round(len(t64) / res64["wall"], 4),
-                    "time_to_steady_p50_s": float(np.percentile(t64, 50)) if len(t64) else None,
-                    "time_to_steady_p99_s": float(np.percentile(t64, 99)) if len(t64) else None,
-                    "states": {k: sum(1 for r in r64 if r["state"] == k) for k in {r["state"] for r in r64}},
-                    "autotune_best": res64["tune"]["best"] if res64["tune"] else None,
-                    "max_rel_diff_vs_one_at_a_time_fp64": same64,
-                    "baseline_instances_time_s": round(max([r["t_done"] or 0 for r in r64[: len(brecs)]]), 3)}
+        gate["fp64_one_at_a_time_converged"] += int(bb["status"] == lks.LKS_OK)
+        dm = rel(m, bb) if m["state"] != "fp32_unstable" else float("inf")
+        d32 = rel(f32r, bb) if f32r["state"] != "unstable" else float("inf")
+        da = max(bb["l2_u"], bb["l2_b"])
+        gate["mixed_vs_fp64_same_grid_rel_l2"].append(dm)
+        gate["fp32_vs_fp64_same_grid_rel_l2"].append(d32)
+        gate["fp64_vs_analytic_rel_l2"].append(da)
+        gate["mixed_vs_fp64_same_grid_le_1e-4"] += int(dm <= 1e-4)
+        gate["fp32_vs_fp64_same_grid_le_1e-4"] += int(d32 <= 1e-4)
+        if da <= 1e-4:
+            gate["fp64_meets_analytic_le_1e-4"] += 1
+            gate["mixed_meets_analytic_where_fp64_does"] += int(max(m["l2_u"], m["l2_b"]) <= 1e-4)
     out = {"workload": "sweep", "metric": "sweep solves/s", "unit": "solves/s", "higher_is_better": True,
-           "sample": len(sample), "of": len(specs), "dtype": "f32",
-           "value": round(len(done) / res["wall"], 3), "wall_s": round(res["wall"], 3),
-           "time_to_steady_p50_s": float(np.percentile(t_done, 50)),
-           "time_to_steady_p99_s": float(np.percentile(t_done, 99)),
-           "states": states, "glups": round(node_updates / res["wall"] / 1e9, 2), "launches": res["launches"],
-           "autotune": res["tune"], "tail_shape_at_s": res["tail_shape_at"],
-           "fp64_batched": fp64_batched,
-           "gate_l2_le_1e-4": {"resolved_instances": len(resolved), "pass": int(sum(g <= 1e-4 for g in gate)),
-                               "median_l2": float(np.median(gate)) if gate else None},
-           "baseline_fp64_one_at_a_time": {
-               "instances": len(brecs), "solves_per_s": round(len(brecs) / base["wall"], 4),
-               "latency_p50_s": float(np.percentile(blat, 50)), "latency_p99_s": float(np.percentile(blat, 99)),
-               "steps": [r["steps"] for r in brecs], "solve_s": [round(r["solve_s"], 3) for r in brecs],
-               "batched_steps_same_instances": [r["steps"] for r in same],
-               "fp32_batched_vs_fp64_rel_l2": vs64,
-               "fp64_vs_analytic_rel_l2": [max(r["l2_u"], r["l2_b"]) for r in brecs]},
+           "sample": len(sample), "of": len(specs), "dtype": "f32->f64",
+           "value": round(len(mconv) / mix["wall"], 3),
+           "mixed_lane": {"handoff_tol": 1e-5, "tol": 1e-10, "wall_s": round(mix["wall"], 3),
+                          "converged": len(mconv), "states": states_of(mrecs),
+                          "fp32_states": states_of([{"state": r["fp32_state"]} for r in mrecs]),
+                          "time_to_steady_p50_s": pct([r["t_done"] for r in mconv], 50),
+                          "time_to_steady_p99_s": pct([r["t_done"] for r in mconv], 99),
+                          "glups": round(mnodes / mix["wall"] / 1e9, 2), "launches": mix["launches"],
+                          "steps_fp32_total": int(sum(r["steps_fp32"] for r in mrecs)),
+                          "steps_fp64_total": int(sum(r["steps_fp64"] for r in mrecs))},
+           "fp32_only": {"wall_s": round(res["wall"], 3), "solves_per_s": round(len(done) / res["wall"], 3),
+                         "time_to_steady_p50_s": pct([r["t_done"] for r in done], 50),
+                         "time_to_steady_p99_s": pct([r["t_done"] for r in done], 99),
+                         "states": states_of(recs), "glups": round(node_updates / res["wall"] / 1e9, 2),
+                         "launches": res["launches"], "autotune": res["tune"],
+                         "tail_shape_at_s": res["tail_shape_at"]},
+           "fp64_batched": {"instances": len(r64), "wall_s": round(res64["wall"], 3),
+                            "solves_per_s": round(sum(r["t_done"] is not None for r in r64) / res64["wall"], 4),
+                            "time_to_steady_p50_s": pct([r["t_done"] for r in r64], 50),
+                            "time_to_steady_p99_s": pct([r["t_done"] for r in r64], 99),
+                            "states": states_of(r64)},
+           "same_sample": {
+               "instances": K,
+               "mixed_lane": {"wall_s": round(mixK["wall"], 3), "states": states_of(mixK["records"]),
+                              "solves_per_s": round(sum(r["state"] == "converged" for r in mixK["records"])
+                                                    / mixK["wall"], 4),
+                              "time_to_steady_p50_s": pct([r["t_done"] for r in mixK["records"]], 50),
+                              "time_to_steady_p99_s": pct([r["t_done"] for r in mixK["records"]], 99)},
+               "one_at_a_time_fp64": {"wall_s": round(base["wall"], 3),
+                                      "solves_per_s": round(sum(r["status"] == lks.LKS_OK for r in brecs)
+                                                            / base["wall"], 4),
+                                      "time_to_steady_p50_s": pct([r["t_done"] for r in brecs], 50),
+                                      "time_to_steady_p99_s": pct([r["t_done"] for r in brecs], 99),
+                                      "statuses": {lks._status_name(k): sum(r["status"] == k for r in brecs)
+                                                   for k in {r["status"] for r in brecs}}},
+               "gate": gate},
            "settings": {"quantum": args.sweep_quantum, "max_steps": args.sweep_max_steps, "check_every": 100,
-                        "time_budget_s": args.sweep_time}}
+                        "time_budget_s": args.sweep_time, "mixed_shape": [128, 1, 1]}}
     print(json.dumps(out), flush=True)
     return 0
 
@@ -661,14 +703,19 @@ def bench_serve(args):
     lks.load()
     from paper_2112_13930_gb300 import sweep
 
-    def replay(rate):
+    finish = args.serve_finish_tol if args.serve_finish_tol > 0 else None
+
+    def replay(rate, n=None):
         trace = workloads.serve_trace(args.serve_requests, rate=rate, seed=5)
+        if n is not None:
+            trace = trace[:n]
         srv = serve.Server("f32", budget_bytes=120 << 30, small_pool_bytes=16 << 30, small_max_nodes=32768,
                            large_workers=args.serve_workers, tol=1e-9, check_every=100, quantum=args.serve_quantum,
-                           max_steps=args.serve_max_steps, inplace=args.serve_inplace)
+                           max_steps=args.serve_max_steps, inplace=args.serve_inplace, finish_tol=finish)
         recs = srv.serve(trace, time_limit=args.serve_time)
         srv.close()
         summ = serve.summarize(recs, len(trace))
+        summ["_records"] = recs
         errs = [max(sweep.analytic_error(r["req"], r["u"], r["b"])) for r in recs
                 if r.get("state") in serve.STEADY_STATES]
         if errs:
@@ -682,19 +729,43 @@ def bench_serve(args):
         return trace, summ
 
     trace, summ = replay(args.serve_rate)
-    base = serve.serve_one_at_a_time(trace[: args.serve_baseline], "f64", tol=1e-9, check_every=100,
+    summ.pop("_records")
+    # the same first K requests through both arms: the server alone on them, and FIFO one-at-a-time FP64
+    K = args.serve_baseline
+    _, ssum = replay(args.serve_rate, K)
+    srecs = {r["req"]["index"]: r for r in ssum.pop("_records")}
+    base = serve.serve_one_at_a_time(trace[:K], "f64", tol=1e-9, check_every=100,
                                      max_steps=args.serve_max_steps, time_limit=args.serve_time)
-    bsum = serve.summarize(base, args.serve_baseline)
+    bsum = serve.summarize(base, K)
+    gate = {"requests": K, "fp64_steady": 0, "served_vs_fp64_same_grid_le_1e-4": 0,
+            "fp64_meets_analytic_le_1e-4": 0, "served_meets_analytic_where_fp64_does": 0,
+            "served_vs_fp64_same_grid_rel_l2": []}
+    for b in base:
+        r = srecs.get(b["req"]["index"])
+        if r is None or r.get("u") is None or b["state"] not in serve.STEADY_STATES:
+            gate["served_vs_fp64_same_grid_rel_l2"].append(None)
+            continue
+        gate["fp64_steady"] += 1
+        d = max(float(np.sqrt(np.mean((r["u"] - b["u"]) ** 2)) / max(1e-300, np.max(np.abs(b["u"])))),
+                float(np.sqrt(np.mean((r["b"] - b["b"]) ** 2)) / max(1e-300, np.max(np.abs(b["b"])))))
+        gate["served_vs_fp64_same_grid_rel_l2"].append(d)
+        gate["served_vs_fp64_same_grid_le_1e-4"] += int(d <= 1e-4)
+        if max(sweep.analytic_error(b["req"], b["u"], b["b"])) <= 1e-4:
+            gate["fp64_meets_analytic_le_1e-4"] += 1
+            gate["served_meets_analytic_where_fp64_does"] += int(max(sweep.analytic_error(r["req"], r["u"], r["b"]))
+                                                                 <= 1e-4)
     out = {"workload": "serve", "metric": "served solves/s", "unit": "solves/s", "higher_is_better": True,
-           "dtype": "f32", "value": round(summ["solves_per_s"], 3), "summary": summ,
-           "offered_rate_per_s": args.serve_rate, "baseline_fp64_fifo": bsum,
+           "dtype": "f32->f64" if finish else "f32", "value": round(summ["solves_per_s"], 3), "summary": summ,
+           "offered_rate_per_s": args.serve_rate,
+           "same_sample": {"requests": K, "served": ssum, "one_at_a_time_fp64_fifo": bsum, "gate": gate},
            "settings": {"requests": args.serve_requests, "max_steps": args.serve_max_steps,
-                        "buffers": "one, in place" if args.serve_inplace else "two",
+                        "buffers": "one, in place" if args.serve_inplace else "two", "finish_tol": finish,
                         "quantum": args.serve_quantum, "large_workers": args.serve_workers,
                         "time_limit_s": args.serve_time}}
     if args.serve_underload > 0:
         # the same requests offered below capacity: latency is then solve time, not queueing
         _, under = replay(args.serve_underload * summ["solves_per_s"])
+        under.pop("_records")
         out["underload"] = under
     print(json.dumps(out), flush=True)
     return 0
@@ -759,6 +830,19 @@ def bench_validation(args):
            "convergence_orders": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in o.items()}
                                   for o in orders],
            "csv_dir": args.validation_out}
+    if args.validation_record:
+        # the record kept with the sources: per-case errors, E3 orders and the per-experiment table
+        import shutil
+        os.makedirs(args.validation_record, exist_ok=True)
+        for name in ("summary.csv", "convergence.csv"):
+            shutil.copy(os.path.join(args.validation_out, name),
+                        os.path.join(args.validation_record, "validation_" + name))
+        with open(os.path.join(args.validation_record, "validation_table.csv"), "w") as fh:
+            fh.write("exp,cases,converged,max_l2_u_or_min_order,max_l2_b_or_max_order\n")
+            for t in validation.table(rows, orders):
+                fh.write("%s,%d,%d,%.4g,%.4g\n" % (t["exp"], t["cases"], t["converged"], t["max_l2_u"],
+                                                    t["max_l2_b"]))
+        out["record_dir"] = args.validation_record
     print(json.dumps(out), flush=True)
     return 0
 
@@ -884,16 +968,20 @@ def main():
                     help="preset of the five benchmark configurations: 1 = c1, 2 = main, 3 = precision, "
                          "4 = sweep, 5 = serve")
     ap.add_argument("--validation-out", default="validation_out")
+    ap.add_argument("--validation-record", default="",
+                    help="--workload validation: also write the summary CSVs into this directory")
     ap.add_argument("--precision-steps", type=int, default=1000)
     ap.add_argument("--precision-max-steps", type=int, default=3_000_000)
     ap.add_argument("--sweep-sample", type=int, default=512)
-    ap.add_argument("--sweep-baseline", type=int, default=8)
+    ap.add_argument("--sweep-baseline", type=int, default=64)
     ap.add_argument("--sweep-fp64-sample", type=int, default=64)
     ap.add_argument("--sweep-quantum", type=int, default=20000)
     ap.add_argument("--sweep-max-steps", type=int, default=2_000_000)
     ap.add_argument("--sweep-time", type=float, default=600.0)
     ap.add_argument("--serve-requests", type=int, default=400)
-    ap.add_argument("--serve-baseline", type=int, default=20)
+    ap.add_argument("--serve-baseline", type=int, default=64)
+    ap.add_argument("--serve-finish-tol", type=float, default=1e-5,
+                    help="hand-off residual of the FP64 finish (0: FP32 only)")
     ap.add_argument("--serve-quantum", type=int, default=2000)
     ap.add_argument("--serve-max-steps", type=int, default=200_000)
     ap.add_argument("--serve-workers", type=int, default=6)

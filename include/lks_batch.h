@@ -123,6 +123,20 @@ lks_status lks_batch_result(const lks_batch* b, int32_t slot, lks_instance_resul
  * LKS_MOMENTS_PROFILES).  Synchronises. */
 lks_status lks_batch_moments(lks_batch* b, int32_t slot, int what, double* host_out);
 
+/* Copy one instance's current state out as FP64 absolute populations (deviation + rest equilibrium),
+ * host_f 9 x ny x nx and host_g 2 x 5 x ny x nx in the layout of lks.h, as lks_get_state does.  With
+ * lks_batch_set_state this moves an instance between batches of different storage types -- e.g. an
+ * FP32 solve that reached its rounding floor continued in an FP64 batch to a tolerance FP32 cannot
+ * certify.  Uses a temporary device buffer of 19 nx ny doubles.  Synchronises. */
+lks_status lks_batch_get_state(lks_batch* b, int32_t slot, double* host_f, double* host_g);
+
+/* Replace one instance's state by FP64 absolute populations (layout as lks_batch_get_state), rounded
+ * to the batch's storage type, and restart its bookkeeping: step count 0, status RUNNING, residual
+ * snapshot taken from the new state, stall history cleared.  Its descriptor (tol, check_every,
+ * max_steps, walls, force) is unchanged.  Uses a temporary device buffer of 19 nx ny doubles.
+ * Synchronises. */
+lks_status lks_batch_set_state(lks_batch* b, int32_t slot, const double* host_f, const double* host_g);
+
 /* Free a slot and its pool memory (the instance may be in any state).  Synchronises. */
 lks_status lks_batch_remove(lks_batch* b, int32_t slot);
 

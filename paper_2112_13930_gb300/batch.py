@@ -70,6 +70,8 @@ SIGNATURES = {
     "lks_batch_run": (ctypes.c_int, [_VP, ctypes.c_int64, _I32P]),
     "lks_batch_result": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(InstanceResult)]),
     "lks_batch_moments": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int, _DP]),
+    "lks_batch_get_state": (ctypes.c_int, [_VP, ctypes.c_int32, _DP, _DP]),
+    "lks_batch_set_state": (ctypes.c_int, [_VP, ctypes.c_int32, _DP, _DP]),
     "lks_batch_remove": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "lks_batch_set_shape": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "lks_batch_autotune": (ctypes.c_int, [_VP, ctypes.c_int64, _I32P, _I32P, _I32P, ctypes.c_int32, _DP, _I32P]),
@@ -169,6 +171,22 @@ class Batch:
     def profiles(self, slot):
         m = self.moments(slot, _lks.MOMENTS_PROFILES)
         return m[1], m[3]
+
+    def get_state(self, slot):
+        """FP64 absolute populations (f (9, ny, nx), g (2, 5, ny, nx)) of one instance."""
+        nx, ny = self.shapes[slot]
+        f = np.empty((9, ny, nx))
+        g = np.empty((2, 5, ny, nx))
+        self._check(lib().lks_batch_get_state(self._h, slot, f.ctypes.data_as(_DP), g.ctypes.data_as(_DP)))
+        return f, g
+
+    def set_state(self, slot, f, g):
+        """Replace one instance's state (FP64 absolute populations) and restart its bookkeeping."""
+        nx, ny = self.shapes[slot]
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        assert f.shape == (9, ny, nx) and g.shape == (2, 5, ny, nx)
+        self._check(lib().lks_batch_set_state(self._h, slot, f.ctypes.data_as(_DP), g.ctypes.data_as(_DP)))
 
     def remove(self, slot):
         self._check(lib().lks_batch_remove(self._h, slot))

@@ -21,7 +21,12 @@ using lks::WallCoef;
 namespace {
 
 thread_local std::string g_last_error = "";
-constexpr int64_t kGraphSteps = 64;  // even, so a graph returns the state to the buffer it started in
+// Captured graphs of 64, 32, ..., 2 steps (even, so a graph returns the state to the buffer it started
+// in), one per size and starting buffer, built on first use: lks_step(n) runs n as a few graph
+// launches (n = 100: 64 + 32 + 4) plus at most one direct launch, which matters for small lattices
+// whose steps cost less than a launch.
+constexpr int kGraphSizes = 6;
+constexpr int64_t kGraphSteps[kGraphSizes] = {64, 32, 16, 8, 4, 2};
 constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -197,7 +202,7 @@ struct lks_handle {
     double c_bot = 0.0, c_top = 0.0, u_bot = 0.0, u_top = 0.0;
     StepParams<double> sp;
     int64_t steps = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[kGraphSizes][2] = {};
     bool graphs_disabled = false;
     std::string err;
 };
@@ -234,11 +239,12 @@ void refresh_params(lks_handle* h) {
 }
 
 void drop_graphs(lks_handle* h) {
-    for (int k = 0; k < 2; ++k)
-        if (h->graph[k]) {
-            cudaGraphExecDestroy(h->graph[k]);
-            h->graph[k] = nullptr;
-        }
+    for (int g = 0; g < kGraphSizes; ++g)
+        for (int k = 0; k < 2; ++k)
+            if (h->graph[g][k]) {
+                cudaGraphExecDestroy(h->graph[g][k]);
+                h->graph[g][k] = nullptr;
+            }
 }
 
 // One step.  Two-buffer handles step from buffer `src` into the other; in-place handles take
@@ -251,14 +257,14 @@ cudaError_t step_once(lks_handle* h, int src, cudaStream_t st) {
                             h->staged ? &h->ss : nullptr);
 }
 
-// Capture kGraphSteps steps starting from buffer `start` into an executable graph.
-cudaError_t build_graph(lks_handle* h, int start) {
+// Capture kGraphSteps[size] steps starting from buffer `start` into an executable graph.
+cudaError_t build_graph(lks_handle* h, int size, int start) {
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     int src = start;
     cudaError_t le = cudaSuccess;
-    for (int64_t k = 0; k < kGraphSteps && le == cudaSuccess; ++k) {
+    for (int64_t k = 0; k < kGraphSteps[size] && le == cudaSuccess; ++k) {
         le = step_once(h, src, h->cap_stream);
         src ^= 1;
     }
@@ -268,7 +274,7 @@ cudaError_t build_graph(lks_handle* h, int start) {
         return le;
     }
     if (e != cudaSuccess) return e;
-    e = cudaGraphInstantiate(&h->graph[start], graph, 0);
+    e = cudaGraphInstantiate(&h->graph[size][start], graph, 0);
     cudaGraphDestroy(graph);
     return e;
 }
@@ -440,19 +446,21 @@ lks_status lks_step(lks_handle* h, int64_t n) {
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (n < 0) return fail(h, LKS_EINVAL, "n must be >= 0");
     if (h->p.inplace && (n & 1)) return fail(h, LKS_EINVAL, "an in-place handle steps in pairs: n must be even");
-    while (n >= kGraphSteps && !h->graphs_disabled) {
-        if (!h->graph[h->cur]) {
-            cudaError_t e = build_graph(h, h->cur);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                h->graphs_disabled = true;  // fall back to direct launches
-                break;
+    for (int g = 0; g < kGraphSizes && !h->graphs_disabled; ++g) {
+        while (n >= kGraphSteps[g] && !h->graphs_disabled) {
+            if (!h->graph[g][h->cur]) {
+                cudaError_t e = build_graph(h, g, h->cur);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    h->graphs_disabled = true;  // fall back to direct launches
+                    break;
+                }
             }
+            cudaError_t e = cudaGraphLaunch(h->graph[g][h->cur], h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+            n -= kGraphSteps[g];
+            h->steps += kGraphSteps[g];
         }
-        cudaError_t e = cudaGraphLaunch(h->graph[h->cur], h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
-        n -= kGraphSteps;
-        h->steps += kGraphSteps;
     }
     for (int64_t k = 0; k < n; ++k) {
         cudaError_t e = step_once(h, h->cur, h->stream);

@@ -898,6 +898,77 @@ lks_status lks_batch_moments(lks_batch* b, int32_t slot, int what, double* host_
     return LKS_OK;
 }
 
+lks_status lks_batch_get_state(lks_batch* b, int32_t slot, double* host_f, double* host_g) {
+    if (!b) return bfail(nullptr, LKS_EINVAL, "batch is NULL");
+    if (slot < 0 || slot >= (int32_t)b->slots.size() || !b->slots[slot].used) return bfail(b, LKS_EINVAL, "bad slot");
+    if (!host_f || !host_g) return bfail(b, LKS_EINVAL, "host_f/host_g is NULL");
+    InstDev I;
+    cudaError_t e = cudaMemcpyAsync(&I, b->d_tab + slot, sizeof(InstDev), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "lks_batch_get_state");
+    const Slot& s = b->slots[slot];
+    const int64_t N = (int64_t)s.nx * s.ny;
+    double* dtmp = nullptr;
+    e = cudaMalloc((void**)&dtmp, 19 * (size_t)N * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, LKS_ENOMEM, "cudaMalloc of the state staging buffer failed");
+    }
+    e = lks::launch_to_abs(b->cfg.storage, I.f[I.cur], I.g[I.cur], N, 0, N, I.pd.B0, dtmp, dtmp + 9 * N, b->stream,
+                           I.pd.coupling);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_f, dtmp, 9 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_g, dtmp + 9 * N, 10 * N * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(dtmp);
+    if (e != cudaSuccess) return bcuda(b, e, "lks_batch_get_state");
+    return LKS_OK;
+}
+
+lks_status lks_batch_set_state(lks_batch* b, int32_t slot, const double* host_f, const double* host_g) {
+    if (!b) return bfail(nullptr, LKS_EINVAL, "batch is NULL");
+    if (slot < 0 || slot >= (int32_t)b->slots.size() || !b->slots[slot].used) return bfail(b, LKS_EINVAL, "bad slot");
+    if (!host_f || !host_g) return bfail(b, LKS_EINVAL, "host_f/host_g is NULL");
+    InstDev I;
+    cudaError_t e = cudaMemcpyAsync(&I, b->d_tab + slot, sizeof(InstDev), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "lks_batch_set_state");
+    const Slot& s = b->slots[slot];
+    const int64_t N = (int64_t)s.nx * s.ny;
+    double* dtmp = nullptr;
+    e = cudaMalloc((void**)&dtmp, 19 * (size_t)N * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, LKS_ENOMEM, "cudaMalloc of the state staging buffer failed");
+    }
+    e = cudaMemcpyAsync(dtmp, host_f, 9 * N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dtmp + 9 * N, host_g, 10 * N * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = lks::launch_from_abs(b->cfg.storage, dtmp, dtmp + 9 * N, N, 0, N, I.pd.B0, I.f[I.cur], I.g[I.cur],
+                                 b->stream, I.pd.coupling);
+    if (e == cudaSuccess)
+        e = lks::launch_snapshot(b->cfg.storage, I.f[I.cur], I.g[I.cur], s.nx, s.ny, I.pd.B0, I.pd.Fx, I.snap,
+                                 b->stream, I.pd.coupling, I.tau_m);
+    // a fresh start from the new state: step count, residual history and status reset
+    I.steps = 0;
+    I.state = LKS_INST_RUNNING;
+    I.best_r = INFINITY;
+    I.residual = INFINITY;
+    I.stall = 0;
+    b->h_res[slot].state = LKS_INST_RUNNING;
+    b->h_res[slot].cur = I.cur;
+    b->h_res[slot].steps = 0;
+    b->h_res[slot].residual = INFINITY;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_tab + slot, &I, sizeof(InstDev), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_res + slot, &b->h_res[slot], sizeof(ResultDev), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(dtmp);
+    if (e != cudaSuccess) return bcuda(b, e, "lks_batch_set_state");
+    return LKS_OK;
+}
+
 lks_status lks_batch_remove(lks_batch* b, int32_t slot) {
     if (!b) return bfail(nullptr, LKS_EINVAL, "batch is NULL");
     if (slot < 0 || slot >= (int32_t)b->slots.size() || !b->slots[slot].used) return bfail(b, LKS_EINVAL, "bad slot");

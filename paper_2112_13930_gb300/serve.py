@@ -14,6 +14,12 @@ the GPU:
 Every result is the same as the request solved alone: the per-node update and the per-instance
 residual reduction do not depend on what else is resident.
 
+FP64 finish (finish_tol set): the lanes run in the server's storage type (FP32) only to a hand-off
+residual `finish_tol` (or until they stall at FP32's rounding floor), then continue in FP64 to `tol`,
+a residual FP32 cannot certify: small-lane instances move into a second, FP64 batch
+(lks_batch_get_state / lks_batch_set_state), large-lane lattices are replaced by an FP64 lattice
+with the same state (lks_get_state / lks_set_state).
+
 Failure handling (all on the host): a request the library rejects (LKS_EINVAL) is recorded as
 "rejected" and the server continues; an exception while solving a large-lane request is recorded
 as "error" and its stream and memory share are released; a request can be cancelled while queued
@@ -35,6 +41,20 @@ from . import sweep as _sweep
 TAU = _sweep.TAU
 
 
+def _finish_fp64(lat32, req, stream, tol, check_every, max_steps):
+    """Continue a lattice's state in FP64 to tol: lks_get_state -> FP64 lattice -> lks_set_state."""
+    f, g = lat32.get_state()
+    lat32.close()
+    lat = _default_lattice(req, "f64", stream)
+    try:
+        lat.set_state(f, g)
+        steps, r, status = lat.run_to_steady(tol, check_every, max_steps, raise_on_fail=False)
+        u, b = lat.profiles()
+    finally:
+        lat.close()
+    return steps, r, status, u, b
+
+
 def _default_lattice(req, storage, stream, inplace=False):
     p = _sweep.lattice_params(req)
     lat = _lks.Lattice(req["nx"], req["ny"], TAU, TAU, p["B0"], p["Fx"], req["closure"], storage, stream=stream,
@@ -46,17 +66,25 @@ def _default_lattice(req, storage, stream, inplace=False):
 class Server:
     def __init__(self, storage="f32", budget_bytes=120 << 30, small_pool_bytes=8 << 30, small_max_nodes=32768,
                  max_small=8192, large_workers=6, tol=1e-9, check_every=100, quantum=2000, max_steps=10**9,
-                 shape=None, batch=None, lattice_factory=None, streams=None, inplace=False):
+                 shape=None, batch=None, lattice_factory=None, streams=None, inplace=False, finish_tol=None):
         """inplace=True: every request keeps one population buffer (in-place pairs of steps, same
         results), so the memory budget admits about twice the requests; quantum, check_every and
-        max_steps must then be even."""
+        max_steps must then be even.  finish_tol: hand-off residual of the FP64 finish (None: off)."""
         self.storage = storage
         self.inplace = bool(inplace)
         self.tol, self.check_every, self.quantum, self.max_steps = tol, check_every, quantum, max_steps
+        self.finish_tol = finish_tol
         self.small_max_nodes = small_max_nodes
-        small_pool_bytes = min(small_pool_bytes, budget_bytes // 2)
-        self.large_budget = budget_bytes - small_pool_bytes
+        small_pool_bytes = min(small_pool_bytes, budget_bytes // (4 if finish_tol else 2))
+        self.large_budget = budget_bytes - small_pool_bytes * (2 if finish_tol else 1)
         self.large_used = 0
+        self.batch64 = None
+        self.small64 = {}  # FP64-batch slot -> request record
+        if finish_tol:
+            self.batch64 = _batch.Batch("f64", max_instances=max_small, pool_bytes=small_pool_bytes,
+                                        threads_per_group=shape[0] if shape else 0,
+                                        groups_per_cta=shape[1] if shape else 0,
+                                        cluster_ctas=shape[2] if shape and len(shape) > 2 else 0)
         if batch is None:
             batch = _batch.Batch(storage, max_instances=max_small, pool_bytes=small_pool_bytes,
                                  threads_per_group=shape[0] if shape else 0, groups_per_cta=shape[1] if shape else 0,
@@ -82,12 +110,15 @@ class Server:
         d = _sweep.make_desc(req, self.tol, self.check_every, self.max_steps)
         if self.is_small(req):
             return _batch.instance_footprint(d, self.storage, self.inplace)
-        return _lks.footprint_bytes(req["nx"], req["ny"], req["closure"], self.storage, inplace=self.inplace)
+        fp = _lks.footprint_bytes(req["nx"], req["ny"], req["closure"], self.storage, inplace=self.inplace)
+        if self.finish_tol:  # the FP64 lattice replaces the first one: the larger of the two
+            fp = max(fp, _lks.footprint_bytes(req["nx"], req["ny"], req["closure"], "f64"))
+        return fp
 
     # -- small lane ------------------------------------------------------------------------
     def try_admit_small(self, req, now, out):
         """True when the request left the queue (admitted or rejected), False when it must wait."""
-        d = _sweep.make_desc(req, self.tol, self.check_every, self.max_steps)
+        d = _sweep.make_desc(req, self.finish_tol or self.tol, self.check_every, self.max_steps)
         try:
             slot = self.batch.add(d)
         except _lks.LksError as e:
@@ -112,19 +143,52 @@ class Server:
             st, steps, r = self.batch.result(slot)
             if st == _batch.INST_RUNNING:
                 continue
+            if self.batch64 is not None and st in (_batch.INST_CONVERGED, _batch.INST_STALLED):
+                # hand the state over to the FP64 batch; wait there for a slot and memory
+                d = _sweep.make_desc(rec["req"], self.tol, self.check_every, self.max_steps)
+                s64 = self.batch64.add(d)
+                if s64 is None:
+                    continue
+                self.batch64.set_state(s64, *self.batch.get_state(slot))
+                self.batch.remove(slot)
+                del self.small_slots[slot]
+                rec["steps_fp32"] = int(steps)
+                self.small64[s64] = rec
+                continue
             del self.small_slots[slot]
             u, b = self.batch.profiles(slot)
             self.batch.remove(slot)
             rec.update({"state": _batch.STATE_NAMES[st], "steps": int(steps), "residual": r, "t_done": now,
                         "u": u, "b": b})
             out.append(rec)
+        for slot in list(self.small64):
+            st, steps, r = self.batch64.result(slot)
+            if st == _batch.INST_RUNNING:
+                continue
+            rec = self.small64.pop(slot)
+            u, b = self.batch64.profiles(slot)
+            self.batch64.remove(slot)
+            rec.update({"state": _batch.STATE_NAMES[st], "steps": rec["steps_fp32"] + int(steps), "residual": r,
+                        "t_done": now, "u": u, "b": b})
+            out.append(rec)
 
     # -- large lane ------------------------------------------------------------------------
     def _solve_large(self, req, sidx):
         lat = self.lattice_factory(req, self.streams[sidx])
         try:
-            steps, r, status = lat.run_to_steady(self.tol, self.check_every, self.max_steps, raise_on_fail=False)
-            u, b = lat.profiles()
+            if self.finish_tol:
+                steps, r, status = lat.run_to_steady(self.finish_tol, self.check_every, self.max_steps,
+                                                     raise_on_fail=False)
+                if status in (_lks.LKS_OK, _lks.LKS_ESTALLED):
+                    s64, r, status, u, b = _finish_fp64(lat, req, self.streams[sidx], self.tol, self.check_every,
+                                                        self.max_steps)
+                    steps += s64
+                else:
+                    u, b = lat.profiles()
+            else:
+                steps, r, status = lat.run_to_steady(self.tol, self.check_every, self.max_steps,
+                                                     raise_on_fail=False)
+                u, b = lat.profiles()
         finally:
             lat.close()
         state = {_lks.LKS_OK: "converged", _lks.LKS_ENOTCONVERGED: "max_steps", _lks.LKS_ESTALLED: "stalled",
@@ -193,8 +257,11 @@ class Server:
                 q_small.popleft()
             while q_large and self.try_admit_large(q_large[0], now, out):
                 q_large.popleft()
-            if self.small_slots:
-                self.batch.run(self.quantum)
+            if self.small_slots or self.small64:
+                if self.small_slots:
+                    self.batch.run(self.quantum)
+                if self.small64:
+                    self.batch64.run(self.quantum)
             else:
                 time.sleep(0.0005)
             now = time.perf_counter() - t0
@@ -210,6 +277,8 @@ class Server:
     def close(self):
         self.pool.shutdown(wait=True)
         self.batch.close()
+        if self.batch64 is not None:
+            self.batch64.close()
 
 
 def serve_one_at_a_time(trace, storage="f64", tol=1e-9, check_every=100, max_steps=10**9, time_limit=None):

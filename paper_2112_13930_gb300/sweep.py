@@ -118,3 +118,79 @@ def run_one_at_a_time(specs, storage="f64", tol=1e-10, check_every=100, max_step
         recs.append({"index": spec["index"], "steps": int(steps), "residual": r, "status": int(status),
                      "solve_s": te - ts, "t_done": te - t0, "l2_u": eu, "l2_b": eb, "u": u, "b": bx})
     return {"records": recs, "wall": time.perf_counter() - t0}
+
+
+def run_mixed(specs, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=20000, max_steps=10**9,
+              shape=None, time_budget=None):
+    """The mixed-precision lane: every instance starts in an FP32 batch with tolerance handoff_tol;
+    as soon as it leaves RUNNING there (converged at handoff_tol, or stalled at FP32's rounding floor)
+    its state moves (lks_batch_get_state / lks_batch_set_state) into an FP64 batch that runs it to
+    tol, a residual FP32 storage cannot certify.  The two batches' launches alternate on the GPU.
+    Unstable instances and instances at max_steps end in the FP32 lane.  Time-to-steady of an instance
+    is the wall time at the end of the FP64 launch in which it left RUNNING."""
+    import torch
+    d32 = [make_desc(s, handoff_tol, check_every, max_steps) for s in specs]
+    d64 = [make_desc(s, tol, check_every, max_steps) for s in specs]
+    pool32 = sum(_batch.instance_footprint(d, "f32") for d in d32) + (1 << 20)
+    pool64 = sum(_batch.instance_footprint(d, "f64") for d in d64) + (1 << 20)
+    kw = {}
+    if shape:
+        kw = dict(threads_per_group=shape[0], groups_per_cta=shape[1], cluster_ctas=shape[2] if len(shape) > 2 else 0)
+    b32 = _batch.Batch("f32", max_instances=len(specs), pool_bytes=pool32, **kw)
+    b64 = _batch.Batch("f64", max_instances=len(specs), pool_bytes=pool64, **kw)
+    s32 = [b32.add(d) for d in d32]
+    s64 = [None] * len(specs)
+    steps32 = [0] * len(specs)
+    state32 = [None] * len(specs)
+    done_at = [None] * len(specs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    running32, running64, launches = len(specs), 0, 0
+    while running32 or running64:
+        if running32:
+            running32 = b32.run(quantum)
+            launches += 1
+            for k, s in enumerate(s32):
+                if s is None:
+                    continue
+                st, steps, r = b32.result(s)
+                if st == _batch.INST_RUNNING:
+                    continue
+                steps32[k], state32[k] = int(steps), _batch.STATE_NAMES[st]
+                if st in (_batch.INST_CONVERGED, _batch.INST_STALLED):
+                    f, g = b32.get_state(s)
+                    s64[k] = b64.add(d64[k])
+                    b64.set_state(s64[k], f, g)
+                    b32.remove(s)
+                    s32[k] = None
+                else:
+                    done_at[k] = time.perf_counter() - t0  # ends in the FP32 lane
+        running64 = b64.run(quantum)
+        launches += 1
+        now = time.perf_counter() - t0
+        for k, s in enumerate(s64):
+            if s is not None and done_at[k] is None and b64.result(s)[0] != _batch.INST_RUNNING:
+                done_at[k] = now
+        running64 = sum(1 for k, s in enumerate(s64) if s is not None and done_at[k] is None)
+        if time_budget is not None and now > time_budget:
+            break
+    wall = time.perf_counter() - t0
+    recs = []
+    for k, spec in enumerate(specs):
+        if s64[k] is not None:
+            st, steps, r = b64.result(s64[k])
+            u, bx = b64.profiles(s64[k])
+            state, steps64 = _batch.STATE_NAMES[st], int(steps)
+        else:
+            st, steps, r = b32.result(s32[k])
+            u, bx = b32.profiles(s32[k])
+            state, steps64 = "fp32_" + _batch.STATE_NAMES[st], 0
+            steps32[k] = int(steps)
+        eu, eb = analytic_error(spec, u, bx)
+        recs.append({"index": spec["index"], "ny": spec["ny"], "ha": spec["ha"], "c": spec["c"], "kind": spec["kind"],
+                     "state": state, "fp32_state": state32[k], "steps_fp32": steps32[k], "steps_fp64": steps64,
+                     "residual": r, "t_done": done_at[k], "l2_u": eu, "l2_b": eb,
+                     "nodes": spec["nx"] * spec["ny"], "u": u, "b": bx})
+    b32.close()
+    b64.close()
+    return {"records": recs, "wall": wall, "launches": launches}

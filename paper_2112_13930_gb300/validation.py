@@ -75,10 +75,16 @@ def _desc(case, tol, max_steps):
     return d, a, fx
 
 
-def run(out_dir, tol=1e-10, max_steps=20_000_000, quantum=50_000, storage="f64"):
-    """Solve every case in one batch; write CSVs to out_dir; return the summary rows."""
+def case_name(case):
+    return "%s_%s_Ha%g_cl%g_cu%g_N%d" % (case["exp"], case["closure"], case["ha"], case["c_l"], case["c_u"],
+                                         case["ny"])
+
+
+def run(out_dir, tol=1e-10, max_steps=20_000_000, quantum=50_000, storage="f64", select=None):
+    """Solve every case (or those for which select(case) is true) in one batch; write CSVs to
+    out_dir; return the summary rows and the E3 convergence orders."""
     os.makedirs(out_dir, exist_ok=True)
-    cs = cases()
+    cs = [c for c in cases() if select is None or select(c)]
     descs = [_desc(c, tol, max_steps) for c in cs]
     pool = sum(_batch.instance_footprint(d, storage) for d, _, _ in descs) + (1 << 20)
     b = _batch.Batch(storage, max_instances=len(cs), pool_bytes=pool, threads_per_group=128, groups_per_cta=1)
@@ -96,8 +102,7 @@ def run(out_dir, tol=1e-10, max_steps=20_000_000, quantum=50_000, storage="f64")
         else:
             ua, ba = profiles.couette(y, a, case["ha"], case["c_l"], case["c_u"], case["u_w"], case["tau_f"],
                                       case["tau_m"])
-        name = "%s_%s_Ha%g_cl%g_cu%g_N%d" % (case["exp"], case["closure"], case["ha"], case["c_l"], case["c_u"],
-                                             case["ny"])
+        name = case_name(case)
         with open(os.path.join(out_dir, name + ".csv"), "w", newline="") as fh:
             w = csv.writer(fh)
             w.writerow(["y", "xi", "u_x", "u_x_closed_form", "B_x", "B_x_closed_form"])
@@ -106,7 +111,7 @@ def run(out_dir, tol=1e-10, max_steps=20_000_000, quantum=50_000, storage="f64")
                             "%.12e" % ba[k]])
         rows.append(dict(case=name, exp=case["exp"], closure=case["closure"], ha=case["ha"], c_l=case["c_l"],
                          c_u=case["c_u"], ny=case["ny"], state=_batch.STATE_NAMES[st], steps=int(steps), residual=r,
-                         l2_u=profiles.rel_l2(u, ua), l2_b=profiles.rel_l2(bx, ba)))
+                         l2_u=profiles.rel_l2(u, ua), l2_b=profiles.rel_l2(bx, ba), u=u, b=bx))
     b.close()
     # E3 convergence orders between consecutive resolutions (relative errors; a = N/2 or (N-1)/2)
     orders = []
@@ -120,12 +125,30 @@ def run(out_dir, tol=1e-10, max_steps=20_000_000, quantum=50_000, storage="f64")
                 orders.append(dict(closure=closure, c=c, n0=r0["ny"], n1=r1["ny"],
                                    order_u=-math.log(r1["l2_u"] / r0["l2_u"]) / math.log(a1 / a0),
                                    order_b=-math.log(r1["l2_b"] / r0["l2_b"]) / math.log(a1 / a0)))
+    fields = [k for k in rows[0] if k not in ("u", "b")]
     with open(os.path.join(out_dir, "summary.csv"), "w", newline="") as fh:
-        w = csv.DictWriter(fh, fieldnames=list(rows[0].keys()))
+        w = csv.DictWriter(fh, fieldnames=fields, extrasaction="ignore")
         w.writeheader()
         w.writerows(rows)
-    with open(os.path.join(out_dir, "convergence.csv"), "w", newline="") as fh:
-        w = csv.DictWriter(fh, fieldnames=list(orders[0].keys()))
-        w.writeheader()
-        w.writerows(orders)
+    if orders:
+        with open(os.path.join(out_dir, "convergence.csv"), "w", newline="") as fh:
+            w = csv.DictWriter(fh, fieldnames=list(orders[0].keys()))
+            w.writeheader()
+            w.writerows(orders)
     return rows, orders
+
+
+def table(rows, orders):
+    """Per experiment: cases, converged cases, max relative L2 errors of u_x and B_x; E3 order range."""
+    out = []
+    for exp in sorted({r["exp"] for r in rows}):
+        sub = [r for r in rows if r["exp"] == exp]
+        out.append(dict(exp=exp, cases=len(sub), converged=sum(r["state"] == "converged" for r in sub),
+                        max_l2_u=max(r["l2_u"] for r in sub), max_l2_b=max(r["l2_b"] for r in sub)))
+    for closure in ("link", "moment"):
+        sub = [o for o in orders if o["closure"] == closure]
+        if sub:
+            out.append(dict(exp="E3 order (%s)" % closure, cases=len(sub), converged=len(sub),
+                            max_l2_u=min(min(o["order_u"], o["order_b"]) for o in sub),
+                            max_l2_b=max(max(o["order_u"], o["order_b"]) for o in sub)))
+    return out

@@ -244,3 +244,65 @@ def test_batch_rejects_mixed_coupling(mods):
     with pytest.raises(lks.LksError):
         b.add(d)
     b.close()
+
+
+def test_state_transfer_between_batches(mods):
+    """lks_batch_get_state / lks_batch_set_state: an FP64 instance copied into another batch continues
+    as the original does (to the rounding of the FP64 absolute populations), and its bookkeeping
+    restarts (steps 0, RUNNING)."""
+    lks, batch = mods
+    d = _descs(batch, n=2, check_every=50)[0]
+    a = batch.Batch("f64", max_instances=2, pool_bytes=8 << 20)
+    b = batch.Batch("f64", max_instances=2, pool_bytes=8 << 20)
+    sa = a.add(d)
+    a.run(400)
+    f, g = a.get_state(sa)
+    sb = b.add(d)
+    b.set_state(sb, f, g)
+    st, steps, _ = b.result(sb)
+    assert st == batch.INST_RUNNING and steps == 0
+    f2, g2 = b.get_state(sb)
+    np.testing.assert_allclose(f2, f, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(g2, g, rtol=0, atol=1e-15)
+    a.run(300)
+    b.run(300)
+    ma, mb = a.moments(sa), b.moments(sb)
+    for k in (1, 3):
+        assert np.max(np.abs(ma[k] - mb[k])) <= 1e-12 * np.max(np.abs(ma[k]))
+    a.close()
+    b.close()
+
+
+def test_fp32_floor_finished_in_fp64(mods):
+    """The mixed-precision lane: an FP32 solve run to a hand-off tolerance of 1e-5 (or stopped at its
+    rounding floor, STALLED), moved into an FP64 batch, converges there to 1e-10 and agrees with a
+    pure FP64 solve of the same instance."""
+    lks, batch = mods
+    ny, ha, c = 129, 10.0, 0.5
+    a = ny / 2
+    b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+    fx = an.force_for_centre_speed(0.01 * 64 / (ny - 1), ha, c, a, 0.8)
+    d32 = batch.make_desc(4, ny, "link", 0.8, 0.8, b0, fx, c, c, tol=1e-5, check_every=100, max_steps=4_000_000)
+    d64 = batch.make_desc(4, ny, "link", 0.8, 0.8, b0, fx, c, c, tol=1e-10, check_every=100, max_steps=4_000_000)
+    b32 = batch.Batch("f32", max_instances=1, pool_bytes=8 << 20)
+    s32 = b32.add(d32)
+    while b32.run(100_000):
+        pass
+    st32, steps32, r32 = b32.result(s32)
+    assert st32 in (batch.INST_CONVERGED, batch.INST_STALLED), (st32, steps32, r32)
+    b64 = batch.Batch("f64", max_instances=2, pool_bytes=16 << 20)
+    sf = b64.add(d64)
+    b64.set_state(sf, *b32.get_state(s32))
+    sp = b64.add(d64)
+    while b64.run(100_000):
+        pass
+    stf, stepsf, rf = b64.result(sf)
+    stp, stepsp, rp = b64.result(sp)
+    assert stf == batch.INST_CONVERGED and stp == batch.INST_CONVERGED
+    uf, bf = b64.profiles(sf)
+    up, bp = b64.profiles(sp)
+    assert np.max(np.abs(uf - up)) <= 1e-6 * np.max(np.abs(up))
+    assert np.max(np.abs(bf - bp)) <= 1e-6 * np.max(np.abs(bp))
+    assert stepsf < stepsp   # the FP32 phase already covered part of the way
+    b32.close()
+    b64.close()

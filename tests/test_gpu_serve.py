@@ -78,3 +78,59 @@ def test_admission_waits_for_memory(mods):
     dones = sorted(r["t_done"] for r in recs)
     for k in range(1, len(tr)):
         assert admits[k] >= dones[k - 1] - 1e-9   # the next one got in only after one left
+
+
+def test_served_fp64_finish_equals_solo_mixed_solves(mods):
+    """With finish_tol the server hands each request from FP32 (at residual 1e-5) to FP64 (to 1e-9);
+    every result equals the same hand-off done alone: small lane, an FP32 batch then an FP64 batch
+    through lks_batch_get_state / lks_batch_set_state; large lane, an FP32 lattice then an FP64
+    lattice through lks_get_state / lks_set_state -- bit for bit."""
+    lks, batch, serve, sweep, workloads = mods
+    tr = _trace(workloads)[:8]
+    kw = dict(tol=1e-9, check_every=100, max_steps=40_000)
+    srv = serve.Server("f32", budget_bytes=1 << 30, small_pool_bytes=128 << 20, small_max_nodes=400,
+                       large_workers=2, quantum=2000, shape=(64, 2), finish_tol=1e-5, **kw)
+    recs = srv.serve(tr, time_limit=600)
+    srv.close()
+    assert len(recs) == len(tr)
+    for rec in recs:
+        req = rec["req"]
+        if rec["lane"] == "small":
+            b32 = batch.Batch("f32", max_instances=1, pool_bytes=64 << 20, threads_per_group=64, groups_per_cta=1)
+            s = b32.add(sweep.make_desc(req, 1e-5, 100, 40_000))
+            while b32.run(2000):
+                pass
+            st32, steps32, _ = b32.result(s)
+            if st32 in (batch.INST_CONVERGED, batch.INST_STALLED):
+                b64 = batch.Batch("f64", max_instances=1, pool_bytes=64 << 20, threads_per_group=64,
+                                  groups_per_cta=1)
+                s64 = b64.add(sweep.make_desc(req, 1e-9, 100, 40_000))
+                b64.set_state(s64, *b32.get_state(s))
+                while b64.run(2000):
+                    pass
+                st, steps64, _ = b64.result(s64)
+                u, bx = b64.profiles(s64)
+                steps = steps32 + steps64
+                b64.close()
+            else:
+                st, steps = st32, steps32
+                u, bx = b32.profiles(s)
+            b32.close()
+            assert rec["state"] == batch.STATE_NAMES[st]
+        else:
+            p = sweep.lattice_params(req)
+            lat = lks.Lattice(req["nx"], req["ny"], 0.8, 0.8, p["B0"], p["Fx"], req["closure"], "f32")
+            lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
+            steps, r, status = lat.run_to_steady(1e-5, 100, 40_000, raise_on_fail=False)
+            if status in (lks.LKS_OK, lks.LKS_ESTALLED):
+                f, g = lat.get_state()
+                lat.close()
+                lat = lks.Lattice(req["nx"], req["ny"], 0.8, 0.8, p["B0"], p["Fx"], req["closure"], "f64")
+                lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
+                lat.set_state(f, g)
+                s64, r, status = lat.run_to_steady(1e-9, 100, 40_000, raise_on_fail=False)
+                steps += s64
+            u, bx = lat.profiles()
+            lat.close()
+        assert steps == rec["steps"]
+        assert np.array_equal(u, rec["u"]) and np.array_equal(bx, rec["b"])

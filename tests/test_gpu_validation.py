@@ -1,0 +1,82 @@
+"""The paper's validation experiments (Sec. VIII) on the GPU through validation.py: a reduced set of
+E1 (body force, link-based), E2 (body force, moment-based), E4/E5 (Hartmann-Couette, link / moment)
+and an E3 pair (grid convergence), solved with the FP64 batched engine to a residual of 1e-10.
+
+Each case's profiles equal the FP64 oracle's after the same number of steps (1e-11 of the profile
+scale), its error against the closed form is within the E-tables' bounds, and the E3 pair converges
+at second order; the summary CSVs the driver writes hold the same numbers."""
+import csv
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+SUBSET = {
+    "E1_link_Ha5_cl0.5_cu0.5_N101",
+    "E2_moment_Ha20_cl0.1_cu0.1_N101",
+    "E4_link_Ha5_cl0.5_cu0.5_N101",
+    "E5_moment_Ha20_cl0.5_cu0_N101",
+    "E3_link_Ha20_cl0.5_cu0.5_N50",
+    "E3_link_Ha20_cl0.5_cu0.5_N100",
+}
+# closed-form bounds: twice the largest error of each experiment over its full case list on GB300
+BOUND = {"E1": 5e-3, "E2": 6e-3, "E3": 2e-2, "E4": 4e-3, "E5": 4e-3}
+
+
+@pytest.fixture(scope="module")
+def solved(tmp_path_factory):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_13930_gb300 import build, lks, validation
+    build.build()
+    lks.load()
+    out = tmp_path_factory.mktemp("validation")
+    rows, orders = validation.run(str(out), select=lambda c: validation.case_name(c) in SUBSET)
+    return validation, rows, orders, out
+
+
+def test_subset_is_the_intended_one(solved):
+    _, rows, _, _ = solved
+    assert {r["case"] for r in rows} == SUBSET
+
+
+def test_cases_converge_within_the_closed_form_bounds(solved):
+    _, rows, _, _ = solved
+    for r in rows:
+        assert r["state"] == "converged", r["case"]
+        assert r["residual"] < 1e-10
+        assert r["l2_u"] < BOUND[r["exp"]] and r["l2_b"] < BOUND[r["exp"]], (r["case"], r["l2_u"], r["l2_b"])
+
+
+def test_profiles_equal_the_oracle(solved):
+    validation, rows, _, _ = solved
+    by_name = {validation.case_name(c): c for c in validation.cases()}
+    for r in rows:
+        d, a, fx = validation._desc(by_name[r["case"]], 1e-10, 20_000_000)
+        o = oracle.Oracle(d.nx, d.ny, d.tau_f, d.tau_m, d.B0, d.Fx, d.closure, d.c_bottom, d.c_top, d.u_bottom,
+                          d.u_top)
+        o.step(r["steps"])
+        uo, bo = o.profiles()
+        assert np.max(np.abs(r["u"] - uo)) <= 1e-11 * np.max(np.abs(uo)), r["case"]
+        assert np.max(np.abs(r["b"] - bo)) <= 1e-11 * np.max(np.abs(bo)), r["case"]
+
+
+def test_e3_pair_is_second_order(solved):
+    _, _, orders, _ = solved
+    assert len(orders) == 1
+    assert 1.8 < orders[0]["order_u"] < 2.2 and 1.8 < orders[0]["order_b"] < 2.2, orders
+
+
+def test_summary_csv_holds_the_rows(solved):
+    _, rows, _, out = solved
+    with open(os.path.join(str(out), "summary.csv")) as fh:
+        got = {row["case"]: row for row in csv.DictReader(fh)}
+    for r in rows:
+        assert float(got[r["case"]]["l2_u"]) == pytest.approx(r["l2_u"], rel=1e-12)
+        assert int(got[r["case"]]["steps"]) == r["steps"]
