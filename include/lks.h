@@ -152,9 +152,10 @@ lks_status lks_create(const lks_params* p, lks_handle** out);
  * effect for steps enqueued afterwards. */
 lks_status lks_set_walls(lks_handle* h, double c_bottom, double c_top, double u_bottom, double u_top);
 
-/* Enqueue n >= 0 fused collide-stream steps (steps a1-a6 of the hot path).
- * Asynchronous; long runs go through a captured CUDA graph.  n must be even
- * for an in-place handle (LKS_EINVAL). */
+/* Enqueue n >= 0 fused collide-stream steps (pull-stream, wall closures, moments, equilibria,
+ * collision and store in one kernel per step).  Asynchronous; n runs as captured CUDA graphs of
+ * 64, 32, ..., 2 steps (built on first use, rebuilt after lks_set_walls) plus at most one direct
+ * launch.  n must be even for an in-place handle (LKS_EINVAL). */
 lks_status lks_step(lks_handle* h, int64_t n);
 
 /* Steps taken since lks_create / lks_set_state. */

@@ -213,7 +213,7 @@ __device__ __forceinline__ V tree_sum3(V (&v)[N]) {
     return v[0];
 }
 
-// Moments, equilibria, source and collision of one node or of a pair of nodes (a3-a5).  F(k) returns
+// Moments, equilibria, source and collision of one node or of a pair of nodes.  F(k) returns
 // the streamed value of slot k (wall terms included), out(k, v) takes the post-collision value of
 // slot k.  With the rest (rho = 1, u = 0, B = (0, B0, 0)) subtracted, per direction a of D3Q19
 //   f^eq_a - f^rest_a = w_a (drho + rho b_a) + 4.5 w_a [ (|e_a|^2/2 - 1/6) q - (e_a.B)^2 + (e_a.B_rest)^2 ]

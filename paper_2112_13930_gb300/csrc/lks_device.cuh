@@ -141,7 +141,7 @@ __device__ __forceinline__ float2 recip(float2 rho) { return make_float2(recip(r
 template <typename V> __device__ __forceinline__ V zero_of() { return V(0); }
 template <> __device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.0f, 0.0f); }
 
-// a4-a5 for g (Eqs. geqmagneticfield, LKSformagneticfield): g' = (1 - w_m) g + w_m g^eq,dev with
+// Equilibrium and collision of g (Eqs. geqmagneticfield, LKSformagneticfield): g' = (1 - w_m) g + w_m g^eq,dev with
 //   g^eq_x = W (Bx - 3 e_y E),  g^eq,dev_y = W (dBy + 3 e_x E),  E = u_x B_y - u_y B_x.
 template <typename C, typename V>
 __device__ __forceinline__ void collide_g(V gx[5], V gy[5], V ux, V uy, V bx, V by, V dby, const StepParams<C>& p) {
@@ -175,7 +175,7 @@ template <typename C, typename V>
 __device__ __forceinline__ void collide_node(V f[9], V gx[5], V gy[5], const StepParams<C>& p) {
     const auto half = C(0.5), three = C(3), four5 = C(4.5), one5 = C(1.5);
 
-    // a3: moments
+    // moments
     const auto drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
     const auto rho = C(1) + drho;
     const auto jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
@@ -187,7 +187,7 @@ __device__ __forceinline__ void collide_node(V f[9], V gx[5], V gy[5], const Ste
     const auto dby = ((gy[0] + gy[1]) + (gy[2] + gy[3])) + gy[4];
     const auto by = p.B0 + dby;
 
-    // a4-a5 for f.  Post-collision deviation:
+    // equilibrium, source and collision of f.  Post-collision deviation:
     //   f' = (1 - w) f + w f^eq,dev + (1 - 1/(2 tau)) S
     //   f^eq,dev_a = w_a (drho + rho bm1_a) + M_a,  bm1_a = 3 eu + 4.5 eu^2 - 1.5 u^2
     //   S_a = 3 (e_ax - u_x) F_x w_a (1 + bm1_a)
@@ -363,7 +363,7 @@ __device__ __forceinline__ void collide(V f[9], V gx[5], V gy[5], const StepPara
         collide_node<C>(f, gx, gy, p);
 }
 
-// One node of the fused step (hot-path steps a1-a6): pull-stream from (fin, gin), wall closure,
+// One node of the fused step: pull-stream from (fin, gin), wall closure,
 // moments, equilibria, collision, store to (fout, gout).  n = y*nx + x of a lattice laid out as
 // f[a][y][x], g[k][a][y][x].  Every element of fin/gin is read by exactly one node per step:
 // interior rows pull from rows y-1 / y / y+1 (Eqs. LBMforflowfield, LKSformagneticfield);
@@ -386,7 +386,7 @@ __device__ __forceinline__ void step_node_with(const S* fin, const S* gin, S* fo
     C f[9], gx[5], gy[5];
     const S* gxin = gin;
     const S* gyin = gin + 5 * N;
-    // a1: pull-stream, periodic in x
+    // pull-stream, periodic in x
     f[0] = L::ld(fin + 0 * N + rc + i);
     f[1] = L::ld(fin + 1 * N + rc + im);
     f[3] = L::ld(fin + 3 * N + rc + ip);
@@ -410,7 +410,7 @@ __device__ __forceinline__ void step_node_with(const S* fin, const S* gin, S* fo
         gx[4] = L::ld(gxin + 4 * N + rn + i);
         gy[4] = L::ld(gyin + 4 * N + rn + i);
     }
-    // a2: wall closures
+    // wall closures
     if (CLOSURE == 0) {
         if (bottom) {
             const WallCoef<C>& w = p.bot;
@@ -432,9 +432,9 @@ __device__ __forceinline__ void step_node_with(const S* fin, const S* gin, S* fo
         if (bottom) moment_closure_bottom<C, COUPLING>(f, gx, gy, p.bot, p);
         if (top) moment_closure_top<C, COUPLING>(f, gx, gy, p.top, p);
     }
-    // a3-a5
+    // moments, equilibria, collision
     collide<C, COUPLING>(f, gx, gy, p);
-    // a6: store
+    // store
     S* gxo = gout;
     S* gyo = gout + 5 * N;
 #pragma unroll

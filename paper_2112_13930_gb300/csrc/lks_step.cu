@@ -1,4 +1,4 @@
-// lks_step.cu -- the fused collide-stream kernel (hot path steps a1-a6) of one lattice.
+// lks_step.cu -- the fused collide-stream kernel of one lattice (pull, wall closures, collision, store).
 //
 // One thread per node (the per-node work is step_node in lks_device.cuh), nodes numbered n = y*nx + x so that a warp reads 32 consecutive
 // x positions of each population plane: every one of the 19 loads and 19 stores of a warp
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256, CLOSURE == 0 ? 3 : 4) step_kernel_pair(co
         B = P::hi(w);
     };
     const int64_t ec = (int64_t)j * nx, es = ec - nx, en = ec + nx;   // element row starts
-    // a1: pull-stream (rows y-1 / y / y+1), periodic in x
+    // pull-stream (rows y-1 / y / y+1), periodic in x
     pull_same(fw, 0, rc, true, fA[0], fB[0]);
     pull_left(fw, fin, 1, rc, ec, true, fA[1], fB[1]);
     pull_right(fw, fin, 3, rc, ec, true, fA[3], fB[3]);
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256, CLOSURE == 0 ? 3 : 4) step_kernel_pair(co
     pull_right(gyw, gys, 3, rc, ec, true, gyA[3], gyB[3]);
     pull_same(gyw, 2, rs, !bottom, gyA[2], gyB[2]);
     pull_same(gyw, 4, rn, !top, gyA[4], gyB[4]);
-    // a2: wall closures
+    // wall closures
     if (CLOSURE == 0) {
         if (bottom) {
             const WallCoef<float>& w = p.bot;
@@ -168,10 +168,10 @@ __global__ void __launch_bounds__(256, CLOSURE == 0 ? 3 : 4) step_kernel_pair(co
             moment_closure_top<float, COUPLING>(fB, gxB, gyB, p.top, p);
         }
     }
-    // a3-a5
+    // moments, equilibria, collision
     collide<float, COUPLING>(fA, gxA, gyA, p);
     collide<float, COUPLING>(fB, gxB, gyB, p);
-    // a6: store both nodes of each plane as one word
+    // store both nodes of each plane as one word
     if (!active) return;
     uint32_t* fo = reinterpret_cast<uint32_t*>(fout);
     uint32_t* go = reinterpret_cast<uint32_t*>(gout);

@@ -1,6 +1,6 @@
 // lks_step_staged.cu -- the fused step of one lattice with 16-bit deviation storage, rows staged
 // through shared memory by the bulk-copy engine (two-buffer handles; nx a multiple of 8 and at least
-// kSegX).  Hot-path steps a1-a6 as in step_node_with (lks_device.cuh), with the same per-node
+// kSegX).  The pull, wall closures, collision and store as in step_node_with (lks_device.cuh), with the same per-node
 // arithmetic: the results agree bit for bit with the one- and two-node kernels.
 //
 // A task is a row segment of up to kSegX nodes (x0 .. x0 + T - 1 of row y).  For each of the 19
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
                     gx[a] = v[9 + a];
                     gy[a] = v[14 + a];
                 }
-                // a2: wall closures (the link slots hold the node's own outgoing populations)
+                // wall closures (the link slots hold the node's own outgoing populations)
                 if (W && CLOSURE == 0) {
                     if (bottom) {
                         const WallCoef<float>& w = p.bot;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) step_kernel_staged(const S* __res
                         gy[4] = -gy[4];
                     }
                 }
-                // moment closure, a3-a5 for both nodes
+                // moment closure, moments, equilibria and collision for both nodes
                 close_collide_pair<CLOSURE, COUPLING, W>(f, gx, gy, p, bottom, top);
                 const int64_t q = ((int64_t)y * nx + x0) / 2 + tid;  // the pair's word in every plane
                 uint32_t* fo = reinterpret_cast<uint32_t*>(fout);
