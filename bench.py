@@ -655,6 +655,24 @@ def bench_sweep(args):
         if da <= 1e-4:
             gate["fp64_meets_analytic_le_1e-4"] += 1
             gate["mixed_meets_analytic_where_fp64_does"] += int(max(m["l2_u"], m["l2_b"]) <= 1e-4)
+    # L2-resident copy bandwidth (2 x 24 MB, well inside the 129 MB L2), the roofline of the batched
+    # kernel whose small instances stay in L2 while resident
+    a = torch.empty(6 << 20, dtype=torch.float32, device="cuda")
+    bbuf = torch.empty_like(a)
+    for _ in range(20):
+        bbuf.copy_(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(5):
+        e0.record()
+        for _ in range(200):
+            bbuf.copy_(a)
+        e1.record()
+        e1.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3 / 200
+        best = dt if best is None else min(best, dt)
+    l2_gbs = 2 * a.numel() * 4 / best / 1e9
+    del a, bbuf
     out = {"workload": "sweep", "metric": "sweep solves/s", "unit": "solves/s", "higher_is_better": True,
            "sample": len(sample), "of": len(specs), "dtype": "f32->f64",
            "value": round(len(mconv) / mix["wall"], 3),
@@ -670,6 +688,11 @@ def bench_sweep(args):
                          "time_to_steady_p50_s": pct([r["t_done"] for r in done], 50),
                          "time_to_steady_p99_s": pct([r["t_done"] for r in done], 99),
                          "states": states_of(recs), "glups": round(node_updates / res["wall"] / 1e9, 2),
+                         "roofline_l2": {"bound": "l2", "achieved": round(node_updates / res["wall"] * 152 / 1e9, 1),
+                                         "peak": round(l2_gbs, 1), "unit": "GB/s",
+                                         "frac": round(node_updates / res["wall"] * 152 / 1e9 / l2_gbs, 4),
+                                         "peak_source": "measured here: torch copy of 24 MB within L2, best of 5",
+                                         "note": "whole sweep wall time, launch gaps and the tail included"},
                          "launches": res["launches"], "autotune": res["tune"],
                          "tail_shape_at_s": res["tail_shape_at"]},
            "fp64_batched": {"instances": len(r64), "wall_s": round(res64["wall"], 3),
