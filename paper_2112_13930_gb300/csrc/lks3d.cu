@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(256) step3_duct_kernel(const S* __restrict__ f
 // which the producer waits for before it refills the stage, so kStages3 - 1 tasks' reads are in
 // flight while one is computed.  Two such groups of eight consumer warps take alternate tasks, so
 // one group's loads and arithmetic overlap the other's (17 resident warps per SM instead of 9; the
-// collision reads each node's g values twice, see collide3, to fit 120 registers per thread).
+// collision reads each node's g values twice, see collide3, to fit 96 registers per thread).
 // Each consumer thread takes two x-adjacent nodes (x even) as one
 // float2 (packed FP32 arithmetic), reading 32-bit words of the staged rows and storing one word
 // per plane.  Each slot takes a fixed kTaskNodes3 elements of a stage, so the slot offsets are
@@ -468,10 +468,11 @@ constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 inline int rows_per_task3(int nx, int ny) { return std::max(1, std::min(ny, kTaskNodes3 / nx)); }
 inline size_t staged_smem3() { return 128 + (size_t)kStages3 * kStageElems3 * 2; }
 
-// 17 warps x 32 threads x 120 registers = 65280 of the SM's 65536: one block per SM (its shared
-// memory allows no more), with every warp resident.
+// The register file is handed out to warps in groups of four: 17 warps take the registers of 20,
+// and 20 x 32 threads x 96 registers = 61440 of the SM's 65536 (at 120 registers the block would
+// not fit at all).  One block per SM (its shared memory allows no more), every warp resident.
 template <typename S>
-__global__ void __maxnreg__(120) step3_staged_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
+__global__ void __maxnreg__(96) step3_staged_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
                                                                     S* __restrict__ fout, S* __restrict__ gout,
                                                                     const Params3<float> p, int R, int* err) {
     extern __shared__ __align__(128) unsigned char sm3[];
