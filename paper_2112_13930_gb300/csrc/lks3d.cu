@@ -220,16 +220,13 @@ __device__ __forceinline__ V tree_sum3(V (&v)[N]) {
 // with b_a = 3 e.u + 4.5 (e.u)^2 - 1.5 u^2 and q = |B|^2 - B0^2; the source is
 // (1 - 1/(2 tau_f)) 3 w_a (e_a - u).F (1 + b_a); and per component i of B on D3Q7
 //   g'_ai = (1 - w_m) g_ai + w_m W_a (dB_i + 4 e_ad E_di),  E_di = u_d B_i - B_d u_i  (E_ii = 0).
-//
-// Order: the 21 g values are first read only for their sums (B), then the 19 f values are read,
-// updated and written, and only then are the g values read again (F(19 + k) a second time) for
-// their own update -- so that f and g are never live together.  The arithmetic is the same in
-// every caller; for the staged kernel, whose F reads shared memory, this halves the values held in
-// registers across the f update.
 template <typename V, typename C, typename In, typename Out>
 __device__ __forceinline__ void collide3(const Params3<C>& p, In F, Out out) {
     using namespace lks;
     typedef VecOf<V> K;
+    V f[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) f[a] = F(a);
     // Moments.  FP64 (bound by the FP64 pipe's latency and rate) sums as balanced trees; FP32 and
     // the FP32x2 pairs keep left-to-right sums, which need fewer live registers in the staged
     // kernel.  The one-node and two-node FP32 paths use the same order, so they agree bit for bit.
@@ -245,20 +242,6 @@ __device__ __forceinline__ void collide3(const Params3<C>& p, In F, Out out) {
             return r;
         }
     };
-    V bx, dby, bz;
-    {
-        V t7[3][7];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int a = 0; a < 7; ++a) t7[i][a] = F(19 + 7 * i + a);
-        bx = sum_of(t7[0]);
-        dby = sum_of(t7[1]);
-        bz = sum_of(t7[2]);
-    }
-    V f[19];
-#pragma unroll
-    for (int a = 0; a < 19; ++a) f[a] = F(a);
     V t19[19];
 #pragma unroll
     for (int a = 0; a < 19; ++a) t19[a] = f[a];
@@ -278,6 +261,15 @@ __device__ __forceinline__ void collide3(const Params3<C>& p, In F, Out out) {
     const V rho = vadd(K::set(C(1)), drho);
     const V inv = vrecip(rho);
     const V ux = vmul(vadd(jx, K::set(p.hFx)), inv), uy = vmul(jy, inv), uz = vmul(jz, inv);
+    V g[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) g[k] = F(19 + k);
+    V t7[3][7];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < 7; ++a) t7[i][a] = g[7 * i + a];
+    const V bx = sum_of(t7[0]), dby = sum_of(t7[1]), bz = sum_of(t7[2]);
     const V by = vadd(K::set(p.B0), dby);
     const V q = vfma(bx, bx, vfma(bz, bz, vmul(dby, vadd(K::set(p.twoB0), dby))));  // |B|^2 - B0^2
     const V usq = vfma(ux, ux, vfma(uy, uy, vmul(uz, uz)));
@@ -314,12 +306,6 @@ __device__ __forceinline__ void collide3(const Params3<C>& p, In F, Out out) {
         const V sa = vfma(kxe, bm1, kxe);  // K (e_x - u_x) (1 + b)
         out(a, vfma(om1f, f[a], vfma(omf, feq, sa)));
     }
-    // read the g values again for their update (a compiler barrier keeps a reader of memory from
-    // reusing values it loaded for the sums above)
-    asm volatile("" ::: "memory");
-    V g[21];
-#pragma unroll
-    for (int k = 0; k < 21; ++k) g[k] = F(19 + k);
     const V o1 = K::set(p.om1m), ow0 = K::set(p.omW0), ow1 = K::set(p.omW1);
     const V u[3] = {ux, uy, uz}, B[3] = {bx, by, bz};
     auto comp = [&](int i, V dBi) {
@@ -447,20 +433,15 @@ __global__ void __launch_bounds__(256) step3_duct_kernel(const S* __restrict__ f
 // an index wrap within the staged row.  Eight consumer warps take the task's nodes: 40 values from
 // shared memory, collide3, 40 stores; each warp then arrives on the stage's `empty` barrier,
 // which the producer waits for before it refills the stage, so kStages3 - 1 tasks' reads are in
-// flight while one is computed.  Two such groups of eight consumer warps take alternate tasks, so
-// one group's loads and arithmetic overlap the other's (17 resident warps per SM instead of 9; the
-// collision reads each node's g values twice, see collide3, to fit 96 registers per thread).
-// Each consumer thread takes two x-adjacent nodes (x even) as one
+// flight while one is computed.  Each consumer thread takes two x-adjacent nodes (x even) as one
 // float2 (packed FP32 arithmetic), reading 32-bit words of the staged rows and storing one word
 // per plane.  Each slot takes a fixed kTaskNodes3 elements of a stage, so the slot offsets are
 // constants.  Rows must be 16-byte aligned: nx a multiple of 8, and nx <= kTaskNodes3.  A wait
 // that runs out (kWaitNs) sets *err and ends that warp's loop; the producer then waits, within the
 // same limit, for the last copies it issued to each stage before it returns.
-constexpr int kTaskNodes3 = 512;                 // nodes of a task: threads of a consumer group x 2
-constexpr int kGroupWarps3 = kTaskNodes3 / 64;   // warps of a consumer group (one task at a time)
-constexpr int kGroups3 = 2;                      // consumer groups: group c takes tasks c, c + 2, ...
-constexpr int kConsumerWarps3 = kGroups3 * kGroupWarps3;
-constexpr int kThreads3 = kConsumerWarps3 * 32 + 32;  // consumers + the producer warp
+constexpr int kTaskNodes3 = 512;                 // nodes of a task: consumer threads x 2
+constexpr int kConsumerWarps3 = kTaskNodes3 / 64;
+constexpr int kThreads3 = kTaskNodes3 / 2 + 32;  // consumers + the producer warp
 constexpr int kStages3 = 5;
 constexpr int kStageElems3 = 40 * kTaskNodes3;   // a slot takes kTaskNodes3 elements of a stage
 constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
@@ -468,11 +449,8 @@ constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 inline int rows_per_task3(int nx, int ny) { return std::max(1, std::min(ny, kTaskNodes3 / nx)); }
 inline size_t staged_smem3() { return 128 + (size_t)kStages3 * kStageElems3 * 2; }
 
-// The register file is handed out to warps in groups of four: 17 warps take the registers of 20,
-// and 20 x 32 threads x 96 registers = 61440 of the SM's 65536 (at 120 registers the block would
-// not fit at all).  One block per SM (its shared memory allows no more), every warp resident.
 template <typename S>
-__global__ void __maxnreg__(96) step3_staged_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
+__global__ void __launch_bounds__(kThreads3, 1) step3_staged_kernel(const S* __restrict__ fin, const S* __restrict__ gin,
                                                                     S* __restrict__ fout, S* __restrict__ gout,
                                                                     const Params3<float> p, int R, int* err) {
     extern __shared__ __align__(128) unsigned char sm3[];
@@ -489,7 +467,7 @@ __global__ void __maxnreg__(96) step3_staged_kernel(const S* __restrict__ fin, c
     if (tid == 0) {
         for (int s = 0; s < kStages3; ++s) {
             lks::mbar_init(&full[s], 1);
-            lks::mbar_init(&empty[s], kGroupWarps3);
+            lks::mbar_init(&empty[s], kConsumerWarps3);
         }
         lks::mbar_init_fence();
     }
@@ -554,14 +532,12 @@ __global__ void __maxnreg__(96) step3_staged_kernel(const S* __restrict__ fin, c
         return;
     }
 
-    // consumers: group c = warp / kGroupWarps3 takes the block's tasks c, c + kGroups3, ...; its
-    // thread q holds nodes x, x + 1 (x = 2 q mod nx, even) of task row j = 2 q / nx
+    // consumers: thread tid holds nodes x, x + 1 (x = 2 tid mod nx, even) of task row j = 2 tid / nx
     typedef lks::Packed<S> P;
-    const int group = warp / kGroupWarps3, q = tid - group * kGroupWarps3 * 32;
-    const int j = (2 * q) / nx, x = 2 * q - j * nx;
+    const int j = (2 * tid) / nx, x = 2 * tid - j * nx;
     const int nw = nx / 2, xw = x / 2;                        // words per row, the pair's word
     const int xwm = xw == 0 ? nw - 1 : xw - 1, xwp = xw == nw - 1 ? 0 : xw + 1;
-    for (int64_t it = group; it < nmine; it += kGroups3) {
+    for (int64_t it = 0; it < nmine; ++it) {
         const int s = (int)(it % kStages3);
         if (!lks::mbar_wait_bounded(&full[s], (uint32_t)(it / kStages3) & 1u, kWaitNs)) {
             atomicExch(err, 1);
