@@ -46,9 +46,11 @@ def _pair(l3, case, storage, seed=0):
     o = oracle.Oracle3D(nx, ny, nz, 0.8, 0.7, B0, Fx, c[0], c[1], u[0], u[1], side=True, c_back=cs[0],
                         c_front=cs[1])
     f_rest, g_rest = o.f.copy(), o.g.copy()
+    # a perturbation large enough that the deviations the parity bound is relative to (>~1e-4) sit well
+    # above the FP64 rounding of the O(1) absolute populations the oracle works in (~1e-15)
     rng = np.random.default_rng(seed)
-    o.f += 1e-3 * rng.uniform(-1, 1, o.f.shape) * np.abs(o.f)
-    o.g += 1e-5 * rng.uniform(-1, 1, o.g.shape)
+    o.f += 1e-2 * rng.uniform(-1, 1, o.f.shape) * np.abs(o.f)
+    o.g += 1e-4 * rng.uniform(-1, 1, o.g.shape)
     gpu = l3.Lattice3D(nx, ny, nz, 0.8, 0.7, B0, Fx, storage)
     gpu.set_walls(c[0], c[1], u[0], u[1])
     gpu.set_side_walls(cs[0], cs[1])
@@ -75,8 +77,12 @@ def test_duct_fp64_matches_oracle(l3, case):
         fg, gg = gpu.get_state()
         df = float(np.max(np.abs(o.f - f_rest)))
         dg = float(np.max(np.abs(o.g - g_rest)))
-        assert np.max(np.abs(fg - o.f)) <= REL64 * df
-        assert np.max(np.abs(gg - o.g)) <= REL64 * dg
+        # relative to the largest deviation, with a floor at the FP64 rounding of the absolute
+        # populations the oracle steps (64 ulp of max |f|): nx = 1 ducts damp the perturbation fast
+        floor_f = 64 * np.finfo(np.float64).eps * float(np.max(np.abs(o.f)))
+        floor_g = 64 * np.finfo(np.float64).eps * float(np.max(np.abs(o.g)))
+        assert np.max(np.abs(fg - o.f)) <= REL64 * df + floor_f
+        assert np.max(np.abs(gg - o.g)) <= REL64 * dg + floor_g
         _fields_close(o.moments(), gpu.moments(), REL64)
     gpu.close()
 
