@@ -224,6 +224,23 @@ lks_status lks_get_state(lks_handle* h, double* host_f, double* host_g);
  * writes them.  Synchronises. */
 lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host_g);
 
+/* Bytes of the handle's state in its own storage image: 19 x nx x ny populations of the storage
+ * type (lks_storage), the 9 f planes then the 10 g planes, each plane ny x nx -- the deviations as
+ * held on the device (FP16 times 2^14; in-place 16-bit handles with even nx keep their rows
+ * interleaved, see lks_params.inplace).  0 for a NULL handle. */
+size_t lks_state_bytes(const lks_handle* h);
+
+/* Copy the state out in that storage image (a bit-exact checkpoint, at the storage type's size:
+ * half the bytes of lks_get_state for FP32, a quarter for 16-bit).  bytes must equal
+ * lks_state_bytes(h) (LKS_EINVAL otherwise); host memory is written by the copy engine (page-locked
+ * host memory moves at the link's full rate).  Synchronises. */
+lks_status lks_get_state_raw(lks_handle* h, void* host, size_t bytes);
+
+/* Replace the state by an image written by lks_get_state_raw of a handle with the same nx, ny,
+ * storage, inplace and B0 (the image is taken as is), reset the step counter and take the residual
+ * snapshot from it.  bytes must equal lks_state_bytes(h).  Synchronises. */
+lks_status lks_set_state_raw(lks_handle* h, const void* host, size_t bytes);
+
 /* Block until all work of the handle has finished; reports asynchronous errors. */
 /* Self-test of the bounded device waits (failure detection without a GPU fault): enqueue on the
  * handle's stream one warp that waits, with the staged kernels' bounded wait, on a shared-memory

@@ -621,6 +621,43 @@ lks_status lks_set_state(lks_handle* h, const double* host_f, const double* host
     return LKS_OK;
 }
 
+size_t lks_state_bytes(const lks_handle* h) {
+    if (!h) return 0;
+    return 19 * (size_t)h->p.nx * (size_t)h->p.ny * lks::storage_bytes(h->p.storage);
+}
+
+lks_status lks_get_state_raw(lks_handle* h, void* host, size_t bytes) {
+    NvtxRange nvtx_range("lks_get_state_raw");
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!host) return fail(h, LKS_EINVAL, "host is NULL");
+    if (bytes != lks_state_bytes(h)) return fail(h, LKS_EINVAL, "bytes differs from lks_state_bytes()");
+    const size_t fb = 9 * (size_t)h->p.nx * h->p.ny * lks::storage_bytes(h->p.storage);
+    cudaError_t e = cudaMemcpyAsync(host, h->f[h->cur], fb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char*)host + fb, h->g[h->cur], bytes - fb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lks_get_state_raw");
+    return staged_check(h, "lks_get_state_raw");
+}
+
+lks_status lks_set_state_raw(lks_handle* h, const void* host, size_t bytes) {
+    NvtxRange nvtx_range("lks_set_state_raw");
+    if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
+    if (!host) return fail(h, LKS_EINVAL, "host is NULL");
+    if (bytes != lks_state_bytes(h)) return fail(h, LKS_EINVAL, "bytes differs from lks_state_bytes()");
+    const size_t fb = 9 * (size_t)h->p.nx * h->p.ny * lks::storage_bytes(h->p.storage);
+    cudaError_t e = cudaMemcpyAsync(h->f[h->cur], host, fb, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->g[h->cur], (const char*)host + fb, bytes - fb, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = lks::launch_snapshot(h->p.storage, h->f[h->cur], h->g[h->cur], h->p.nx, h->p.ny, h->p.B0, h->p.Fx,
+                                 h->snap, h->stream, h->p.coupling, h->p.tau_m, ilv_of(h));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lks_set_state_raw");
+    h->steps = 0;
+    return LKS_OK;
+}
+
 lks_status lks_selftest_wait_timeout(lks_handle* h, double limit_s) {
     if (!h) return fail(nullptr, LKS_EINVAL, "handle is NULL");
     if (!h->staged) return fail(h, LKS_EINVAL, "lks_selftest_wait_timeout: the handle runs no staged kernel");

@@ -71,6 +71,9 @@ SIGNATURES = {
     "lks_get_state": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     "lks_set_state": (ctypes.c_int, [ctypes.c_void_p, _dp, _dp]),
     "lks_sync": (ctypes.c_int, [ctypes.c_void_p]),
+    "lks_state_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "lks_get_state_raw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "lks_set_state_raw": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "lks_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "lks_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "lks_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -230,6 +233,25 @@ class Lattice:
         g = np.ascontiguousarray(g, dtype=np.float64)
         assert f.shape == (9, self.ny, self.nx) and g.shape == (2, 5, self.ny, self.nx)
         _check(load().lks_set_state(self._h, _dptr(f), _dptr(g)), self._h)
+
+    def state_bytes(self):
+        return int(load().lks_state_bytes(self._h))
+
+    def get_state_raw(self, out=None):
+        """The state in the library's storage image (uint8, lks_state_bytes long): a bit-exact
+        checkpoint.  out: optional uint8 numpy array or (pinned) CPU torch tensor to write into."""
+        n = self.state_bytes()
+        if out is None:
+            out = np.empty(n, dtype=np.uint8)
+        ptr = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+        _check(load().lks_get_state_raw(self._h, ctypes.c_void_p(ptr), n), self._h)
+        return out
+
+    def set_state_raw(self, image):
+        """Replace the state by a storage image from get_state_raw (numpy uint8 or CPU torch tensor)."""
+        ptr = image.ctypes.data if isinstance(image, np.ndarray) else image.data_ptr()
+        n = image.nbytes if isinstance(image, np.ndarray) else image.numel() * image.element_size()
+        _check(load().lks_set_state_raw(self._h, ctypes.c_void_p(ptr), n), self._h)
 
     def save(self, path, **meta):
         """Checkpoint: the state (FP64 absolute populations via lks_get_state) and the step count."""
