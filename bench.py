@@ -651,10 +651,12 @@ def bench_sweep(args):
     r64 = res64["records"]
     # (4), (5) the same first K instances, both arms
     K = args.sweep_baseline
-    mixK = sweep.run_mixed(sample[:K], handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=args.sweep_quantum,
-                           max_steps=args.sweep_max_steps, shape=(128, 1, 1))
-    base = sweep.run_one_at_a_time(sample[:K], "f64", tol=1e-10, check_every=100, max_steps=args.sweep_max_steps)
+    base = sweep.run_one_at_a_time(sample[:K], "f64", tol=1e-10, check_every=100, max_steps=args.sweep_max_steps,
+                                   time_limit=args.sweep_time)
     brecs = base["records"]
+    K = len(brecs)   # the instances the baseline reached within its time limit: both arms solve those
+    mixK = sweep.run_mixed(sample[:K], handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=args.sweep_quantum,
+                           max_steps=args.sweep_max_steps, shape=(128, 1, 1), time_budget=args.sweep_time)
     gate = {"instances": K, "fp64_one_at_a_time_unstable": 0, "fp64_one_at_a_time_converged": 0,
             "mixed_vs_fp64_same_grid_le_1e-4": 0, "fp32_vs_fp64_same_grid_le_1e-4": 0,
             "fp64_meets_analytic_le_1e-4": 0, "mixed_meets_analytic_where_fp64_does": 0,

@@ -97,14 +97,17 @@ def run_batched(specs, storage="f32", tol=1e-10, check_every=100, quantum=20000,
     return {"records": recs, "wall": wall, "launches": launches, "tune": tune, "tail_shape_at": tail_at}
 
 
-def run_one_at_a_time(specs, storage="f64", tol=1e-10, check_every=100, max_steps=10**9):
+def run_one_at_a_time(specs, storage="f64", tol=1e-10, check_every=100, max_steps=10**9, time_limit=None):
     """The baseline: for each instance in order, lks_create -> lks_set_walls -> lks_run_to_steady
     -> lks_moments -> lks_destroy on the same GPU.  Latency of instance k = sum of solve times
-    up to k (first-in first-out, all present at t = 0)."""
+    up to k (first-in first-out, all present at t = 0).  time_limit: stop starting new instances
+    after that many seconds (the records then cover the first instances only)."""
     import torch
     recs = []
     t0 = time.perf_counter()
     for spec in specs:
+        if time_limit is not None and time.perf_counter() - t0 > time_limit:
+            break
         p = lattice_params(spec)
         ts = time.perf_counter()
         lat = _lks.Lattice(spec["nx"], spec["ny"], TAU, TAU, p["B0"], p["Fx"], spec["closure"], storage)
