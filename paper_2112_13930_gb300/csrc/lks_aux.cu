@@ -1,5 +1,7 @@
 // lks_aux.cu -- initial state, moments, x-averaged profiles, the steady-state residual
 // reduction and the FP64 <-> storage conversions.  None of these is on the per-step path.
+#include <type_traits>
+
 #include "lks_device.cuh"
 #include "lks_internal.h"
 
@@ -80,9 +82,36 @@ __global__ void init_kernel(S* f, S* g, int64_t N, double B0, uint64_t seed, dou
 // Coupling 0: rho u = sum f~ e - F/2.  Coupling 1: the force includes J x B; the stored g carries
 // (1 - 1/tau_m) Lambda^(1) of the last collision, so with k' = 3/(tau_m - 1) and
 // D~ = Lambda~_yx - Lambda~_xy:  J_z = k' [D~ + 2 (B_y (j_x - F_ext/2) - B_x j_y)/rho] / (1 - k' |B|^2/rho).
+//
+// FP32 and 16-bit storage (C = float, Maxwell coupling): the per-node sums and u are taken in FP32,
+// the type the state is held and stepped in -- the stored values carry FP32 precision at best, so
+// FP64 here only cost time (these readouts were FP64-pipe bound) -- and converted to FP64 for the
+// accumulation across nodes, which stays FP64.  FP64 storage and the Lorentz coupling take FP64.
 template <typename S, typename C>
 __device__ __forceinline__ void node_moments(const S* f, const S* g, int64_t N, int64_t n, const MomentModel& mm,
                                              double m[5]) {
+    if constexpr (std::is_same<C, float>::value) {
+        if (mm.coupling == 0) {
+            float fv[9], gv5[10];
+#pragma unroll
+            for (int a = 0; a < 9; ++a) fv[a] = load_s<S, C>(f + a * N + n);
+#pragma unroll
+            for (int a = 0; a < 10; ++a) gv5[a] = load_s<S, C>(g + a * N + n);
+            const float drho = (((fv[0] + fv[1]) + (fv[2] + fv[3])) + ((fv[4] + fv[5]) + (fv[6] + fv[7]))) + fv[8];
+            const float jx = ((fv[1] - fv[3]) + (fv[5] - fv[6])) + (fv[8] - fv[7]);
+            const float jy = ((fv[2] - fv[4]) + (fv[5] + fv[6])) - (fv[7] + fv[8]);
+            const float bx = ((gv5[0] + gv5[1]) + (gv5[2] + gv5[3])) + gv5[4];
+            const float dby = ((gv5[5] + gv5[6]) + (gv5[7] + gv5[8])) + gv5[9];
+            const float rho = 1.0f + drho;
+            const float inv = __frcp_rn(rho);
+            m[0] = (double)rho;
+            m[1] = (double)__fmul_rn(__fadd_rn(jx, -0.5f * (float)mm.Fx), inv);
+            m[2] = (double)__fmul_rn(jy, inv);
+            m[3] = (double)bx;
+            m[4] = mm.B0 + (double)dby;
+            return;
+        }
+    }
     double drho = 0.0, jx = 0.0, jy = 0.0, bx = 0.0, dby = 0.0;
     double gv[10];
 #pragma unroll
