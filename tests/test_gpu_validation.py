@@ -4,7 +4,7 @@ and an E3 pair (grid convergence), solved with the FP64 batched engine to a resi
 
 Each case's profiles equal the FP64 oracle's after the same number of steps (1e-11 of the profile
 scale), its error against the closed form is within the E-tables' bounds, and the E3 pair converges
-at second order; the summary CSVs the driver writes hold the same numbers."""
+at second order; the summary CSVs validation.run writes hold the same numbers."""
 import csv
 import math
 import os
