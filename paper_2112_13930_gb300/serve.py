@@ -18,7 +18,8 @@ FP64 finish (finish_tol set): the lanes run in the server's storage type (FP32) 
 residual `finish_tol` (or until they stall at FP32's rounding floor), then continue in FP64 to `tol`,
 a residual FP32 cannot certify: small-lane instances move into a second, FP64 batch
 (lks_batch_get_state / lks_batch_set_state), large-lane lattices are replaced by an FP64 lattice
-with the same state (lks_get_state / lks_set_state).
+with the same state (lks_get_state / lks_set_state).  max_steps is the request's whole budget: the
+FP64 phase gets what the FP32 phase left.
 
 Failure handling (all on the host): a request the library rejects (LKS_EINVAL) is recorded as
 "rejected" and the server continues; an exception while solving a large-lane request is recorded
@@ -42,7 +43,8 @@ TAU = _sweep.TAU
 
 
 def _finish_fp64(lat32, req, stream, tol, check_every, max_steps):
-    """Continue a lattice's state in FP64 to tol: lks_get_state -> FP64 lattice -> lks_set_state."""
+    """Continue a lattice's state in FP64 to tol (at most max_steps more steps): lks_get_state ->
+    FP64 lattice -> lks_set_state."""
     f, g = lat32.get_state()
     lat32.close()
     lat = _default_lattice(req, "f64", stream)
@@ -143,9 +145,14 @@ class Server:
             st, steps, r = self.batch.result(slot)
             if st == _batch.INST_RUNNING:
                 continue
-            if self.batch64 is not None and st in (_batch.INST_CONVERGED, _batch.INST_STALLED):
-                # hand the state over to the FP64 batch; wait there for a slot and memory
-                d = _sweep.make_desc(rec["req"], self.tol, self.check_every, self.max_steps)
+            if self.batch64 is not None and st in (_batch.INST_CONVERGED, _batch.INST_STALLED) \
+                    and steps < self.max_steps:
+                # hand the state over to the FP64 batch with what is left of the step budget; wait
+                # there for a slot and memory
+                left = self.max_steps - int(steps)
+                if self.inplace:
+                    left -= left & 1
+                d = _sweep.make_desc(rec["req"], self.tol, self.check_every, left)
                 s64 = self.batch64.add(d)
                 if s64 is None:
                     continue
@@ -179,9 +186,10 @@ class Server:
             if self.finish_tol:
                 steps, r, status = lat.run_to_steady(self.finish_tol, self.check_every, self.max_steps,
                                                      raise_on_fail=False)
-                if status in (_lks.LKS_OK, _lks.LKS_ESTALLED):
+                if status in (_lks.LKS_OK, _lks.LKS_ESTALLED) and steps < self.max_steps:
+                    # the FP64 phase gets what is left of the request's step budget
                     s64, r, status, u, b = _finish_fp64(lat, req, self.streams[sidx], self.tol, self.check_every,
-                                                        self.max_steps)
+                                                        self.max_steps - steps)
                     steps += s64
                 else:
                     u, b = lat.profiles()

@@ -128,7 +128,8 @@ def run_mixed(specs, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=20000
     """The mixed-precision lane: every instance starts in an FP32 batch with tolerance handoff_tol;
     as soon as it leaves RUNNING there (converged at handoff_tol, or stalled at FP32's rounding floor)
     its state moves (lks_batch_get_state / lks_batch_set_state) into an FP64 batch that runs it to
-    tol, a residual FP32 storage cannot certify.  The two batches' launches alternate on the GPU.
+    tol, a residual FP32 storage cannot certify, with what is left of its max_steps (the budget covers
+    both phases).  The two batches' launches alternate on the GPU.
     Unstable instances and instances at max_steps end in the FP32 lane.  Time-to-steady of an instance
     is the wall time at the end of the FP64 launch in which it left RUNNING."""
     import torch
@@ -160,8 +161,10 @@ def run_mixed(specs, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=20000
                 if st == _batch.INST_RUNNING:
                     continue
                 steps32[k], state32[k] = int(steps), _batch.STATE_NAMES[st]
-                if st in (_batch.INST_CONVERGED, _batch.INST_STALLED):
+                if st in (_batch.INST_CONVERGED, _batch.INST_STALLED) and steps < max_steps:
+                    # the FP64 phase gets what is left of the instance's step budget
                     f, g = b32.get_state(s)
+                    d64[k].max_steps = max_steps - int(steps)
                     s64[k] = b64.add(d64[k])
                     b64.set_state(s64[k], f, g)
                     b32.remove(s)

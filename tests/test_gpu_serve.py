@@ -81,7 +81,8 @@ def test_admission_waits_for_memory(mods):
 
 
 def test_served_fp64_finish_equals_solo_mixed_solves(mods):
-    """With finish_tol the server hands each request from FP32 (at residual 1e-5) to FP64 (to 1e-9);
+    """With finish_tol the server hands each request from FP32 (at residual 1e-5) to FP64 (to 1e-9,
+    with what is left of its 40 000-step budget);
     every result equals the same hand-off done alone: small lane, an FP32 batch then an FP64 batch
     through lks_batch_get_state / lks_batch_set_state; large lane, an FP32 lattice then an FP64
     lattice through lks_get_state / lks_set_state -- bit for bit."""
@@ -101,10 +102,10 @@ def test_served_fp64_finish_equals_solo_mixed_solves(mods):
             while b32.run(2000):
                 pass
             st32, steps32, _ = b32.result(s)
-            if st32 in (batch.INST_CONVERGED, batch.INST_STALLED):
+            if st32 in (batch.INST_CONVERGED, batch.INST_STALLED) and steps32 < 40_000:
                 b64 = batch.Batch("f64", max_instances=1, pool_bytes=64 << 20, threads_per_group=64,
                                   groups_per_cta=1)
-                s64 = b64.add(sweep.make_desc(req, 1e-9, 100, 40_000))
+                s64 = b64.add(sweep.make_desc(req, 1e-9, 100, 40_000 - steps32))
                 b64.set_state(s64, *b32.get_state(s))
                 while b64.run(2000):
                     pass
@@ -122,13 +123,13 @@ def test_served_fp64_finish_equals_solo_mixed_solves(mods):
             lat = lks.Lattice(req["nx"], req["ny"], 0.8, 0.8, p["B0"], p["Fx"], req["closure"], "f32")
             lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
             steps, r, status = lat.run_to_steady(1e-5, 100, 40_000, raise_on_fail=False)
-            if status in (lks.LKS_OK, lks.LKS_ESTALLED):
+            if status in (lks.LKS_OK, lks.LKS_ESTALLED) and steps < 40_000:
                 f, g = lat.get_state()
                 lat.close()
                 lat = lks.Lattice(req["nx"], req["ny"], 0.8, 0.8, p["B0"], p["Fx"], req["closure"], "f64")
                 lat.set_walls(p["c_bottom"], p["c_top"], p["u_bottom"], p["u_top"])
                 lat.set_state(f, g)
-                s64, r, status = lat.run_to_steady(1e-9, 100, 40_000, raise_on_fail=False)
+                s64, r, status = lat.run_to_steady(1e-9, 100, 40_000 - steps, raise_on_fail=False)
                 steps += s64
             u, bx = lat.profiles()
             lat.close()
