@@ -143,6 +143,7 @@ def run_mixed(specs, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=20000
     b32 = _batch.Batch("f32", max_instances=len(specs), pool_bytes=pool32, **kw)
     b64 = _batch.Batch("f64", max_instances=len(specs), pool_bytes=pool64, **kw)
     s32 = [b32.add(d) for d in d32]
+    left32 = [False] * len(specs)  # the instance left the FP32 batch (moved on, or ended there)
     s64 = [None] * len(specs)
     steps32 = [0] * len(specs)
     state32 = [None] * len(specs)
@@ -155,11 +156,12 @@ def run_mixed(specs, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=20000
             running32 = b32.run(quantum)
             launches += 1
             for k, s in enumerate(s32):
-                if s is None:
+                if s is None or left32[k]:
                     continue
                 st, steps, r = b32.result(s)
                 if st == _batch.INST_RUNNING:
                     continue
+                left32[k] = True
                 steps32[k], state32[k] = int(steps), _batch.STATE_NAMES[st]
                 if st in (_batch.INST_CONVERGED, _batch.INST_STALLED) and steps < max_steps:
                     # the FP64 phase gets what is left of the instance's step budget

@@ -306,3 +306,40 @@ def test_fp32_floor_finished_in_fp64(mods):
     assert stepsf < stepsp   # the FP32 phase already covered part of the way
     b32.close()
     b64.close()
+
+
+def test_mixed_lane_equals_solo_handoffs(mods):
+    """sweep.run_mixed: every instance's result equals the same hand-off done alone (an FP32 batch of
+    one to the hand-off residual, then, if it converged or stalled within its budget, an FP64 batch of
+    one from that state with what is left of the budget) -- bit for bit; each instance's
+    time-to-steady is recorded once and lies within the run."""
+    lks, batch = mods
+    from paper_2112_13930_gb300 import sweep, workloads
+    specs = workloads.sweep_instances(n=6, seed=11, ny_range=(33, 65), ha_range=(1.0, 4.0))
+    budget, shape = 12_000, (64, 2)
+    out = sweep.run_mixed(specs, handoff_tol=1e-5, tol=1e-9, check_every=100, quantum=1000, max_steps=budget,
+                          shape=shape)
+    kw = dict(threads_per_group=shape[0], groups_per_cta=shape[1])
+    for spec, rec in zip(specs, out["records"]):
+        assert rec["t_done"] is not None and 0.0 <= rec["t_done"] <= out["wall"]
+        b32 = batch.Batch("f32", max_instances=1, pool_bytes=64 << 20, **kw)
+        s = b32.add(sweep.make_desc(spec, 1e-5, 100, budget))
+        while b32.run(1000):
+            pass
+        st32, steps32, _ = b32.result(s)
+        assert rec["fp32_state"] == batch.STATE_NAMES[st32] and rec["steps_fp32"] == steps32
+        if st32 in (batch.INST_CONVERGED, batch.INST_STALLED) and steps32 < budget:
+            b64 = batch.Batch("f64", max_instances=1, pool_bytes=64 << 20, **kw)
+            s64 = b64.add(sweep.make_desc(spec, 1e-9, 100, budget - steps32))
+            b64.set_state(s64, *b32.get_state(s))
+            while b64.run(1000):
+                pass
+            st, steps64, _ = b64.result(s64)
+            u, bx = b64.profiles(s64)
+            assert rec["state"] == batch.STATE_NAMES[st] and rec["steps_fp64"] == steps64
+            b64.close()
+        else:
+            u, bx = b32.profiles(s)
+            assert rec["state"] == "fp32_" + batch.STATE_NAMES[st32] and rec["steps_fp64"] == 0
+        b32.close()
+        assert np.array_equal(u, rec["u"]) and np.array_equal(bx, rec["b"])
