@@ -369,6 +369,22 @@ def bench_ours(args):
                 ts[k].append(v)
         e2e["breakdown_ms"] = {k: round(min(v) * 1e3, 2) for k, v in ts.items()}
         e2e["breakdown_ms"]["steps_at_device_rate"] = round(per_launch * args.steps * 1e3, 2)
+        # the host link's own rate: a plain copy of the same pinned image into device memory (one
+        # cudaMemcpyAsync, CUDA events, best of 3), beside the rate lks_set_state_raw reaches
+        dev_img = torch.empty(img.numel(), dtype=torch.uint8, device="cuda")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_link = math.inf
+        for _ in range(3):
+            ev0.record()
+            dev_img.copy_(img, non_blocking=True)
+            ev1.record()
+            ev1.synchronize()
+            t_link = min(t_link, ev0.elapsed_time(ev1) / 1e3)
+        e2e["host_link"] = {"h2d_gbs": round(img.numel() / t_link / 1e9, 1),
+                            "lks_set_state_raw_gbs": round(img.numel() / min(ts["lks_set_state_raw"]) / 1e9, 1),
+                            "what": "a plain copy of the pinned state image to device memory, against "
+                                    "lks_set_state_raw of the same image (its snapshot pass and synchronisation included)"}
+        del dev_img
         del f_host, g_host, m_host, img
     lat.close()
     del lat
