@@ -537,7 +537,12 @@ def bench_precision(args):
                 import oracle
                 o = oracle.Oracle(n, n, tau, tau, b0c, fxc, oracle.LINK if cl == "link" else oracle.MOMENT, c, c,
                                   seed=seed, perturb_amp=amp)
+                t_or = time.perf_counter()
                 o.step(2)
+                t_or = time.perf_counter() - t_or
+                out["oracle_host"] = {"kind": "oracle", "mlups": round(n * n * 2 / t_or / 1e6, 3),
+                                      "cores": oracle.threads_used(),
+                                      "sample": "2 FP64 oracle steps of the full %d x %d lattice (%.1f s)" % (n, n, t_or)}
                 lat.step(2)
                 mo = o.moments()
                 mg = torch.empty((5, n, n), dtype=torch.float64, device="cuda")
@@ -697,6 +702,34 @@ def bench_sweep(args):
         if da <= 1e-4:
             gate["fp64_meets_analytic_le_1e-4"] += 1
             gate["mixed_meets_analytic_where_fp64_does"] += int(max(m["l2_u"], m["l2_b"]) <= 1e-4)
+    # The FP64 oracle on the host cores: 2000 steps of each of the first instances (until about
+    # --cpu-seconds of CPU work), extrapolated by node-updates to the steps the one-at-a-time FP64
+    # arm needed for its instances.  Marked as an extrapolation.
+    oracle_est = None
+    if not args.skip_cpu:
+        import oracle
+        t_or, nu_or, used, k_or = 0.0, 0, 0, 2000
+        for spec in sample[:K]:
+            if t_or > args.cpu_seconds:
+                break
+            p = sweep.lattice_params(spec)
+            o = oracle.Oracle(spec["nx"], spec["ny"], sweep.TAU, sweep.TAU, p["B0"], p["Fx"],
+                              oracle.LINK if spec["closure"] == "link" else oracle.MOMENT, p["c_bottom"], p["c_top"],
+                              p["u_bottom"], p["u_top"])
+            t1 = time.perf_counter()
+            o.step(k_or)
+            t_or += time.perf_counter() - t1
+            nu_or += spec["nx"] * spec["ny"] * k_or
+            used += 1
+            del o
+        rate = nu_or / t_or
+        need = sum(spec["nx"] * spec["ny"] * bb["steps"] for spec, bb in zip(sample[:K], brecs))
+        oracle_est = {"kind": "oracle", "extrapolated": True, "cores": oracle.threads_used(),
+                      "mlups": round(rate / 1e6, 3), "est_wall_s": round(need / rate, 1),
+                      "node_updates": int(need),
+                      "sample": "%d FP64 oracle steps of each of the first %d instances (%.1f s), scaled to the "
+                                "step counts the one-at-a-time FP64 arm needed on its %d instances" % (
+                                    k_or, used, t_or, K)}
     # L2-resident copy bandwidth (2 x 24 MB, well inside the 129 MB L2), the roofline of the batched
     # kernel whose small instances stay in L2 while resident
     a = torch.empty(6 << 20, dtype=torch.float32, device="cuda")
@@ -756,7 +789,8 @@ def bench_sweep(args):
                                       "time_to_steady_p99_s": pct([r["t_done"] for r in brecs], 99),
                                       "statuses": {lks._status_name(k): sum(r["status"] == k for r in brecs)
                                                    for k in {r["status"] for r in brecs}}},
-               "gate": gate},
+               "gate": gate,
+               "oracle_host": oracle_est},
            "settings": {"quantum": args.sweep_quantum, "max_steps": args.sweep_max_steps, "check_every": 100,
                         "time_budget_s": args.sweep_time, "mixed_shape": [128, 1, 1]}}
     print(json.dumps(out), flush=True)
