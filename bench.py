@@ -792,7 +792,8 @@ def bench_sweep(args):
                "gate": gate,
                "oracle_host": oracle_est},
            "settings": {"quantum": args.sweep_quantum, "max_steps": args.sweep_max_steps, "check_every": 100,
-                        "time_budget_s": args.sweep_time, "mixed_shape": [128, 1, 1]}}
+                        "time_budget_s": args.sweep_time, "mixed_shape": [128, 1, 1],
+                        "mixed_tail_shape": [128, 1, 8], "mixed_tail_below": "number of SMs"}}
     print(json.dumps(out), flush=True)
     return 0
 

@@ -124,14 +124,19 @@ def run_one_at_a_time(specs, storage="f64", tol=1e-10, check_every=100, max_step
 
 
 def run_mixed(specs, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=20000, max_steps=10**9,
-              shape=None, time_budget=None):
+              shape=None, time_budget=None, tail_shape=(128, 1, 8), tail_below=None):
     """The mixed-precision lane: every instance starts in an FP32 batch with tolerance handoff_tol;
     as soon as it leaves RUNNING there (converged at handoff_tol, or stalled at FP32's rounding floor)
     its state moves (lks_batch_get_state / lks_batch_set_state) into an FP64 batch that runs it to
     tol, a residual FP32 storage cannot certify, with what is left of its max_steps (the budget covers
     both phases).  The two batches' launches alternate on the GPU.
     Unstable instances and instances at max_steps end in the FP32 lane.  Time-to-steady of an instance
-    is the wall time at the end of the FP64 launch in which it left RUNNING."""
+    is the wall time at the end of the FP64 launch in which it left RUNNING.
+
+    Shape policy, per batch: `shape` (default 128 threads per instance, one instance per CTA) while
+    the batch holds at least `tail_below` running instances (default: the number of SMs), else
+    `tail_shape` -- each instance on a cluster of CTAs, so that few instances still occupy the GPU.
+    Results do not depend on the shape."""
     import torch
     d32 = [make_desc(s, handoff_tol, check_every, max_steps) for s in specs]
     d64 = [make_desc(s, tol, check_every, max_steps) for s in specs]
@@ -142,6 +147,16 @@ def run_mixed(specs, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=20000
         kw = dict(threads_per_group=shape[0], groups_per_cta=shape[1], cluster_ctas=shape[2] if len(shape) > 2 else 0)
     b32 = _batch.Batch("f32", max_instances=len(specs), pool_bytes=pool32, **kw)
     b64 = _batch.Batch("f64", max_instances=len(specs), pool_bytes=pool64, **kw)
+    base = tuple(shape[:3]) + (1,) * (3 - len(shape)) if shape else (128, 1, 1)
+    if tail_below is None:
+        tail_below = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    cur = {id(b32): base if shape else None, id(b64): base if shape else None}
+
+    def fit_shape(b, running):
+        want = tuple(tail_shape) if tail_shape and running < tail_below else base
+        if cur[id(b)] != want:
+            b.set_shape(*want)
+            cur[id(b)] = want
     s32 = [b32.add(d) for d in d32]
     left32 = [False] * len(specs)  # the instance left the FP32 batch (moved on, or ended there)
     s64 = [None] * len(specs)
@@ -153,6 +168,7 @@ def run_mixed(specs, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=20000
     running32, running64, launches = len(specs), 0, 0
     while running32 or running64:
         if running32:
+            fit_shape(b32, running32)
             running32 = b32.run(quantum)
             launches += 1
             for k, s in enumerate(s32):
@@ -173,6 +189,7 @@ def run_mixed(specs, handoff_tol=1e-5, tol=1e-10, check_every=100, quantum=20000
                     s32[k] = None
                 else:
                     done_at[k] = time.perf_counter() - t0  # ends in the FP32 lane
+        fit_shape(b64, sum(1 for k, s in enumerate(s64) if s is not None and done_at[k] is None))
         running64 = b64.run(quantum)
         launches += 1
         now = time.perf_counter() - t0

@@ -311,14 +311,16 @@ def test_fp32_floor_finished_in_fp64(mods):
 def test_mixed_lane_equals_solo_handoffs(mods):
     """sweep.run_mixed: every instance's result equals the same hand-off done alone (an FP32 batch of
     one to the hand-off residual, then, if it converged or stalled within its budget, an FP64 batch of
-    one from that state with what is left of the budget) -- bit for bit; each instance's
-    time-to-steady is recorded once and lies within the run."""
+    one from that state with what is left of the budget) -- bit for bit, although the batches change
+    shape on the way; each instance's time-to-steady is recorded once and lies within the run."""
     lks, batch = mods
     from paper_2112_13930_gb300 import sweep, workloads
     specs = workloads.sweep_instances(n=6, seed=11, ny_range=(33, 65), ha_range=(1.0, 4.0))
     budget, shape = 12_000, (64, 2)
+    # tail_below=4: each batch runs in the base shape while 4 or more of its instances run, then on
+    # clusters of 8 CTAs per instance
     out = sweep.run_mixed(specs, handoff_tol=1e-5, tol=1e-9, check_every=100, quantum=1000, max_steps=budget,
-                          shape=shape)
+                          shape=shape, tail_shape=(128, 1, 8), tail_below=4)
     kw = dict(threads_per_group=shape[0], groups_per_cta=shape[1])
     for spec, rec in zip(specs, out["records"]):
         assert rec["t_done"] is not None and 0.0 <= rec["t_done"] <= out["wall"]
