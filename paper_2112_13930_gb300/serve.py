@@ -68,10 +68,15 @@ def _default_lattice(req, storage, stream, inplace=False):
 class Server:
     def __init__(self, storage="f32", budget_bytes=120 << 30, small_pool_bytes=8 << 30, small_max_nodes=32768,
                  max_small=8192, large_workers=6, tol=1e-9, check_every=100, quantum=2000, max_steps=10**9,
-                 shape=None, batch=None, lattice_factory=None, streams=None, inplace=False, finish_tol=None):
+                 shape=None, batch=None, lattice_factory=None, streams=None, inplace=False, finish_tol=None,
+                 tail_shape=(128, 1, 8), tail_below=None):
         """inplace=True: every request keeps one population buffer (in-place pairs of steps, same
         results), so the memory budget admits about twice the requests; quantum, check_every and
-        max_steps must then be even.  finish_tol: hand-off residual of the FP64 finish (None: off)."""
+        max_steps must then be even.  finish_tol: hand-off residual of the FP64 finish (None: off).
+        Shape policy of the small lane's batches: `shape` (default 256 threads per instance, one
+        instance per CTA) while a batch holds at least `tail_below` requests (default: the number of
+        SMs), else `tail_shape` (each request on a cluster of CTAs; None: never).  A batch passed
+        in as `batch` keeps the shape its caller gave it.  Results do not depend on the shape."""
         self.storage = storage
         self.inplace = bool(inplace)
         self.tol, self.check_every, self.quantum, self.max_steps = tol, check_every, quantum, max_steps
@@ -87,11 +92,16 @@ class Server:
                                         threads_per_group=shape[0] if shape else 0,
                                         groups_per_cta=shape[1] if shape else 0,
                                         cluster_ctas=shape[2] if shape and len(shape) > 2 else 0)
+        self._own_batch = batch is None
         if batch is None:
             batch = _batch.Batch(storage, max_instances=max_small, pool_bytes=small_pool_bytes,
                                  threads_per_group=shape[0] if shape else 0, groups_per_cta=shape[1] if shape else 0,
                                  cluster_ctas=shape[2] if shape and len(shape) > 2 else 0, inplace=inplace)
         self.batch = batch
+        self.base_shape = (tuple(shape[:3]) + (1,) * (3 - len(shape))) if shape else (256, 1, 1)
+        self.tail_shape = tuple(tail_shape) if tail_shape else None
+        self.tail_below = tail_below  # None: the number of SMs, looked up at first use
+        self._shape = {}  # id(batch) -> the shape last set (None: as created)
         self.lattice_factory = lattice_factory or (
             lambda req, stream: _default_lattice(req, storage, stream, inplace))
         if streams is None:
@@ -267,8 +277,10 @@ class Server:
                 q_large.popleft()
             if self.small_slots or self.small64:
                 if self.small_slots:
+                    self._fit_shape(self.batch, len(self.small_slots))
                     self.batch.run(self.quantum)
                 if self.small64:
+                    self._fit_shape(self.batch64, len(self.small64))
                     self.batch64.run(self.quantum)
             else:
                 time.sleep(0.0005)
@@ -281,6 +293,18 @@ class Server:
             rec["t_arrival"] = rec["req"]["t_arrival"]
             rec["latency"] = rec["t_done"] - rec["t_arrival"]
         return out
+
+    def _fit_shape(self, b, n):
+        """Clusters of CTAs per request while the batch holds fewer than tail_below requests."""
+        if b is self.batch and not self._own_batch:
+            return
+        if self.tail_below is None:
+            import torch
+            self.tail_below = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        want = self.tail_shape if self.tail_shape and n < self.tail_below else self.base_shape
+        if self._shape.get(id(b), self.base_shape) != want:
+            b.set_shape(*want)
+            self._shape[id(b)] = want
 
     def close(self):
         self.pool.shutdown(wait=True)
