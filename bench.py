@@ -722,6 +722,7 @@ def bench_sweep(args):
             nu_or += spec["nx"] * spec["ny"] * k_or
             used += 1
             del o
+    if not args.skip_cpu and used > 0:
         rate = nu_or / t_or
         need = sum(spec["nx"] * spec["ny"] * bb["steps"] for spec, bb in zip(sample[:K], brecs))
         oracle_est = {"kind": "oracle", "extrapolated": True, "cores": oracle.threads_used(),
