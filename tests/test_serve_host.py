@@ -148,3 +148,46 @@ def test_large_lane_memory_budget_serialises():
     srv.close()
     assert all(r["state"] == "converged" for r in recs)
     assert FakeLattice.peak == 1          # the large-lane share holds one lattice at a time
+
+
+class ShapedFakeBatch(FakeBatch):
+    """FakeBatch that the server creates itself (it stands in for batch.Batch) and that records
+    every shape the server sets."""
+    made = []
+
+    def __init__(self, storage, max_instances, pool_bytes, threads_per_group=0, groups_per_cta=0, cluster_ctas=0,
+                 inplace=False, **kw):
+        super().__init__(max_instances)
+        self.shapes = []
+        ShapedFakeBatch.made.append(self)
+
+    def set_shape(self, threads_per_group, groups_per_cta, cluster_ctas=1):
+        self.shapes.append(((threads_per_group, groups_per_cta, cluster_ctas), len(self.slots)))
+
+
+def test_small_lane_moves_to_clusters_below_tail(monkeypatch):
+    """The server's own small-lane batch keeps its base shape while it holds tail_below or more
+    requests and moves to tail_shape (clusters of CTAs) once fewer remain; a batch handed in by
+    the caller is never reshaped."""
+    ShapedFakeBatch.made = []
+    monkeypatch.setattr(serve._batch, "Batch", ShapedFakeBatch)
+    FakeLattice.active = FakeLattice.peak = 0
+    trace = [_req(i, ny=30 + 10 * i) for i in range(5)]   # done after 300, 400, ..., 700 steps
+    srv = serve.Server("f32", budget_bytes=1 << 30, small_pool_bytes=1 << 29, small_max_nodes=1000, max_small=8,
+                       large_workers=1, tol=1e-9, quantum=100, lattice_factory=FakeLattice, streams=[None],
+                       shape=(64, 2), tail_shape=(128, 1, 8), tail_below=3)
+    recs = srv.serve(trace, time_limit=30)
+    srv.close()
+    assert sorted(r["state"] for r in recs) == ["converged"] * 5
+    assert len(ShapedFakeBatch.made) == 1
+    # 5, 4, 3 resident: the base shape (64, 2, 1), set at creation; 2 resident: the clusters, once
+    assert ShapedFakeBatch.made[0].shapes == [((128, 1, 8), 2)]
+
+    given = ShapedFakeBatch("f32", 8, 1 << 29)
+    srv = serve.Server("f32", budget_bytes=1 << 30, small_pool_bytes=1 << 29, small_max_nodes=1000, max_small=8,
+                       large_workers=1, tol=1e-9, quantum=100, lattice_factory=FakeLattice, streams=[None],
+                       batch=given, tail_shape=(128, 1, 8), tail_below=3)
+    recs = srv.serve([_req(i, ny=30 + 10 * i) for i in range(5)], time_limit=30)
+    srv.close()
+    assert sorted(r["state"] for r in recs) == ["converged"] * 5
+    assert given.shapes == []
