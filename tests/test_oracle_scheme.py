@@ -364,3 +364,45 @@ def test_lorentz_coupling_rest_state_and_stored_moments(closure):
     o.step(5)
     _, _, mom = o.step_detail()
     np.testing.assert_allclose(o.moments(), mom, rtol=1e-12, atol=1e-16)
+
+
+# ---- total-pressure balance across a steady channel ------------------------------------------
+# In a fully developed channel nothing varies along x, so the steady y-momentum balance reads
+# d/dy Pi_yy = F_y.  With the Maxwell stress in f^eq (R1) the momentum flux is
+# Pi_yy = rho c_s^2 + |B|^2/2 - B_y^2 and F_y = 0; with the paper's Lorentz force (Sec. IV-V) the
+# flux is rho c_s^2 and F_y = J_z B_x with J_z = -dB_x/dy (B_y = B0 is uniform), i.e.
+# F_y = -d/dy (B_x^2/2).  Either way rho c_s^2 + B_x^2/2 is the same at every y: the density carries
+# the magnetic pressure of the induced field.  With the stress in the equilibrium this holds
+# exactly on the lattice; through the force it holds to the scheme's O(N^-2).
+
+
+def _steady_channel(ny, closure, coupling, ha=5.0, c=0.5):
+    a = ny / 2 if closure == oracle.LINK else (ny - 1) / 2
+    b0 = an.b0_from_ha(ha, a, 0.8, 0.8)
+    fx = an.force_for_centre_speed(0.01, ha, c, a, 0.8)
+    o = oracle.Oracle(2, ny, 0.8, 0.8, b0, fx, closure, c, c, coupling=coupling)
+    o.run_to_steady(1e-12, 200, 3_000_000)
+    m = o.moments()
+    return m[0].mean(axis=1), m[3].mean(axis=1)
+
+
+def _pressure_spread(rho, bx):
+    """Spread of rho c_s^2 + B_x^2/2 across the channel, relative to the largest B_x^2/2."""
+    total = rho * CS2 + 0.5 * bx ** 2
+    return (total.max() - total.min()) / (0.5 * np.max(bx ** 2))
+
+
+@pytest.mark.parametrize("closure", [oracle.LINK, oracle.MOMENT])
+def test_maxwell_channel_total_pressure_is_uniform(closure):
+    rho, bx = _steady_channel(33, closure, 0)
+    assert _pressure_spread(rho, bx) < 1e-9
+    # and the density does vary, by the magnetic pressure
+    assert (rho.max() - rho.min()) * CS2 > 0.99 * 0.5 * np.max(bx ** 2)
+
+
+@pytest.mark.parametrize("closure", [oracle.LINK, oracle.MOMENT])
+def test_lorentz_channel_total_pressure_is_uniform_at_second_order(closure):
+    s33 = _pressure_spread(*_steady_channel(33, closure, 1))
+    s65 = _pressure_spread(*_steady_channel(65, closure, 1))
+    assert s33 < 5e-3 and s65 < 1.5e-3, (s33, s65)
+    assert 3.0 < s33 / s65 < 4.6, (s33, s65)
