@@ -220,3 +220,22 @@ def test_mutant_fails_a_pin(tmp_path, name):
     text = open(SRC3).read()
     assert text.count(old) == 1, name
     assert not _pins_pass(_compile(tmp_path, name, text.replace(old, new)))
+
+
+def test_steady_channel_total_pressure_is_uniform():
+    """Nothing varies along x or z in the steady channel, so d/dy Pi_yy = 0.  With the Maxwell stress
+    in the D3Q19 equilibrium (trace part included), Pi_yy = rho c_s^2 + |B|^2/2 - B_y^2 with B_y = B0
+    uniform, so rho c_s^2 + B_x^2/2 is the same at every y, exactly on the lattice; the density
+    carries the induced field's magnetic pressure."""
+    ny = 33
+    a = ny / 2
+    b0 = an.b0_from_ha(5.0, a, 0.8, 0.8)
+    fx = an.force_for_centre_speed(0.01, 5.0, 0.5, a, 0.8)
+    o = oracle.Oracle3D(1, ny, 1, 0.8, 0.8, b0, fx, c_bot=0.5, c_top=0.5)
+    o.run_to_steady(1e-12, 200, 3_000_000)
+    m = o.moments()
+    rho, bx = m[0][0, :, 0], m[4][0, :, 0]
+    mag = 0.5 * np.max(bx ** 2)
+    total = rho / 3.0 + 0.5 * bx ** 2
+    assert (total.max() - total.min()) < 1e-9 * mag
+    assert (rho.max() - rho.min()) / 3.0 > 0.99 * mag
