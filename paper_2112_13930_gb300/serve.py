@@ -101,7 +101,7 @@ class Server:
         self.base_shape = (tuple(shape[:3]) + (1,) * (3 - len(shape))) if shape else (256, 1, 1)
         self.tail_shape = tuple(tail_shape) if tail_shape else None
         self.tail_below = tail_below  # None: the number of SMs, looked up at first use
-        self._shape = {}  # id(batch) -> the shape last set (None: as created)
+        self._shape = {}  # id(batch) -> the shape last set (absent: base_shape, as the batch was created)
         self.lattice_factory = lattice_factory or (
             lambda req, stream: _default_lattice(req, storage, stream, inplace))
         if streams is None:
