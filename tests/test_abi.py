@@ -183,3 +183,33 @@ def test_3d_footprint_counts_both_buffers(lib):
         fp = lks3d.footprint_bytes(256, 256, 256, storage)
         pops = 2 * 40 * n * sb
         assert pops + 2 * n * 8 <= fp < pops + 2 * n * 8 + (1 << 20)
+
+
+def test_newer_entry_points_validate_before_device_work(lib):
+    """The raw state image, the allocation-free residual, the duct's side walls and the batch state
+    transfer and shape calls reject a NULL handle or bad arguments before any device work."""
+    buf = (ctypes.c_double * 16)()
+    vp = ctypes.cast(buf, ctypes.c_void_p)
+    dp = ctypes.cast(buf, ctypes.POINTER(ctypes.c_double))
+    assert lib.lks_state_bytes(None) == 0
+    assert lib.lks_get_state_raw(None, vp, 16) == lks.LKS_EINVAL
+    assert lib.lks_set_state_raw(None, vp, 16) == lks.LKS_EINVAL
+
+    def noalloc(f=vp, g=vp, storage=lks.F64, nx=4, ny=8, coupling=lks.MAXWELL, tau_m=0.8, snap=vp, out=dp):
+        return lib.lks_residual_noalloc(f, g, storage, nx, ny, 0.01, 0.0, coupling, tau_m, snap, out, None)
+
+    assert noalloc(f=None) == lks.LKS_EINVAL
+    assert noalloc(snap=None) == lks.LKS_EINVAL
+    assert noalloc(out=None) == lks.LKS_EINVAL
+    assert noalloc(storage=7) == lks.LKS_EINVAL
+    assert noalloc(nx=0) == lks.LKS_EINVAL
+    assert noalloc(coupling=5) == lks.LKS_EINVAL
+    assert noalloc(coupling=lks.LORENTZ, tau_m=1.02) == lks.LKS_EINVAL   # J cannot be read back at tau_m = 1
+    assert noalloc(nx=1 << 16, ny=(1 << 14) + 1) == lks.LKS_EINVAL       # above 2^30 nodes
+    assert b"lks_residual_noalloc" in lib.lks_last_error(None)
+
+    from paper_2112_13930_gb300 import lks3d  # noqa: F401 -- the 3D signatures are set on load
+    assert lib.lks3_set_side_walls(None, 1, 0.1, 0.1) == lks.LKS_EINVAL
+    assert lib.lks_batch_get_state(None, 0, dp, dp) == lks.LKS_EINVAL
+    assert lib.lks_batch_set_state(None, 0, dp, dp) == lks.LKS_EINVAL
+    assert lib.lks_batch_set_shape(None, 128, 1, 8) == lks.LKS_EINVAL
